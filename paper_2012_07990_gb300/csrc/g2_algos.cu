@@ -1,0 +1,656 @@
+// g2_algos.cu — BFS, connected components, delta-stepping SSSP and
+// betweenness centrality (Sec. VII) as host loops over edgeset.apply rounds
+// (the default, unfused schedules: the host reads the frontier size every
+// round, Fig. 3 left / right).  The fused variants live in g2_fused.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "g2_host.h"
+#include "g2_lb.cuh"
+
+namespace g2 {
+
+g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
+                    const g2_schedule &s, cudaStream_t st, int32_t *d_err);
+g2_status sssp_fused(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
+                     const g2_schedule &s, cudaStream_t st, int32_t *d_err);
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_bfs_init(int32_t *depth, int32_t *parent, int32_t n, int32_t src, int32_t *q,
+                           int32_t *cnt) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        depth[v] = v == src ? 0 : -1;
+        if (parent) parent[v] = v == src ? src : -1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        q[0] = src;
+        *cnt = 1;
+    }
+}
+
+__global__ void k_fill_i32(int32_t *a, int64_t n, int32_t val) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        a[v] = val;
+}
+
+__global__ void k_iota(int32_t *a, int32_t n) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        a[v] = (int32_t)v;
+}
+
+// Pointer jumping: every label is replaced by the root of its chain.  Roots
+// do not change during this kernel (hooking ran before it), so the chase ends.
+__global__ void k_compress(int32_t *label, int32_t n) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t l = label[v];
+        int32_t p = label[l];
+        while (p != l) {
+            l = p;
+            p = label[l];
+        }
+        label[v] = l;
+    }
+}
+
+// list of vertices whose label differs from the round-start snapshot
+__global__ void k_changed(const int32_t *label, const int32_t *lab0, int32_t n, int32_t *q,
+                          int32_t *cnt) {
+    int lane = threadIdx.x & 31;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = base + lane;
+        bool p = v < n && label[v] != lab0[v];
+        warp_append(q, cnt, n, nullptr, (int32_t)v, p);
+    }
+    (void)lane;
+}
+
+// smallest dist among far-pile entries that are not stale (dist >= T)
+__global__ void k_far_min(const int32_t *far, int32_t nfar, const int32_t *dist, int32_t T,
+                          int32_t *out_min) {
+    int32_t best = G2_INF32;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nfar;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t d = dist[far[i]];
+        if (d >= T && d < best) best = d;
+    }
+    best = (int32_t)__reduce_min_sync(G2_FULL, (unsigned)best);
+    if ((threadIdx.x & 31) == 0 && best != G2_INF32) atomicMin(out_min, best);
+}
+
+// split the far pile at the new threshold: stale entries (dist < Told) are
+// dropped, dist < Tnew go to the near list, the rest to the next far pile
+__global__ void k_far_split(const int32_t *far, int32_t nfar, const int32_t *dist, int32_t Told,
+                            int32_t Tnew, int32_t *nearq, int32_t *nearcnt, int32_t *far2,
+                            int32_t *far2cnt, int32_t cap, int32_t *stamp2, int32_t round2,
+                            int32_t *err) {
+    int lane = threadIdx.x & 31;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < nfar;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + lane;
+        int32_t v = 0, d = G2_INF32;
+        bool ok = i < nfar;
+        if (ok) {
+            v = far[i];
+            d = dist[v];
+        }
+        bool to_near = ok && d >= Told && d < Tnew;
+        bool to_far = ok && d >= Tnew;
+        if (to_far) stamp2[v] = round2;
+        warp_append(nearq, nearcnt, cap, err, v, to_near);
+        warp_append(far2, far2cnt, cap, err, v, to_far);
+    }
+    (void)lane;
+}
+
+// BC: max sigma over a level (positive doubles order like their bit patterns)
+__global__ void k_level_max(const int32_t *lvl, int32_t cnt, const double *sigma,
+                            unsigned long long *out) {
+    unsigned long long best = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(sigma[lvl[i]]);
+        if (b > best) best = b;
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        unsigned long long o = __shfl_xor_sync(G2_FULL, best, d);
+        if (o > best) best = o;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
+}
+
+__global__ void k_level_scale(const int32_t *lvl, int32_t cnt, double *sigma, int e) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        sigma[lvl[i]] = ldexp(sigma[lvl[i]], -e);
+}
+
+// Backward (dependency) step of Brandes for the vertices of one level:
+// delta[v] = sigma[v] * sum_{w: v->w, depth[w] = depth[v]+1} (1 + delta[w]) / sigma[w]
+// times 2^(E_d - E_{d+1}) for the per-level scale exponents.
+struct PullBCDelta {
+    const int32_t *depth;
+    const double *sigma;
+    double *delta;
+    double *bc;
+    int32_t src;
+    double ratio;  // 2^(E_d - E_{d+1})
+    typedef int32_t Ctx;
+    typedef double Acc;
+    __device__ __forceinline__ Ctx ctx(int32_t v) const { return depth[v]; }
+    __device__ __forceinline__ bool filter(Ctx) const { return true; }
+    __device__ __forceinline__ Acc identity() const { return 0.0; }
+    __device__ __forceinline__ Acc edge(Ctx dv, int32_t w, int32_t) const {
+        return depth[w] == dv + 1 ? (1.0 + delta[w]) / sigma[w] : 0.0;
+    }
+    __device__ __forceinline__ Acc combine(Acc a, Acc b) const { return a + b; }
+    __device__ __forceinline__ bool stop(Acc) const { return false; }
+    __device__ __forceinline__ int finish(int32_t v, Ctx, Acc a) const {
+        double dv = sigma[v] * a * ratio;
+        delta[v] = dv;
+        if (v != src) bc[v] += dv;
+        return 0;
+    }
+};
+
+template <class P, int G>
+__global__ void __launch_bounds__(kCta) k_pull_list(DevGraph g, const int32_t *cand, int32_t ncand,
+                                                    P op) {
+    OutCtx none;
+    memset(&none, 0, sizeof(none));
+    Member all{MEM_ALL, nullptr, nullptr};
+    lb_pull<P, G>(g, cand, ncand, all, op, none, blockIdx.x, gridDim.x, nullptr);
+}
+
+template <class P>
+static void launch_pull_list(g2_graph *g, int lb, const P &op, const int32_t *cand, int32_t ncand,
+                             cudaStream_t st) {
+    if (ncand <= 0) return;
+    const DevGraph dg = g->topo->view();
+    if (lb == G2_LB_VERTEX_BASED)
+        k_pull_list<P, 1><<<grid_for(g, ncand, kCta), kCta, 0, st>>>(dg, cand, ncand, op);
+    else if (lb == G2_LB_CM)
+        k_pull_list<P, kCta><<<grid_for(g, (int64_t)ncand * kCta, kCta), kCta, 0, st>>>(dg, cand,
+                                                                                        ncand, op);
+    else
+        k_pull_list<P, 32><<<grid_for(g, (int64_t)ncand * 32, kCta), kCta, 0, st>>>(dg, cand, ncand,
+                                                                                   op);
+    stats().launches += 1;
+}
+
+// --------------------------------------------------------------- helpers
+struct Ping {
+    int32_t *q[2];
+    uint32_t *bm[2];
+    uint8_t *bo[2];
+    int32_t qcap;
+};
+
+static g2_status get_ping(g2_graph *g, Ping &p, bool bitmaps, bool boolmaps) {
+    const int32_t n = std::max(g->topo->n, 1);
+    G2_TRY(ws(g, B_Q0, (size_t)n, &p.q[0]));
+    G2_TRY(ws(g, B_Q1, (size_t)n, &p.q[1]));
+    p.qcap = n;
+    p.bm[0] = p.bm[1] = nullptr;
+    p.bo[0] = p.bo[1] = nullptr;
+    size_t words = (size_t)(n + 31) / 32 + 1;
+    if (bitmaps) {
+        G2_TRY(ws(g, B_BM0, words, &p.bm[0]));
+        G2_TRY(ws(g, B_BM1, words, &p.bm[1]));
+    }
+    if (boolmaps) {
+        G2_TRY(ws(g, B_BOOL0, (size_t)n, &p.bo[0]));
+        G2_TRY(ws(g, B_BOOL1, (size_t)n, &p.bo[1]));
+    }
+    return G2_OK;
+}
+
+static bool hybrid_uses(const g2_hybrid &h, int what) {
+    auto uses = [&](const g2_schedule &s) {
+        if (what == 0) return s.direction == G2_PULL || s.frontier_creation != G2_FUSED;
+        return false;
+    };
+    return uses(h.s1) || (h.criteria == G2_INPUT_VERTEXSET_SIZE && uses(h.s2));
+}
+
+static int dedup_of(const g2_schedule &s) {
+    if (s.dedup == G2_DEDUP_DISABLED) return DD_NONE;
+    if (s.dedup_type == G2_DEDUP_BITMAP) return DD_BITMAP;
+    if (s.dedup_type == G2_DEDUP_BOOLMAP) return DD_BOOLMAP;
+    return DD_STAMP;
+}
+
+// One frontier round of a vertex-set loop: brings `cur` (parity p) to the
+// representation the schedule wants, runs the round into parity 1-p with the
+// schedule's frontier creation, and returns the new vertexset with its size.
+static g2_status frontier_round(g2_graph *g, const g2_schedule &s, const OpArgs &a, VSet cur,
+                                int p, const Ping &pp, int32_t *ctrs, int32_t *d_err, VSet &next,
+                                cudaStream_t st) {
+    VSet in = cur;
+    if (cur.rep != -1) {
+        if (s.direction == G2_PUSH && cur.rep != OUT_SPARSE) {
+            VSet t{OUT_SPARSE, pp.q[p], pp.qcap, ctrs + p, nullptr, nullptr, cur.size};
+            G2_TRY(vset_convert(g, cur, OUT_SPARSE, t, st));
+            in = t;
+        } else if (s.direction == G2_PULL) {
+            int want = s.pull_frontier == G2_BITMAP ? OUT_BITMAP : OUT_BOOLMAP;
+            if (cur.rep != want) {
+                VSet t{want, nullptr, 0, nullptr, pp.bm[p], pp.bo[p], cur.size};
+                G2_TRY(vset_convert(g, cur, want, t, st));
+                in = t;
+            }
+        }
+    }
+    const int32_t n = g->topo->n;
+    OutArgs o;
+    memset(&o, 0, sizeof(o));
+    int q = 1 - p;
+    if (s.frontier_creation == G2_FUSED) {
+        o.rep = OUT_SPARSE;
+        o.q = pp.q[q];
+        o.qcap = pp.qcap;
+        o.cnt = ctrs + q;
+        o.dedup = dedup_of(s);
+        G2_CK(cudaMemsetAsync(o.cnt, 0, 4, st));
+        next = VSet{OUT_SPARSE, o.q, o.qcap, o.cnt, nullptr, nullptr, 0};
+    } else if (s.frontier_creation == G2_UNFUSED_BITMAP) {
+        o.rep = OUT_BITMAP;
+        o.bitmap = pp.bm[q];
+        G2_CK(cudaMemsetAsync(o.bitmap, 0, ((size_t)(n + 31) / 32 + 1) * 4, st));
+        next = VSet{OUT_BITMAP, nullptr, 0, nullptr, o.bitmap, nullptr, 0};
+    } else {
+        o.rep = OUT_BOOLMAP;
+        o.boolmap = pp.bo[q];
+        G2_CK(cudaMemsetAsync(o.boolmap, 0, (size_t)std::max(n, 1), st));
+        next = VSet{OUT_BOOLMAP, nullptr, 0, nullptr, nullptr, o.boolmap, 0};
+    }
+    G2_TRY(apply_round(g, s, a, in, o, st));
+    if (s.direction == G2_PUSH) stats().push_rounds++;
+    else stats().pull_rounds++;
+    if (next.rep != OUT_SPARSE) G2_TRY(vset_count(g, next, ctrs + 2, st));
+    G2_TRY(read_counters(g, ctrs, 4, st, d_err));
+    next.size = next.rep == OUT_SPARSE ? g->h_ctr[q] : g->h_ctr[2];
+    return G2_OK;
+}
+
+static g2_status check_src(const g2_graph *g, int32_t src) {
+    if (src < 0 || src >= g->topo->n) return fail(G2_EINVAL, "source vertex out of range");
+    return G2_OK;
+}
+
+// ===================================================================== BFS
+g2_status bfs_plain(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent, const g2_hybrid &h,
+                    cudaStream_t st, int32_t *d_err) {
+    const int32_t n = g->topo->n;
+    Ping pp;
+    G2_TRY(get_ping(g, pp, true, true));
+    int32_t *ctrs = d_err - 62;
+    k_bfs_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(depth, parent, n, src, pp.q[0], ctrs + 0);
+    stats().launches += 1;
+    VSet cur{OUT_SPARSE, pp.q[0], pp.qcap, ctrs + 0, nullptr, nullptr, 1};
+    OpArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kind = K_BFS;
+    a.i0 = depth;
+    a.i1 = parent;
+    a.err = d_err;
+    a.threshold = G2_INF32;
+    int p = 0;
+    while (cur.size > 0) {
+        const g2_schedule &s = pick_schedule(h, cur.size, n);
+        G2_TRY(check_schedule(g, s, K_BFS, false));
+        if (s.load_balance == G2_LB_EDGE_ONLY)
+            return fail(G2_EUNSUPPORTED, "BFS is frontier-driven; EDGE_ONLY is for full sweeps");
+        VSet next;
+        G2_TRY(frontier_round(g, s, a, cur, p, pp, ctrs, d_err, next, st));
+        cur = next;
+        p = 1 - p;
+        stats().iterations++;
+        if (stats().iterations > n + 1) return fail(G2_EOVERFLOW, "BFS did not terminate");
+    }
+    return G2_OK;
+}
+
+// ====================================================================== CC
+g2_status cc_run(g2_graph *g, int32_t *label, const g2_hybrid &h, cudaStream_t st,
+                 int32_t *d_err) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    Ping pp;
+    G2_TRY(get_ping(g, pp, true, true));
+    int32_t *ctrs = d_err - 62;
+    int32_t *lab0;
+    G2_TRY(ws(g, B_I0, (size_t)std::max(n, 1), &lab0));
+    k_iota<<<grid_for(g, n, kCta), kCta, 0, st>>>(label, n);
+    stats().launches += 1;
+    VSet cur{-1, nullptr, 0, nullptr, nullptr, nullptr, n};
+    int p = 0;
+    while (cur.size > 0) {
+        const g2_schedule &s = pick_schedule(h, cur.size, n);
+        G2_TRY(check_schedule(g, s, s.direction == G2_PULL ? K_LABEL : K_HOOK, true));
+        G2_CK(cudaMemcpyAsync(lab0, label, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+        OpArgs a;
+        memset(&a, 0, sizeof(a));
+        a.i0 = label;
+        a.err = d_err;
+        a.threshold = G2_INF32;
+        OutArgs none;
+        memset(&none, 0, sizeof(none));
+        none.rep = OUT_NONE;
+        VSet in = cur;
+        if (s.direction == G2_PUSH) {
+            a.kind = K_HOOK;
+            // an EDGE_ONLY sweep covers every arc, a superset of the active ones
+            if (s.load_balance == G2_LB_EDGE_ONLY) in = VSet{-1, nullptr, 0, nullptr, nullptr, nullptr, n};
+            stats().push_rounds++;
+        } else {
+            a.kind = K_LABEL;
+            if (cur.rep != -1) {
+                int want = s.pull_frontier == G2_BITMAP ? OUT_BITMAP : OUT_BOOLMAP;
+                VSet tt{want, nullptr, 0, nullptr, pp.bm[p], pp.bo[p], cur.size};
+                G2_TRY(vset_convert(g, cur, want, tt, st));
+                in = tt;
+            }
+            stats().pull_rounds++;
+        }
+        G2_TRY(apply_round(g, s, a, in, none, st));
+        k_compress<<<grid_for(g, n, kCta), kCta, 0, st>>>(label, n);
+        int q = 1 - p;
+        G2_CK(cudaMemsetAsync(ctrs + q, 0, 4, st));
+        k_changed<<<grid_for(g, n, kCta), kCta, 0, st>>>(label, lab0, n, pp.q[q], ctrs + q);
+        stats().launches += 2;
+        G2_TRY(read_counters(g, ctrs, 4, st, d_err));
+        cur = VSet{OUT_SPARSE, pp.q[q], pp.qcap, ctrs + q, nullptr, nullptr, g->h_ctr[q]};
+        p = q;
+        stats().iterations++;
+        if (stats().iterations > n + 2) return fail(G2_EOVERFLOW, "CC did not converge");
+    }
+    return G2_OK;
+}
+
+// ==================================================================== SSSP
+g2_status sssp_plain(g2_graph *g, int32_t src, int32_t delta, int32_t *dist, const g2_hybrid &h,
+                     cudaStream_t st, int32_t *d_err) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    Ping pp;
+    G2_TRY(get_ping(g, pp, false, false));
+    int32_t *ctrs = d_err - 62;
+    int32_t *far[2], *stamp2;
+    G2_TRY(ws(g, B_Q2, (size_t)std::max(n, 1), &far[0]));
+    G2_TRY(ws(g, B_Q3, (size_t)std::max(n, 1), &far[1]));
+    G2_TRY(ws(g, B_STAMP2, (size_t)std::max(n, 1), &stamp2));
+    if (g->round2 == 0 || g->round2 > 0x7ffffff0) {
+        G2_CK(cudaMemsetAsync(stamp2, 0, (size_t)std::max(n, 1) * 4, st));
+        g->round2 = 0;
+    }
+    // near lists: capacity n with deduplication; without it one round can
+    // enqueue a vertex once per improving arc, so up to m entries
+    const g2_schedule &s0 = h.s1;
+    int32_t *nq[2] = {pp.q[0], pp.q[1]};
+    int32_t ncap = pp.qcap;
+    if (s0.dedup == G2_DEDUP_DISABLED ||
+        (h.criteria == G2_INPUT_VERTEXSET_SIZE && h.s2.dedup == G2_DEDUP_DISABLED)) {
+        int32_t *big;
+        size_t half = (size_t)t->m + (size_t)n + 1;
+        G2_TRY(ws(g, B_BIG, 2 * half, &big));
+        nq[0] = big;
+        nq[1] = big + half;
+        ncap = (int32_t)std::min<size_t>(half, 2147483647u);
+    }
+    k_fill_i32<<<grid_for(g, n, kCta), kCta, 0, st>>>(dist, n, G2_INF32);
+    int32_t zero = 0, one = 1;
+    G2_CK(cudaMemcpyAsync(dist + src, &zero, 4, cudaMemcpyHostToDevice, st));
+    G2_CK(cudaMemcpyAsync(nq[0], &src, 4, cudaMemcpyHostToDevice, st));
+    G2_CK(cudaMemcpyAsync(ctrs + 0, &one, 4, cudaMemcpyHostToDevice, st));
+    stats().launches += 1;
+    int64_t T = delta;  // bucket 0 = [0, delta)
+    int fp = 0;
+    int32_t round2 = ++g->round2;
+    G2_CK(cudaMemsetAsync(ctrs + 4, 0, 8, st));
+    int32_t near_size = 1, p = 0;
+    for (;;) {
+        while (near_size > 0) {
+            const g2_schedule &s = pick_schedule(h, near_size, n);
+            G2_TRY(check_schedule(g, s, K_RELAX, false));
+            if (s.direction != G2_PUSH || s.load_balance == G2_LB_EDGE_ONLY)
+                return fail(G2_EUNSUPPORTED, "delta-stepping relaxes in the PUSH direction");
+            if (s.frontier_creation != G2_FUSED)
+                return fail(G2_EUNSUPPORTED, "the near/far queue needs FUSED frontier creation");
+            OpArgs a;
+            memset(&a, 0, sizeof(a));
+            a.kind = K_RELAX;
+            a.i0 = dist;
+            a.err = d_err;
+            a.threshold = (int32_t)std::min<int64_t>(T, G2_INF32);
+            OutArgs o;
+            memset(&o, 0, sizeof(o));
+            o.rep = OUT_SPARSE;
+            o.dedup = dedup_of(s);
+            int q = 1 - p;
+            if (o.dedup == DD_NONE && nq[0] == pp.q[0])
+                return fail(G2_EINVAL, "dedup DISABLED must be set on the first schedule too");
+            o.q = nq[q];
+            o.qcap = ncap;
+            o.cnt = ctrs + q;
+            G2_CK(cudaMemsetAsync(o.cnt, 0, 4, st));
+            o.q2 = far[fp];
+            o.q2cap = std::max(n, 1);
+            o.cnt2 = ctrs + 4 + fp;
+            o.stamp2 = stamp2;
+            o.round2 = round2;
+            VSet in{OUT_SPARSE, nq[p], ncap, ctrs + p, nullptr, nullptr, near_size};
+            G2_TRY(apply_round(g, s, a, in, o, st));
+            stats().push_rounds++;
+            G2_TRY(read_counters(g, ctrs, 8, st, d_err));
+            near_size = g->h_ctr[q];
+            p = q;
+            stats().iterations++;
+        }
+        int32_t nfar = g->h_ctr[4 + fp];
+        if (nfar == 0) break;
+        int32_t Told = (int32_t)std::min<int64_t>(T, G2_INF32);
+        int32_t inf = G2_INF32;
+        G2_CK(cudaMemcpyAsync(ctrs + 6, &inf, 4, cudaMemcpyHostToDevice, st));
+        k_far_min<<<grid_for(g, nfar, kCta), kCta, 0, st>>>(far[fp], nfar, dist, Told, ctrs + 6);
+        G2_TRY(read_counters(g, ctrs, 8, st, d_err));
+        int32_t dmin = g->h_ctr[6];
+        if (dmin == G2_INF32) break;
+        int64_t Tnew = ((int64_t)dmin / delta + 1) * (int64_t)delta;
+        int32_t Tn = (int32_t)std::min<int64_t>(Tnew, G2_INF32);
+        int nf = 1 - fp;
+        int32_t round2n = ++g->round2;
+        G2_CK(cudaMemsetAsync(ctrs + p, 0, 4, st));
+        G2_CK(cudaMemsetAsync(ctrs + 4 + nf, 0, 4, st));
+        k_far_split<<<grid_for(g, nfar, kCta), kCta, 0, st>>>(far[fp], nfar, dist, Told, Tn, nq[p],
+                                                             ctrs + p, far[nf], ctrs + 4 + nf,
+                                                             std::max(n, 1), stamp2, round2n, d_err);
+        stats().launches += 2;
+        G2_TRY(read_counters(g, ctrs, 8, st, d_err));
+        near_size = g->h_ctr[p];
+        fp = nf;
+        round2 = round2n;
+        T = Tnew;
+        stats().barriers++;  // buckets advanced
+    }
+    return G2_OK;
+}
+
+// ====================================================================== BC
+g2_status bc_run(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const g2_hybrid &h,
+                 cudaStream_t st, int32_t *d_err) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    int32_t *ctrs = d_err - 62;
+    int32_t *depth, *lvl;
+    double *sigma, *delta;
+    Ping pp;
+    G2_TRY(get_ping(g, pp, true, true));
+    G2_TRY(ws(g, B_I0, (size_t)std::max(n, 1), &depth));
+    G2_TRY(ws(g, B_LVL, (size_t)std::max(n, 1), &lvl));
+    G2_TRY(ws(g, B_D0, (size_t)std::max(n, 1), &sigma));
+    G2_TRY(ws(g, B_D1, (size_t)std::max(n, 1), &delta));
+    unsigned long long *d_max;
+    G2_TRY(ws(g, B_ARCS, 2, &d_max));
+    d_max += 1;  // slot 0 counts arcs; slot 1 holds the level maximum
+    G2_CK(cudaMemsetAsync(bc, 0, (size_t)n * 8, st));
+    std::vector<int32_t> off;
+    std::vector<int> E;
+    for (int32_t i = 0; i < k; ++i) {
+        int32_t s0 = srcs[i];
+        k_bfs_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(depth, nullptr, n, s0, lvl, ctrs + 3);
+        G2_CK(cudaMemsetAsync(sigma, 0, (size_t)n * 8, st));
+        G2_CK(cudaMemsetAsync(delta, 0, (size_t)n * 8, st));
+        double one = 1.0;
+        G2_CK(cudaMemcpyAsync(sigma + s0, &one, 8, cudaMemcpyHostToDevice, st));
+        off.assign(1, 0);
+        off.push_back(1);
+        E.assign(1, 0);
+        // forward: level-synchronous BFS; every level's list is appended to lvl
+        for (int d = 0;; ++d) {
+            int32_t b = off[d], e = off[d + 1];
+            int32_t size = e - b;
+            if (size == 0) break;
+            const g2_schedule &s = pick_schedule(h, size, n);
+            G2_TRY(check_schedule(g, s, K_BFS, false));
+            if (s.load_balance == G2_LB_EDGE_ONLY)
+                return fail(G2_EUNSUPPORTED, "BC's BFS is frontier-driven; EDGE_ONLY is for full sweeps");
+            VSet in{OUT_SPARSE, lvl + b, size, nullptr, nullptr, nullptr, size};
+            if (s.direction == G2_PULL) {
+                int want = s.pull_frontier == G2_BITMAP ? OUT_BITMAP : OUT_BOOLMAP;
+                VSet tt{want, nullptr, 0, nullptr, pp.bm[0], pp.bo[0], size};
+                G2_TRY(vset_convert(g, in, want, tt, st));
+                in = tt;
+            }
+            OpArgs a;
+            memset(&a, 0, sizeof(a));
+            a.kind = K_BFS;
+            a.i0 = depth;
+            a.err = d_err;
+            a.threshold = G2_INF32;
+            OutArgs o;
+            memset(&o, 0, sizeof(o));
+            o.rep = OUT_SPARSE;  // the level lists are needed for the backward pass
+            o.q = lvl + e;
+            o.qcap = n - e;
+            o.cnt = ctrs + 3;
+            o.dedup = DD_NONE;
+            G2_CK(cudaMemsetAsync(o.cnt, 0, 4, st));
+            G2_TRY(apply_round(g, s, a, in, o, st));
+            s.direction == G2_PUSH ? stats().push_rounds++ : stats().pull_rounds++;
+            G2_TRY(read_counters(g, ctrs, 4, st, d_err));
+            int32_t nn = g->h_ctr[3];
+            if (nn == 0) break;
+            // sigma of the new level: sum over in-neighbours one level up
+            PullBCSigma ps{depth, sigma};
+            launch_pull_list(g, s.load_balance, ps, lvl + e, nn, st);
+            // rescale the level by a power of two when its counts grow large
+            G2_CK(cudaMemsetAsync(d_max, 0, 8, st));
+            k_level_max<<<grid_for(g, nn, kCta), kCta, 0, st>>>(lvl + e, nn, sigma, d_max);
+            unsigned long long hm = 0;
+            G2_CK(cudaMemcpyAsync(&hm, d_max, 8, cudaMemcpyDeviceToHost, st));
+            G2_CK(cudaStreamSynchronize(st));
+            double mx;
+            memcpy(&mx, &hm, 8);
+            int ex = 0;
+            if (mx > 0) frexp(mx, &ex);
+            int shift = (ex > 256 || ex < -256) ? ex : 0;
+            if (shift) {
+                k_level_scale<<<grid_for(g, nn, kCta), kCta, 0, st>>>(lvl + e, nn, sigma, shift);
+                stats().launches += 1;
+            }
+            E.push_back(E.back() + shift);
+            off.push_back(e + nn);
+            stats().launches += 2;
+            stats().iterations++;
+        }
+        // backward: deepest level first
+        int D = (int)off.size() - 1;  // number of levels
+        for (int d = D - 2; d >= 0; --d) {
+            int32_t b = off[d], cnt = off[d + 1] - b;
+            const g2_schedule &s = pick_schedule(h, cnt, n);
+            PullBCDelta pd{depth, sigma, delta, bc, s0, ldexp(1.0, E[d] - E[d + 1])};
+            launch_pull_list(g, s.load_balance, pd, lvl + b, cnt, st);
+        }
+        G2_TRY(sync_and_check(g, st, d_err));
+    }
+    return G2_OK;
+}
+
+}  // namespace g2
+
+using namespace g2;
+
+// ====================================================================== C ABI
+extern "C" {
+
+g2_status g2_bfs(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent, const g2_hybrid *sched,
+                 void *stream) {
+    if (!g || !depth) return fail(G2_EINVAL, "null graph or depth");
+    G2_TRY(check_src(g, src));
+    cudaStream_t st = as_stream(stream);
+    g2_hybrid h = sched ? *sched : default_hybrid();
+    int32_t *d_err;
+    G2_TRY(begin_call(g, st, &d_err));
+    if (h.s1.kernel_fusion) {
+        if (h.criteria != G2_CRITERIA_NONE && !h.s2.kernel_fusion)
+            return fail(G2_EUNSUPPORTED, "kernel fusion must be set on both hybrid schedules");
+        G2_TRY(bfs_fused(g, src, depth, parent, h.s1, st, d_err));
+    } else {
+        G2_TRY(bfs_plain(g, src, depth, parent, h, st, d_err));
+    }
+    return end_call(g, st, d_err);
+}
+
+g2_status g2_cc(g2_graph *g, int32_t *label, const g2_hybrid *sched, void *stream) {
+    if (!g || !label) return fail(G2_EINVAL, "null graph or label");
+    if (!g->topo->symmetric) return fail(G2_EINVAL, "connected components need a symmetric graph");
+    cudaStream_t st = as_stream(stream);
+    g2_hybrid h = sched ? *sched : default_hybrid();
+    if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "CC has no fused variant");
+    int32_t *d_err;
+    G2_TRY(begin_call(g, st, &d_err));
+    G2_TRY(cc_run(g, label, h, st, d_err));
+    return end_call(g, st, d_err);
+}
+
+g2_status g2_sssp_delta(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
+                        const g2_hybrid *sched, void *stream) {
+    if (!g || !dist) return fail(G2_EINVAL, "null graph or dist");
+    G2_TRY(check_src(g, src));
+    if (!g->topo->w) return fail(G2_EINVAL, "SSSP needs arc weights");
+    cudaStream_t st = as_stream(stream);
+    g2_hybrid h = sched ? *sched : default_hybrid();
+    if (delta <= 0) delta = h.s1.delta > 0 ? h.s1.delta : 1;
+    int32_t *d_err;
+    G2_TRY(begin_call(g, st, &d_err));
+    if (h.s1.kernel_fusion) {
+        G2_TRY(sssp_fused(g, src, delta, dist, h.s1, st, d_err));
+    } else {
+        G2_TRY(sssp_plain(g, src, delta, dist, h, st, d_err));
+    }
+    return end_call(g, st, d_err);
+}
+
+g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const g2_hybrid *sched,
+                void *stream) {
+    if (!g || !bc || (k > 0 && !srcs) || k < 0) return fail(G2_EINVAL, "bad BC arguments");
+    for (int32_t i = 0; i < k; ++i) G2_TRY(check_src(g, srcs[i]));
+    cudaStream_t st = as_stream(stream);
+    g2_hybrid h = sched ? *sched : default_hybrid();
+    if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "BC has no fused variant yet");
+    int32_t *d_err;
+    G2_TRY(begin_call(g, st, &d_err));
+    G2_TRY(bc_run(g, srcs, k, bc, h, st, d_err));
+    return end_call(g, st, d_err);
+}
+
+}  // extern "C"

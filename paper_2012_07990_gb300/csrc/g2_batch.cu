@@ -1,0 +1,442 @@
+// g2_batch.cu — multi-source traversals: up to 64 BFS sources share one
+// frontier loop with one bit per source in per-vertex 64-bit masks, and up to
+// 32 SSSP sources relax stacked distance arrays together, so the topology is
+// read once per round for all of them.  Both reuse the load-balancing library
+// (PUSH) and its PULL routine with mask-valued update functions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "g2_host.h"
+#include "g2_lb.cuh"
+
+namespace g2 {
+
+typedef unsigned long long u64;
+
+// ------------------------------------------------------- multi-source BFS
+// PUSH: the bits of u's frontier mask not yet visited at v are ORed into v's
+// next mask; the first arc to touch v lists it.
+struct OpMsBfs {
+    const u64 *visit;
+    const u64 *fcur;
+    u64 *fnext;
+    typedef u64 S;
+    __device__ __forceinline__ S load(int32_t u) const { return fcur[u]; }
+    __device__ __forceinline__ bool skip(S m) const { return m == 0; }
+    __device__ __forceinline__ int relax(int32_t, S fm, int32_t v, int32_t) const {
+        u64 m = fm & ~visit[v];
+        if (m == 0) return 0;
+        if ((fnext[v] & m) == m) return 0;
+        u64 old = atomicOr(&fnext[v], m);
+        return old == 0 ? 1 : 0;
+    }
+};
+
+// PULL: v ORs the frontier masks of its in-neighbours, stops once every
+// source has reached it.
+struct PullMsBfs {
+    u64 *visit;
+    const u64 *fcur;
+    u64 *fnext;
+    int32_t *depth;
+    int32_t n;
+    int32_t level;  // depth assigned this round
+    u64 full;
+    typedef u64 Ctx;
+    typedef u64 Acc;
+    __device__ __forceinline__ Ctx ctx(int32_t v) const { return visit[v]; }
+    __device__ __forceinline__ bool filter(Ctx c) const { return c != full; }
+    __device__ __forceinline__ Acc identity() const { return 0ull; }
+    __device__ __forceinline__ Acc edge(Ctx, int32_t u, int32_t) const { return fcur[u]; }
+    __device__ __forceinline__ Acc combine(Acc a, Acc b) const { return a | b; }
+    __device__ __forceinline__ bool stop(Acc a) const { return (a & full) == full; }
+    __device__ __forceinline__ int finish(int32_t v, Ctx c, Acc a) const {
+        u64 nm = a & ~c & full;
+        if (!nm) return 0;
+        fnext[v] = nm;
+        visit[v] = c | nm;
+        while (nm) {
+            int i = __ffsll((long long)nm) - 1;
+            nm &= nm - 1;
+            depth[(int64_t)i * n + v] = level;
+        }
+        return 1;
+    }
+};
+
+// after a PUSH round: newly reached bits become visited, depths written
+__global__ void k_ms_commit(const int32_t *touched, int32_t cnt, u64 *visit, const u64 *fnext,
+                            int32_t *depth, int32_t n, int32_t level) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = touched[i];
+        u64 nm = fnext[v];
+        visit[v] |= nm;
+        while (nm) {
+            int b = __ffsll((long long)nm) - 1;
+            nm &= nm - 1;
+            depth[(int64_t)b * n + v] = level;
+        }
+    }
+}
+
+__global__ void k_ms_clear(const int32_t *list, int32_t cnt, u64 *f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        f[list[i]] = 0ull;
+}
+
+__global__ void k_ms_seed(const int32_t *srcs, int32_t k, u64 *visit, u64 *fcur, int32_t *depth,
+                          int32_t n, int32_t *list, int32_t *cnt) {
+    int i = threadIdx.x;
+    if (i < k) {
+        int32_t s = srcs[i];
+        atomicOr(&visit[s], 1ull << i);
+        u64 old = atomicOr(&fcur[s], 1ull << i);
+        depth[(int64_t)i * n + s] = 0;
+        if (old == 0) list[atomicAdd(cnt, 1)] = s;
+    }
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kCta) k_ms_push(DevGraph g, FrontierIn fin, int32_t fsize, Op op,
+                                                  OutCtx out, int lb, unsigned long long *ctr) {
+    switch (lb) {
+        case G2_LB_WM: lb_warp(g, fin, fsize, op, out, blockIdx.x, gridDim.x, ctr); break;
+        case G2_LB_CM: lb_cta(g, fin, fsize, op, out, blockIdx.x, gridDim.x, ctr); break;
+        case G2_LB_ETWC: lb_etwc(g, fin, fsize, op, out, blockIdx.x, gridDim.x, ctr); break;
+        default: lb_vertex(g, fin, fsize, op, out, blockIdx.x, gridDim.x, ctr); break;
+    }
+}
+
+template <class P, int G>
+__global__ void __launch_bounds__(kCta) k_ms_pull(DevGraph g, P op, OutCtx out,
+                                                  unsigned long long *ctr) {
+    Member all{MEM_ALL, nullptr, nullptr};
+    lb_pull<P, G>(g, nullptr, g.n, all, op, out, blockIdx.x, gridDim.x, ctr);
+}
+
+static g2_status batch_lb(const g2_schedule &s) {
+    switch (s.load_balance) {
+        case G2_LB_VERTEX_BASED: case G2_LB_WM: case G2_LB_CM: case G2_LB_ETWC: return G2_OK;
+        default:
+            return fail(G2_EUNSUPPORTED,
+                        "multi-source traversals support VERTEX_BASED, WM, CM and ETWC");
+    }
+}
+
+g2_status bfs_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
+                        const g2_hybrid &h, cudaStream_t st, int32_t *d_err) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    int32_t *ctrs = d_err - 62;
+    u64 *visit, *F[2];
+    int32_t *list[2], *dsrc;
+    G2_TRY(ws(g, B_MS0, (size_t)std::max(n, 1), &visit));
+    G2_TRY(ws(g, B_MS1, (size_t)std::max(n, 1), &F[0]));
+    G2_TRY(ws(g, B_MS2, (size_t)std::max(n, 1), &F[1]));
+    G2_TRY(ws(g, B_Q0, (size_t)std::max(n, 1), &list[0]));
+    G2_TRY(ws(g, B_Q1, (size_t)std::max(n, 1), &list[1]));
+    G2_TRY(ws(g, B_I1, 64, &dsrc));
+    G2_CK(cudaMemsetAsync(visit, 0, (size_t)n * 8, st));
+    G2_CK(cudaMemsetAsync(F[0], 0, (size_t)n * 8, st));
+    G2_CK(cudaMemsetAsync(F[1], 0, (size_t)n * 8, st));
+    G2_CK(cudaMemsetAsync(depth, 0xFF, (size_t)k * n * 4, st));
+    G2_CK(cudaMemcpyAsync(dsrc, srcs, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    k_ms_seed<<<1, 64, 0, st>>>(dsrc, k, visit, F[0], depth, n, list[0], ctrs + 0);
+    stats().launches += 1;
+    G2_TRY(read_counters(g, ctrs, 4, st, d_err));
+    int32_t size = g->h_ctr[0];
+    const u64 full = k == 64 ? ~0ull : ((1ull << k) - 1);
+    unsigned long long *ctr = nullptr;
+    if (count_arcs_enabled()) G2_TRY(ws(g, B_ARCS, 2, &ctr));
+    const DevGraph dg = t->view();
+    int p = 0;
+    for (int level = 1; size > 0; ++level) {
+        const g2_schedule &s = pick_schedule(h, size, n);
+        G2_TRY(batch_lb(s));
+        int q = 1 - p;
+        OutCtx out;
+        memset(&out, 0, sizeof(out));
+        out.mode = OUT_SPARSE;
+        out.q = list[q];
+        out.cnt = ctrs + q;
+        out.cap = n;
+        out.err = d_err;
+        G2_CK(cudaMemsetAsync(ctrs + q, 0, 4, st));
+        if (s.direction == G2_PUSH) {
+            FrontierIn fin{list[p], size, nullptr};
+            OpMsBfs op{visit, F[p], F[q]};
+            k_ms_push<<<grid_for(g, size, kCta), kCta, 0, st>>>(dg, fin, size, op, out,
+                                                               s.load_balance, ctr);
+            G2_TRY(read_counters(g, ctrs, 4, st, d_err));
+            int32_t nt = g->h_ctr[q];
+            if (nt > 0)
+                k_ms_commit<<<grid_for(g, nt, kCta), kCta, 0, st>>>(list[q], nt, visit, F[q], depth,
+                                                                   n, level);
+            stats().push_rounds++;
+            stats().launches += 2;
+        } else {
+            PullMsBfs op{visit, F[p], F[q], depth, n, level, full};
+            if (s.load_balance == G2_LB_WM)
+                k_ms_pull<PullMsBfs, 32><<<grid_for(g, (int64_t)n * 32, kCta), kCta, 0, st>>>(
+                    dg, op, out, ctr);
+            else
+                k_ms_pull<PullMsBfs, 1><<<grid_for(g, n, kCta), kCta, 0, st>>>(dg, op, out, ctr);
+            stats().pull_rounds++;
+            stats().launches += 1;
+        }
+        // the current frontier masks become the (all-zero) next-next array
+        k_ms_clear<<<grid_for(g, size, kCta), kCta, 0, st>>>(list[p], size, F[p]);
+        stats().launches += 1;
+        G2_TRY(read_counters(g, ctrs, 4, st, d_err));
+        size = g->h_ctr[q];
+        p = q;
+        stats().iterations++;
+    }
+    return G2_OK;
+}
+
+// ------------------------------------------------------ multi-source SSSP
+// Masks: M[p][v] = sources whose dist at v improved below the bucket
+// threshold and wait to be relaxed; Far[v] = sources improved to a value at
+// or above it.  Lists hold each vertex once (the first arc that turns its
+// mask non-zero lists it).
+struct OpMsRelax {
+    int32_t *dist;  // [k][n]
+    const int32_t *w;
+    const unsigned *mcur;
+    unsigned *mnext;
+    unsigned *far;
+    int32_t n;
+    int32_t T;
+    int32_t *err;
+    typedef unsigned S;
+    __device__ __forceinline__ S load(int32_t u) const { return mcur[u]; }
+    __device__ __forceinline__ bool skip(S m) const { return m == 0; }
+    __device__ __forceinline__ int relax(int32_t u, S mu, int32_t v, int32_t e) const {
+        const int32_t wt = w[e];
+        unsigned nb = 0, fb = 0;
+        while (mu) {
+            int i = __ffs(mu) - 1;
+            mu &= mu - 1;
+            int32_t du = dist[(int64_t)i * n + u];
+            int64_t nd = (int64_t)du + wt;
+            if (nd >= G2_INF32) {
+                set_error(err, G2_EOVERFLOW);
+                continue;
+            }
+            int32_t *dv = dist + (int64_t)i * n + v;
+            if ((int32_t)nd < *dv) {
+                int32_t old = atomicMin(dv, (int32_t)nd);
+                if ((int32_t)nd < old) {
+                    if ((int32_t)nd < T) nb |= 1u << i;
+                    else fb |= 1u << i;
+                }
+            }
+        }
+        int code = 0;
+        if (nb && atomicOr(&mnext[v], nb) == 0) code |= 1;
+        if (fb && atomicOr(&far[v], fb) == 0) code |= 2;
+        return code;
+    }
+};
+
+__global__ void k_msr_far_min(const int32_t *flist, int32_t cnt, const unsigned *far,
+                              const int32_t *dist, int32_t n, int32_t Told, int32_t *out) {
+    int32_t best = G2_INF32;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = flist[i];
+        unsigned m = far[v];
+        while (m) {
+            int b = __ffs(m) - 1;
+            m &= m - 1;
+            int32_t d = dist[(int64_t)b * n + v];
+            if (d >= Told && d < best) best = d;
+        }
+    }
+    best = (int32_t)__reduce_min_sync(G2_FULL, (unsigned)best);
+    if ((threadIdx.x & 31) == 0 && best != G2_INF32) atomicMin(out, best);
+}
+
+__global__ void k_msr_far_split(const int32_t *flist, int32_t cnt, unsigned *far,
+                                const int32_t *dist, int32_t n, int32_t Told, int32_t Tnew,
+                                unsigned *mnear, int32_t *nlist, int32_t *ncnt, int32_t *flist2,
+                                int32_t *fcnt2, int32_t *err) {
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < cnt;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + (threadIdx.x & 31);
+        int32_t v = 0;
+        unsigned nb = 0, fb = 0;
+        if (i < cnt) {
+            v = flist[i];
+            unsigned m = far[v];
+            while (m) {
+                int b = __ffs(m) - 1;
+                m &= m - 1;
+                int32_t d = dist[(int64_t)b * n + v];
+                if (d < Told) continue;  // settled in an earlier bucket
+                if (d < Tnew) nb |= 1u << b;
+                else fb |= 1u << b;
+            }
+            far[v] = fb;
+            if (nb) mnear[v] = nb;
+        }
+        warp_append(nlist, ncnt, n, err, v, nb != 0);
+        warp_append(flist2, fcnt2, n, err, v, fb != 0);
+    }
+}
+
+__global__ void k_msr_seed(const int32_t *srcs, int32_t k, int32_t *dist, int32_t n, unsigned *m,
+                           int32_t *list, int32_t *cnt) {
+    int i = threadIdx.x;
+    if (i < k) {
+        int32_t s = srcs[i];
+        dist[(int64_t)i * n + s] = 0;
+        if (atomicOr(&m[s], 1u << i) == 0) list[atomicAdd(cnt, 1)] = s;
+    }
+}
+
+__global__ void k_msr_clear(const int32_t *list, int32_t cnt, unsigned *m) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m[list[i]] = 0u;
+}
+
+__global__ void k_fill_i32_b(int32_t *a, int64_t n, int32_t val) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        a[v] = val;
+}
+
+g2_status sssp_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t delta, int32_t *dist,
+                         const g2_hybrid &h, cudaStream_t st, int32_t *d_err) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    int32_t *ctrs = d_err - 62;
+    unsigned *M[2], *far;
+    int32_t *nl[2], *fl[2], *dsrc;
+    G2_TRY(ws(g, B_F0, (size_t)std::max(n, 1), &M[0]));
+    G2_TRY(ws(g, B_F1, (size_t)std::max(n, 1), &M[1]));
+    G2_TRY(ws(g, B_F2, (size_t)std::max(n, 1), &far));
+    G2_TRY(ws(g, B_Q0, (size_t)std::max(n, 1), &nl[0]));
+    G2_TRY(ws(g, B_Q1, (size_t)std::max(n, 1), &nl[1]));
+    G2_TRY(ws(g, B_Q2, (size_t)std::max(n, 1), &fl[0]));
+    G2_TRY(ws(g, B_Q3, (size_t)std::max(n, 1), &fl[1]));
+    G2_TRY(ws(g, B_I1, 64, &dsrc));
+    G2_CK(cudaMemsetAsync(M[0], 0, (size_t)n * 4, st));
+    G2_CK(cudaMemsetAsync(M[1], 0, (size_t)n * 4, st));
+    G2_CK(cudaMemsetAsync(far, 0, (size_t)n * 4, st));
+    k_fill_i32_b<<<grid_for(g, (int64_t)k * n, kCta), kCta, 0, st>>>(dist, (int64_t)k * n, G2_INF32);
+    G2_CK(cudaMemcpyAsync(dsrc, srcs, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    k_msr_seed<<<1, 32, 0, st>>>(dsrc, k, dist, n, M[0], nl[0], ctrs + 0);
+    stats().launches += 2;
+    G2_TRY(read_counters(g, ctrs, 8, st, d_err));
+    int32_t size = g->h_ctr[0];
+    unsigned long long *ctr = nullptr;
+    if (count_arcs_enabled()) G2_TRY(ws(g, B_ARCS, 2, &ctr));
+    const DevGraph dg = t->view();
+    const bool bucketed = delta > 0;
+    int64_t T = bucketed ? delta : (int64_t)G2_INF32;
+    int p = 0, fp = 0;
+    G2_CK(cudaMemsetAsync(ctrs + 4, 0, 8, st));
+    for (;;) {
+        while (size > 0) {
+            const g2_schedule &s = pick_schedule(h, size, n);
+            G2_TRY(batch_lb(s));
+            if (s.direction != G2_PUSH)
+                return fail(G2_EUNSUPPORTED, "multi-source SSSP relaxes in the PUSH direction");
+            int q = 1 - p;
+            OutCtx out;
+            memset(&out, 0, sizeof(out));
+            out.mode = OUT_SPARSE;
+            out.q = nl[q];
+            out.cnt = ctrs + q;
+            out.cap = n;
+            out.q2 = fl[fp];
+            out.cnt2 = ctrs + 4 + fp;
+            out.cap2 = n;
+            out.err = d_err;
+            G2_CK(cudaMemsetAsync(ctrs + q, 0, 4, st));
+            FrontierIn fin{nl[p], size, nullptr};
+            OpMsRelax op{dist, t->w, M[p], M[q], far, n, (int32_t)std::min<int64_t>(T, G2_INF32),
+                         d_err};
+            k_ms_push<<<grid_for(g, size, kCta), kCta, 0, st>>>(dg, fin, size, op, out,
+                                                               s.load_balance, ctr);
+            k_msr_clear<<<grid_for(g, size, kCta), kCta, 0, st>>>(nl[p], size, M[p]);
+            stats().launches += 2;
+            stats().push_rounds++;
+            stats().iterations++;
+            G2_TRY(read_counters(g, ctrs, 8, st, d_err));
+            size = g->h_ctr[q];
+            p = q;
+        }
+        int32_t nfar = g->h_ctr[4 + fp];
+        if (!bucketed || nfar == 0) break;
+        int32_t Told = (int32_t)std::min<int64_t>(T, G2_INF32);
+        int32_t inf = G2_INF32;
+        G2_CK(cudaMemcpyAsync(ctrs + 6, &inf, 4, cudaMemcpyHostToDevice, st));
+        k_msr_far_min<<<grid_for(g, nfar, kCta), kCta, 0, st>>>(fl[fp], nfar, far, dist, n, Told,
+                                                               ctrs + 6);
+        G2_TRY(read_counters(g, ctrs, 8, st, d_err));
+        int32_t dmin = g->h_ctr[6];
+        if (dmin == G2_INF32) break;
+        int64_t Tnew = ((int64_t)dmin / delta + 1) * (int64_t)delta;
+        int nf = 1 - fp;
+        G2_CK(cudaMemsetAsync(ctrs + p, 0, 4, st));
+        G2_CK(cudaMemsetAsync(ctrs + 4 + nf, 0, 4, st));
+        k_msr_far_split<<<grid_for(g, nfar, kCta), kCta, 0, st>>>(
+            fl[fp], nfar, far, dist, n, Told, (int32_t)std::min<int64_t>(Tnew, G2_INF32), M[p],
+            nl[p], ctrs + p, fl[nf], ctrs + 4 + nf, d_err);
+        stats().launches += 2;
+        G2_TRY(read_counters(g, ctrs, 8, st, d_err));
+        size = g->h_ctr[p];
+        fp = nf;
+        T = Tnew;
+        stats().barriers++;
+    }
+    return G2_OK;
+}
+
+}  // namespace g2
+
+using namespace g2;
+
+extern "C" {
+
+g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
+                       const g2_hybrid *sched, void *stream) {
+    if (!g || !depth || !srcs || k < 1 || k > 64) return fail(G2_EINVAL, "need 1 <= k <= 64 sources");
+    for (int32_t i = 0; i < k; ++i)
+        if (srcs[i] < 0 || srcs[i] >= g->topo->n) return fail(G2_EINVAL, "source out of range");
+    if ((int64_t)k * g->topo->n >= (int64_t)1 << 40) return fail(G2_EINVAL, "output too large");
+    cudaStream_t st = as_stream(stream);
+    g2_hybrid h = sched ? *sched : default_hybrid();
+    if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "batched BFS runs unfused rounds");
+    int32_t *d_err;
+    G2_TRY(begin_call(g, st, &d_err));
+    G2_TRY(bfs_batch_run(g, srcs, k, depth, h, st, d_err));
+    return end_call(g, st, d_err);
+}
+
+g2_status g2_sssp_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t delta, int32_t *dist,
+                        const g2_hybrid *sched, void *stream) {
+    if (!g || !dist || !srcs || k < 1 || k > 32) return fail(G2_EINVAL, "need 1 <= k <= 32 sources");
+    if (!g->topo->w) return fail(G2_EINVAL, "SSSP needs arc weights");
+    for (int32_t i = 0; i < k; ++i)
+        if (srcs[i] < 0 || srcs[i] >= g->topo->n) return fail(G2_EINVAL, "source out of range");
+    cudaStream_t st = as_stream(stream);
+    g2_hybrid h = sched ? *sched : default_hybrid();
+    if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "batched SSSP runs unfused rounds");
+    if (delta <= 0 && h.s1.delta > 0) delta = h.s1.delta;
+    int32_t *d_err;
+    G2_TRY(begin_call(g, st, &d_err));
+    G2_TRY(sssp_batch_run(g, srcs, k, delta, dist, h, st, d_err));
+    return end_call(g, st, d_err);
+}
+
+}  // extern "C"

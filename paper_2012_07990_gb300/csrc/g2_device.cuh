@@ -1,0 +1,478 @@
+// g2_device.cuh — device-side building blocks of the traversal kernels:
+// graph view, input/output vertexsets, warp-aggregated enqueue with the three
+// deduplication strategies, the update functions (UDFs) with the atomics the
+// paper's dependence analysis inserts (Sec. VI-B), and a grid barrier whose
+// wait is bounded in time.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "g2.h"
+
+#define G2_FULL 0xffffffffu
+#define G2_INF32 2147483647
+
+namespace g2 {
+
+constexpr int kCta = 256;        // threads per CTA in the traversal kernels
+constexpr int kWarps = kCta / 32;
+
+// ----------------------------------------------------------------- graph view
+struct DevGraph {
+    int32_t n;
+    int32_t m;
+    const int32_t *rowptr;   // CSR, int32[n+1]
+    const int32_t *col;      // int32[m], lists ascending
+    const int32_t *w;        // int32[m] or null
+    const int32_t *crowptr;  // CSC (aliases CSR on symmetric graphs)
+    const int32_t *ccol;
+    const int32_t *cw;
+};
+
+// ----------------------------------------------------------- input vertexset
+// A sparse list (q != null) or all vertices (q == null, item i is vertex i).
+struct FrontierIn {
+    const int32_t *q;
+    int32_t size;             // used when size_ptr == null
+    const int32_t *size_ptr;  // device-resident count (written by an earlier kernel)
+    __device__ __forceinline__ int32_t count() const { return size_ptr ? *size_ptr : size; }
+    __device__ __forceinline__ int32_t vertex(int32_t i) const { return q ? q[i] : i; }
+};
+
+// Membership test of the PULL direction's input frontier.
+enum { MEM_ALL = 0, MEM_BITMAP = 1, MEM_BOOLMAP = 2 };
+struct Member {
+    int kind;
+    const uint32_t *bitmap;
+    const uint8_t *boolmap;
+    __device__ __forceinline__ bool has(int32_t u) const {
+        if (kind == MEM_BITMAP) return (bitmap[u >> 5] >> (u & 31)) & 1u;
+        if (kind == MEM_BOOLMAP) return boolmap[u] != 0;
+        return true;
+    }
+};
+
+// ---------------------------------------------------------- output vertexset
+enum { OUT_NONE = 0, OUT_SPARSE = 1, OUT_BITMAP = 2, OUT_BOOLMAP = 3 };
+enum { DD_NONE = 0, DD_STAMP = 1, DD_BITMAP = 2, DD_BOOLMAP = 3 };
+
+struct OutCtx {
+    int mode;
+    int dedup;
+    int32_t *q;          // OUT_SPARSE list
+    int32_t *cnt;        // its length counter
+    int32_t cap;         // capacity of q
+    uint32_t *bitmap;    // OUT_BITMAP
+    uint8_t *boolmap;    // OUT_BOOLMAP
+    int32_t *stamp;      // DD_STAMP: per-vertex last-enqueue round (monotonic counter)
+    int32_t round;       // the current round's stamp
+    uint32_t *dd_bitmap;  // DD_BITMAP (cleared before the round)
+    uint8_t *dd_boolmap;  // DD_BOOLMAP (cleared before the round)
+    // secondary sparse output (the far pile of the two-bucket priority queue)
+    int32_t *q2;
+    int32_t *cnt2;
+    int32_t cap2;
+    int32_t *stamp2;
+    int32_t round2;
+    int32_t *err;
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void set_error(int32_t *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// Claim v for the output list under the configured deduplication.
+__device__ __forceinline__ bool dedup_claim(const OutCtx &o, int32_t v) {
+    switch (o.dedup) {
+        case DD_STAMP: return atomicExch(&o.stamp[v], o.round) != o.round;
+        case DD_BITMAP: {
+            uint32_t bit = 1u << (v & 31);
+            return !(atomicOr(&o.dd_bitmap[v >> 5], bit) & bit);
+        }
+        case DD_BOOLMAP: {
+            // byte flag, test-then-set: a race may let a duplicate through,
+            // which costs work but not correctness for these updates
+            if (o.dd_boolmap[v]) return false;
+            o.dd_boolmap[v] = 1;
+            return true;
+        }
+        default: return true;
+    }
+}
+
+// Warp-aggregated append of the lanes with `pred` to list q: one atomic per
+// warp.  Must be called by all 32 lanes of the warp.
+__device__ __forceinline__ void warp_append(int32_t *q, int32_t *cnt, int32_t cap, int32_t *err,
+                                            int32_t v, bool pred) {
+    unsigned mask = __ballot_sync(G2_FULL, pred);
+    if (mask == 0) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(mask));
+    base = __shfl_sync(G2_FULL, base, leader);
+    if (pred) {
+        int pos = base + __popc(mask & lanemask_lt());
+        if (pos < cap) q[pos] = v;
+        else set_error(err, G2_EOVERFLOW);
+    }
+}
+
+// Emit destination v; code is a bit set: bit 0 = primary output, bit 1 =
+// secondary (far) output.  Called by all 32 lanes.
+__device__ __forceinline__ void emit(const OutCtx &o, int32_t v, int code) {
+    if (o.mode == OUT_SPARSE) {
+        bool p = code & 1;
+        if (p && o.dedup != DD_NONE) p = dedup_claim(o, v);
+        warp_append(o.q, o.cnt, o.cap, o.err, v, p);
+        if (o.q2) {
+            bool p2 = code & 2;
+            if (p2 && o.stamp2) p2 = atomicExch(&o.stamp2[v], o.round2) != o.round2;
+            warp_append(o.q2, o.cnt2, o.cap2, o.err, v, p2);
+        }
+    } else if (o.mode == OUT_BITMAP) {
+        if (code & 1) atomicOr(&o.bitmap[v >> 5], 1u << (v & 31));
+    } else if (o.mode == OUT_BOOLMAP) {
+        if (code & 1) o.boolmap[v] = 1;
+    }
+}
+
+// ------------------------------------------------------------ update functions
+// Push-side interface: load(u) gives the per-source value carried to every
+// arc of u; skip(s) drops the source; relax(u, s, v, e) applies the update to
+// arc e = u->v and returns the emit code.
+
+struct OpBFS {
+    int32_t *depth;
+    int32_t *parent;  // may be null
+    typedef int32_t S;
+    __device__ __forceinline__ S load(int32_t u) const { return depth[u]; }
+    __device__ __forceinline__ bool skip(S du) const { return du < 0; }
+    __device__ __forceinline__ int relax(int32_t u, S du, int32_t v, int32_t) const {
+        int32_t dv = depth[v];
+        if (dv == -1) {
+            dv = atomicCAS(&depth[v], -1, du + 1);
+            if (dv == -1) {
+                if (parent) atomicMin(reinterpret_cast<unsigned *>(&parent[v]), (unsigned)u);
+                return 1;
+            }
+        }
+        // v reached in this round by another arc: keep the smallest parent
+        if (parent && dv == du + 1) atomicMin(reinterpret_cast<unsigned *>(&parent[v]), (unsigned)u);
+        return 0;
+    }
+};
+
+struct OpRelaxMin {
+    int32_t *dist;
+    const int32_t *w;
+    int32_t *err;
+    int32_t threshold;  // emit 1 if the new value < threshold, else 2 (far)
+    typedef int32_t S;
+    __device__ __forceinline__ S load(int32_t u) const { return dist[u]; }
+    __device__ __forceinline__ bool skip(S du) const { return du == G2_INF32; }
+    __device__ __forceinline__ int relax(int32_t, S du, int32_t v, int32_t e) const {
+        int64_t nd = (int64_t)du + (int64_t)w[e];
+        if (nd >= G2_INF32) {
+            set_error(err, G2_EOVERFLOW);
+            return 0;
+        }
+        int32_t nv = (int32_t)nd;
+        if (nv < dist[v]) {
+            int32_t old = atomicMin(&dist[v], nv);
+            if (nv < old) return nv < threshold ? 1 : 2;
+        }
+        return 0;
+    }
+};
+
+struct OpLabelMin {
+    int32_t *label;
+    typedef int32_t S;
+    __device__ __forceinline__ S load(int32_t u) const { return label[u]; }
+    __device__ __forceinline__ bool skip(S) const { return false; }
+    __device__ __forceinline__ int relax(int32_t, S lu, int32_t v, int32_t) const {
+        if (lu < label[v]) {
+            int32_t old = atomicMin(&label[v], lu);
+            return lu < old ? 1 : 0;
+        }
+        return 0;
+    }
+};
+
+// Hooking step of the Soman et al. connected components: along arc u->v with
+// labels a = label[u], b = label[v], a != b, lower label[max(a,b)] to
+// min(a,b).  Labels are vertex ids of the same component, never above their
+// own vertex, so repeated hooking + pointer jumping ends at the minimum id.
+struct OpHook {
+    int32_t *label;
+    typedef int32_t S;
+    __device__ __forceinline__ S load(int32_t u) const { return label[u]; }
+    __device__ __forceinline__ bool skip(S) const { return false; }
+    __device__ __forceinline__ int relax(int32_t, S a, int32_t v, int32_t) const {
+        int32_t b = label[v];
+        if (a != b) {
+            int32_t hi = a > b ? a : b, lo = a > b ? b : a;
+            if (lo < label[hi]) atomicMin(&label[hi], lo);
+        }
+        return 0;
+    }
+};
+
+struct OpPRAdd {
+    const float *contrib;
+    float *acc;
+    typedef float S;
+    __device__ __forceinline__ S load(int32_t u) const { return contrib[u]; }
+    __device__ __forceinline__ bool skip(S) const { return false; }
+    __device__ __forceinline__ int relax(int32_t, S c, int32_t v, int32_t) const {
+        atomicAdd(&acc[v], c);
+        return 0;
+    }
+};
+
+struct OpBCSigma {
+    const int32_t *depth;
+    double *sigma;
+    typedef int32_t S;
+    __device__ __forceinline__ S load(int32_t u) const { return depth[u]; }
+    __device__ __forceinline__ bool skip(S du) const { return du < 0; }
+    __device__ __forceinline__ int relax(int32_t u, S du, int32_t v, int32_t) const {
+        if (depth[v] == du + 1) atomicAdd(&sigma[v], sigma[u]);
+        return 0;
+    }
+};
+
+// Pull-side interface: ctx(v) loads what the destination needs; filter(c)
+// selects destinations; edge(c, u, e) is the contribution of in-neighbour u
+// (already known to be in the input frontier); combine is associative;
+// stop(acc) allows an early exit; finish(v, c, acc) writes and returns the
+// emit code.
+
+struct PullBFS {
+    int32_t *depth;
+    int32_t *parent;
+    typedef int32_t Ctx;
+    typedef int32_t Acc;  // smallest in-frontier in-neighbour seen
+    __device__ __forceinline__ Ctx ctx(int32_t v) const { return depth[v]; }
+    __device__ __forceinline__ bool filter(Ctx dv) const { return dv == -1; }
+    __device__ __forceinline__ Acc identity() const { return G2_INF32; }
+    __device__ __forceinline__ Acc edge(Ctx, int32_t u, int32_t) const { return u; }
+    __device__ __forceinline__ Acc combine(Acc a, Acc b) const { return a < b ? a : b; }
+    __device__ __forceinline__ bool stop(Acc a) const { return a != G2_INF32; }
+    __device__ __forceinline__ int finish(int32_t v, Ctx, Acc a) const {
+        if (a == G2_INF32) return 0;
+        depth[v] = depth[a] + 1;
+        if (parent) parent[v] = a;
+        return 1;
+    }
+};
+
+struct PullRelaxMin {
+    int32_t *dist;
+    const int32_t *cw;
+    int32_t *err;
+    typedef int32_t Ctx;
+    typedef int32_t Acc;
+    __device__ __forceinline__ Ctx ctx(int32_t v) const { return dist[v]; }
+    __device__ __forceinline__ bool filter(Ctx) const { return true; }
+    __device__ __forceinline__ Acc identity() const { return G2_INF32; }
+    __device__ __forceinline__ Acc edge(Ctx, int32_t u, int32_t e) const {
+        int32_t du = dist[u];
+        if (du == G2_INF32) return G2_INF32;
+        int64_t nd = (int64_t)du + cw[e];
+        if (nd >= G2_INF32) {
+            set_error(err, G2_EOVERFLOW);
+            return G2_INF32;
+        }
+        return (int32_t)nd;
+    }
+    __device__ __forceinline__ Acc combine(Acc a, Acc b) const { return a < b ? a : b; }
+    __device__ __forceinline__ bool stop(Acc) const { return false; }
+    __device__ __forceinline__ int finish(int32_t v, Ctx dv, Acc a) const {
+        if (a < dv) {
+            dist[v] = a;
+            return 1;
+        }
+        return 0;
+    }
+};
+
+struct PullLabelMin {
+    int32_t *label;
+    typedef int32_t Ctx;
+    typedef int32_t Acc;
+    __device__ __forceinline__ Ctx ctx(int32_t v) const { return label[v]; }
+    __device__ __forceinline__ bool filter(Ctx) const { return true; }
+    __device__ __forceinline__ Acc identity() const { return G2_INF32; }
+    __device__ __forceinline__ Acc edge(Ctx, int32_t u, int32_t) const { return label[u]; }
+    __device__ __forceinline__ Acc combine(Acc a, Acc b) const { return a < b ? a : b; }
+    __device__ __forceinline__ bool stop(Acc) const { return false; }
+    __device__ __forceinline__ int finish(int32_t v, Ctx lv, Acc a) const {
+        if (a < lv) {
+            label[v] = a;
+            return 1;
+        }
+        return 0;
+    }
+};
+
+struct PullPRAdd {
+    const float *contrib;
+    float *acc;
+    typedef int32_t Ctx;
+    typedef float Acc;
+    __device__ __forceinline__ Ctx ctx(int32_t) const { return 0; }
+    __device__ __forceinline__ bool filter(Ctx) const { return true; }
+    __device__ __forceinline__ Acc identity() const { return 0.f; }
+    __device__ __forceinline__ Acc edge(Ctx, int32_t u, int32_t) const { return contrib[u]; }
+    __device__ __forceinline__ Acc combine(Acc a, Acc b) const { return a + b; }
+    __device__ __forceinline__ bool stop(Acc) const { return false; }
+    __device__ __forceinline__ int finish(int32_t v, Ctx, Acc a) const {
+        acc[v] += a;
+        return 0;
+    }
+};
+
+struct PullBCSigma {
+    const int32_t *depth;
+    double *sigma;
+    typedef int32_t Ctx;
+    typedef double Acc;
+    __device__ __forceinline__ Ctx ctx(int32_t v) const { return depth[v]; }
+    __device__ __forceinline__ bool filter(Ctx dv) const { return dv > 0; }
+    __device__ __forceinline__ Acc identity() const { return 0.0; }
+    __device__ __forceinline__ Acc edge(Ctx dv, int32_t u, int32_t) const {
+        return depth[u] == dv - 1 ? sigma[u] : 0.0;
+    }
+    __device__ __forceinline__ Acc combine(Acc a, Acc b) const { return a + b; }
+    __device__ __forceinline__ bool stop(Acc) const { return false; }
+    __device__ __forceinline__ int finish(int32_t v, Ctx, Acc a) const {
+        sigma[v] += a;
+        return 0;
+    }
+};
+
+// ----------------------------------------------------------- warp/block utils
+template <class T>
+__device__ __forceinline__ T shfl(T x, int src) {
+    return __shfl_sync(G2_FULL, x, src);
+}
+
+// inclusive warp scan of an int
+__device__ __forceinline__ int warp_incl_scan(int x) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int t = __shfl_up_sync(G2_FULL, x, d);
+        if (lane >= d) x += t;
+    }
+    return x;
+}
+
+// inclusive block scan over kCta threads; returns this thread's inclusive sum
+// and writes the block total to *total.  smem: kWarps ints.
+__device__ __forceinline__ int block_incl_scan(int x, int *s_warp, int *total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = warp_incl_scan(x);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int v = lane < kWarps ? s_warp[lane] : 0;
+        v = warp_incl_scan(v);
+        if (lane < kWarps) s_warp[lane] = v;
+    }
+    __syncthreads();
+    int off = wid ? s_warp[wid - 1] : 0;
+    *total = s_warp[kWarps - 1];
+    return incl + off;
+}
+
+// Per-warp count of examined arcs into a 64-bit device counter (stats mode).
+__device__ __forceinline__ void count_arcs(unsigned long long *ctr, int k) {
+    if (!ctr) return;
+    unsigned s = __reduce_add_sync(G2_FULL, (unsigned)k);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
+}
+
+// ------------------------------------------------------------- grid barrier
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+struct GridBarrier {
+    unsigned *count;  // zero before the launch
+    unsigned *gen;
+};
+
+// Wait until *flag != 0 or limit_ns has passed.  Returns true if the flag was
+// seen.  Only the calling thread waits.
+__device__ __forceinline__ bool bounded_wait_flag(const unsigned *flag, uint64_t limit_ns) {
+    uint64_t t0 = globaltimer_ns();
+    while (ld_acquire(flag) == 0u) {
+        __nanosleep(100);
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// Barrier across all CTAs of a cooperative launch.  The wait is bounded: a
+// CTA that waits longer than limit_ns records G2_ETIMEOUT in *err and every
+// CTA returns false (callers then leave the kernel).  A CTA also stops
+// waiting once another CTA has recorded an error.
+__device__ __forceinline__ bool grid_sync(const GridBarrier &b, int32_t *err, uint64_t limit_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned g0 = ld_acquire(b.gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(b.count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(b.count, 0u);
+            __threadfence();
+            atomicAdd(b.gen, 1u);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            while (ld_acquire(b.gen) == g0) {
+                __nanosleep(32);
+                if (ld_relaxed_i32(err) != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > limit_ns) {
+                    atomicCAS(err, 0, G2_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (ld_relaxed_i32(err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace g2

@@ -1,0 +1,204 @@
+// g2_host.h — host-side internals of libg2: the graph handle, its device
+// workspace, error and statistics plumbing, and the internal launchers shared
+// by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "g2.h"
+#include "g2_device.cuh"
+
+namespace g2 {
+
+// ------------------------------------------------------------ errors, stats
+void set_error_msg(const std::string &msg);
+g2_status fail(g2_status st, const std::string &msg);
+g2_status cuda_fail(cudaError_t e, const char *what);
+g2_stats &stats();           // thread-local stats of the current call
+bool count_arcs_enabled();   // thread-local
+
+#define G2_CK(call)                                          \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return ::g2::cuda_fail(e_, #call); \
+    } while (0)
+
+#define G2_TRY(expr)                    \
+    do {                                \
+        g2_status s_ = (expr);          \
+        if (s_ != G2_OK) return s_;     \
+    } while (0)
+
+// --------------------------------------------------------------- workspace
+// Named device buffers owned by a graph handle, allocated on first use and
+// reused by every later call (the frontier reuse the paper's liveness analysis
+// enables, Sec. VI-A: no cudaMalloc/cudaFree inside the iteration loops).
+enum Buf {
+    B_Q0, B_Q1, B_Q2, B_Q3,        // sparse queues (capacity n, or m when dedup is off)
+    B_BM0, B_BM1,                  // bitmaps
+    B_BOOL0, B_BOOL1,              // boolmaps
+    B_STAMP, B_STAMP2,             // monotonic-counter dedup stamps
+    B_DDBM, B_DDBOOL,              // bitmap / boolmap dedup flags
+    B_SCAN, B_SCANTMP,             // STRICT prefix sums, scan partials
+    B_TWC_S, B_TWC_M, B_TWC_L,     // TWC buckets
+    B_CTR,                         // small device counters (int32[64])
+    B_ARCS,                        // 64-bit arc counter
+    B_F0, B_F1, B_F2,              // float/int scratch arrays of n (PR, CC)
+    B_D0, B_D1,                    // double arrays of n (BC)
+    B_LVL,                         // BC level queue (int32[n])
+    B_I0, B_I1,                    // int32 arrays of n
+    B_BIG,                         // dedup-disabled overflow queue (capacity m + n)
+    B_MS0, B_MS1, B_MS2,           // multi-source masks (uint64[n])
+    B_COUNT
+};
+
+struct Topology;  // shared by views (reference counted)
+
+}  // namespace g2
+
+struct g2_graph {
+    g2::Topology *topo;
+    void *buf[g2::B_COUNT];
+    size_t cap[g2::B_COUNT];
+    int32_t *h_ctr;   // pinned host mirror of B_CTR
+    int32_t round;    // monotonic-counter stamp (advances every apply round)
+    int32_t round2;
+};
+
+struct g2_frontier {
+    g2_graph *g;
+    int32_t format;
+    int32_t *q;       // SPARSE: list (capacity cap)
+    int32_t cap;
+    int32_t *cnt;     // device int32 length (SPARSE)
+    uint32_t *bitmap; // BITMAP
+    uint8_t *boolmap; // BOOLMAP
+};
+
+namespace g2 {
+
+struct Topology {
+    std::atomic<int> refs;
+    int32_t n;
+    int32_t m;
+    bool symmetric;
+    int device;
+    int sm_count;
+    int64_t l2_bytes;
+    int max_coop_blocks;  // resident CTAs of kCta threads for the fused kernels
+    int32_t *rowptr, *col, *w;     // CSR
+    int32_t *crowptr, *ccol, *cw;  // CSC (== CSR pointers when symmetric)
+    int32_t *coo_src;              // lazily built source of every CSR arc
+    // EdgeBlocking (Algorithm 1) layout
+    int32_t eb_N;
+    int32_t eb_nseg;
+    int32_t *eb_src, *eb_dst;
+    int64_t *eb_seg;     // device [nseg+1]
+    int64_t *h_eb_seg;   // host copy
+    DevGraph view() const {
+        DevGraph d;
+        d.n = n; d.m = m;
+        d.rowptr = rowptr; d.col = col; d.w = w;
+        d.crowptr = crowptr; d.ccol = ccol; d.cw = cw;
+        return d;
+    }
+};
+
+// Device buffer of at least `bytes` bytes for slot b (grown if needed; old
+// contents are NOT kept when it grows).
+g2_status ws_get(g2_graph *g, Buf b, size_t bytes, void **out);
+template <class T>
+inline g2_status ws(g2_graph *g, Buf b, size_t count, T **out) {
+    return ws_get(g, b, count * sizeof(T), reinterpret_cast<void **>(out));
+}
+
+// Stream helpers.
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+g2_status sync_and_check(g2_graph *g, cudaStream_t st, int32_t *d_err);
+int grid_for(const g2_graph *g, int64_t items, int items_per_cta);
+
+// Start of a public call: reset the thread's stats, zero the device error
+// word (returned in *d_err, B_CTR slot 62) and the arc counter.
+g2_status begin_call(g2_graph *g, cudaStream_t st, int32_t **d_err);
+// End of a public call: synchronise, report device errors, collect counters.
+g2_status end_call(g2_graph *g, cudaStream_t st, int32_t *d_err);
+// Read `count` device int32 counters into g->h_ctr (synchronises) and check
+// the error word.
+g2_status read_counters(g2_graph *g, const int32_t *d, int count, cudaStream_t st, int32_t *d_err);
+
+// COO source array of the CSR arcs (built on first use).
+g2_status ensure_coo(g2_graph *g, cudaStream_t st);
+// EdgeBlocking layout for segment size N (Algorithm 1), built on the device.
+g2_status ensure_edge_block(g2_graph *g, int32_t N, cudaStream_t st);
+int32_t default_block_size(const g2_graph *g, int bytes_per_vertex);
+
+// Device-wide exclusive scan of int32 (out[0..count], out[count] = total).
+g2_status exclusive_scan_i32(g2_graph *g, const int32_t *in, int32_t *out, int32_t count,
+                             cudaStream_t st);
+
+// ------------------------------------------------------------- frontiers
+// Internal vertexset: which representation is live and its size (host copy,
+// valid after the round that produced it).
+struct VSet {
+    int rep;           // OUT_SPARSE (list), OUT_BITMAP, OUT_BOOLMAP; or -1 = all vertices
+    int32_t *q;        // list
+    int32_t qcap;
+    int32_t *cnt;      // device length of the list
+    uint32_t *bitmap;
+    uint8_t *boolmap;
+    int32_t size;      // host-known size
+};
+
+// Convert a vertexset to the representation `rep` using buffers `dst`
+// (which must not alias the source's live buffer).
+g2_status vset_convert(g2_graph *g, const VSet &src, int rep, VSet &dst, cudaStream_t st);
+// Exact member count of a bitmap / boolmap on the device into *d_out.
+g2_status vset_count(g2_graph *g, const VSet &v, int32_t *d_out, cudaStream_t st);
+
+// ------------------------------------------------------------- apply engine
+enum OpKind { K_BFS, K_RELAX, K_LABEL, K_PR, K_SIGMA, K_HOOK };
+
+struct OpArgs {
+    OpKind kind;
+    int32_t *i0;       // depth / dist / label
+    int32_t *i1;       // parent
+    const float *f0;   // contrib
+    float *f1;         // acc
+    double *d0;        // sigma
+    int32_t threshold; // RELAX near/far split (INT32_MAX: everything near)
+    int32_t *err;
+};
+
+struct OutArgs {
+    int rep;            // OUT_NONE / OUT_SPARSE / OUT_BITMAP / OUT_BOOLMAP
+    int32_t *q;
+    int32_t qcap;
+    int32_t *cnt;       // device counter of q (zeroed by the caller)
+    uint32_t *bitmap;   // zeroed by the caller
+    uint8_t *boolmap;   // zeroed by the caller
+    int dedup;          // DD_*
+    // far pile (RELAX only)
+    int32_t *q2;
+    int32_t q2cap;
+    int32_t *cnt2;
+    int32_t *stamp2;
+    int32_t round2;
+};
+
+// One edgeset.apply round with a simple schedule.  `in` must already be in
+// the representation the schedule's direction needs: a list (or all
+// vertices) for PUSH, a bitmap / boolmap (or all vertices) for PULL.
+g2_status apply_round(g2_graph *g, const g2_schedule &s, const OpArgs &op, const VSet &in,
+                      const OutArgs &out, cudaStream_t st);
+
+// Check that a simple schedule is valid and implemented for op/direction.
+g2_status check_schedule(const g2_graph *g, const g2_schedule &s, OpKind op, bool all_vertices);
+
+// Pick s1/s2 of a hybrid schedule for an input frontier of `size` vertices.
+const g2_schedule &pick_schedule(const g2_hybrid &h, int32_t size, int32_t n);
+g2_hybrid default_hybrid();
+
+}  // namespace g2

@@ -1,0 +1,460 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs, element by element.
+
+Tolerances: BFS depth/parent, CC labels, SSSP distances and EdgeBlocking
+arrays bit-exact; PageRank L1(gpu, fp64 oracle) <= 1e-5; BC
+|gpu - oracle| <= 1e-6 |oracle| + 1e-12 max|oracle|.
+
+Sizes: RMAT scale 14 (16,384 vertices, ~426K arcs: many CTA tiles and a
+ragged tail), road grids up to 256^2, tiny and degenerate graphs.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_07990_gb300 import graphgen as gg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PR_L1 = 1e-5
+BC_REL, BC_ABS = 1e-6, 1e-12
+
+
+@pytest.fixture(scope="module")
+def g2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_07990_gb300 import build_native
+    build_native.build()
+    from paper_2012_07990_gb300 import g2 as mod
+    return mod
+
+
+def dev(n, dtype=torch.int32):
+    return torch.empty(n, dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    return gg.rmat(14, seed=1)
+
+
+@pytest.fixture(scope="module")
+def grid():
+    return gg.road_grid(128, seed=1)
+
+
+def edge_cases():
+    return [
+        gg.from_arcs(1, [], [], name="single"),
+        gg.from_arcs(4, [], [], name="isolated4"),
+        gg.path(2), gg.path(37), gg.star(300), gg.cycle(1000), gg.complete(40),
+        gg.disjoint_union(gg.path(5), gg.star(70), gg.complete(9)),
+        gg.full_grid(33, 7),
+        gg.gnp(200, 0.02, 3, symmetric=False),
+        gg.gnp(500, 0.01, 4, symmetric=False),
+    ]
+
+
+LBS = ["VERTEX_BASED", "WM", "CM", "STRICT", "TWC", "ETWC"]
+
+
+def push_scheds(g2):
+    out = []
+    for lb in LBS:
+        out.append((f"{lb}/fused", g2.schedule(lb)))
+    out.append(("VB/unfused-bitmap", g2.schedule("VERTEX_BASED", frontier_creation=g2.G2_UNFUSED_BITMAP)))
+    out.append(("WM/unfused-boolmap", g2.schedule("WM", frontier_creation=g2.G2_UNFUSED_BOOLMAP)))
+    out.append(("CM/dedup-bitmap", g2.schedule("CM", dedup_type=g2.G2_DEDUP_BITMAP)))
+    out.append(("ETWC/dedup-boolmap", g2.schedule("ETWC", dedup_type=g2.G2_DEDUP_BOOLMAP)))
+    out.append(("TWC/no-dedup", g2.schedule("TWC", dedup=False)))
+    return out
+
+
+def pull_sched(g2, lb="VERTEX_BASED", rep=None, fc=None):
+    return g2.schedule(lb, direction=g2.G2_PULL, pull_frontier=rep if rep is not None else g2.G2_BITMAP,
+                       frontier_creation=fc if fc is not None else g2.G2_UNFUSED_BITMAP, dedup=False)
+
+
+# ----------------------------------------------------------------------- BFS
+def run_bfs(g2, g, src, sched, parent=True):
+    dg = g2.load_graph(g)
+    d = dev(g.n)
+    p = dev(g.n) if parent else None
+    g2.g2_bfs(dg, src, d, p, sched)
+    return host(d), (host(p) if parent else None)
+
+
+def test_bfs_push_schedules(g2, rmat14):
+    src = rmat14.max_degree_vertex()
+    od, op = oracle.bfs_graph(rmat14, src)
+    for name, s in push_scheds(g2):
+        d, p = run_bfs(g2, rmat14, src, s)
+        assert np.array_equal(d, od), name
+        assert np.array_equal(p, op), name
+
+
+@pytest.mark.parametrize("lb", ["VERTEX_BASED", "WM", "CM"])
+@pytest.mark.parametrize("rep", ["bitmap", "boolmap"])
+@pytest.mark.parametrize("fc", ["fused", "bitmap", "boolmap"])
+def test_bfs_direction_optimising(g2, rmat14, lb, rep, fc):
+    src = rmat14.max_degree_vertex()
+    od, op = oracle.bfs_graph(rmat14, src)
+    r = g2.G2_BITMAP if rep == "bitmap" else g2.G2_BOOLMAP
+    f = {"fused": g2.G2_FUSED, "bitmap": g2.G2_UNFUSED_BITMAP, "boolmap": g2.G2_UNFUSED_BOOLMAP}[fc]
+    for tau in (0.0, 0.02, 2.0):  # always pull / switching / always push
+        h = g2.hybrid(g2.schedule("ETWC"), pull_sched(g2, lb, r, f), tau)
+        d, p = run_bfs(g2, rmat14, src, h)
+        assert np.array_equal(d, od), (lb, rep, fc, tau)
+        assert np.array_equal(p, op), (lb, rep, fc, tau)
+
+
+@pytest.mark.parametrize("lb", ["VERTEX_BASED", "WM", "CM", "ETWC"])
+def test_bfs_fused(g2, rmat14, grid, lb):
+    for g in (rmat14, grid):
+        src = g.max_degree_vertex()
+        od, op = oracle.bfs_graph(g, src)
+        d, p = run_bfs(g2, g, src, g2.schedule(lb, kernel_fusion=True))
+        assert np.array_equal(d, od) and np.array_equal(p, op), lb
+        st = g2.g2_last_stats()
+        assert st["launches"] == 1 and st["iterations"] == od.max() + 1
+
+
+def test_bfs_edge_cases(g2):
+    for g in edge_cases():
+        for src in sorted({0, g.n - 1, g.n // 2}):
+            od, op = oracle.bfs_graph(g, src)
+            for s in (g2.schedule("ETWC"), g2.schedule("TWC"), g2.schedule("STRICT"),
+                      g2.hybrid(g2.schedule("WM"), pull_sched(g2), 0.1),
+                      g2.schedule("CM", kernel_fusion=True)):
+                d, p = run_bfs(g2, g, src, s)
+                assert np.array_equal(d, od), g.name
+                assert np.array_equal(p, op), g.name
+
+
+def test_bfs_default_and_depth_only(g2, rmat14):
+    src = 123
+    od, _ = oracle.bfs_graph(rmat14, src)
+    d, _ = run_bfs(g2, rmat14, src, None, parent=False)
+    assert np.array_equal(d, od)
+
+
+# ------------------------------------------------------------------------ CC
+def cc_scheds(g2):
+    out = [(lb, g2.schedule(lb)) for lb in LBS + ["EDGE_ONLY"]]
+    out += [(f"pull-{lb}", pull_sched(g2, lb)) for lb in ("VERTEX_BASED", "WM", "CM")]
+    out.append(("hybrid", g2.hybrid(g2.schedule("ETWC"), pull_sched(g2, "VERTEX_BASED", g2.G2_BOOLMAP), 0.3)))
+    return out
+
+
+def test_cc(g2, rmat14):
+    grid_sparse = gg.road_grid(96, p_delete=0.45, seed=5)
+    for g in (rmat14, grid_sparse, gg.disjoint_union(gg.path(5), gg.star(70), gg.complete(9))):
+        want = oracle.cc_graph(g)
+        dg = g2.load_graph(g)
+        for name, s in cc_scheds(g2) + [("default", None)]:
+            lab = dev(g.n)
+            g2.g2_cc(dg, lab, s)
+            assert np.array_equal(host(lab), want), (g.name, name)
+
+
+# ---------------------------------------------------------------------- SSSP
+def test_sssp_delta_sweep(g2, rmat14, grid):
+    cases = [(rmat14, gg.pair_weights(rmat14, 255, seed=1)), (grid, gg.pair_weights(grid, 1000, seed=1))]
+    for g, w in cases:
+        src = 0 if g is grid else g.max_degree_vertex()
+        want = oracle.sssp_graph(g, w, src)
+        dg = g2.load_graph(g, w)
+        for delta in (1, 7, 64, 1000, 4096):
+            for lb in ("VERTEX_BASED", "WM", "CM", "STRICT", "TWC", "ETWC"):
+                dist = dev(g.n)
+                g2.g2_sssp_delta(dg, src, delta, dist, g2.schedule(lb))
+                assert np.array_equal(host(dist), want), (g.name, delta, lb)
+
+
+@pytest.mark.parametrize("lb", ["VERTEX_BASED", "WM", "CM", "ETWC"])
+def test_sssp_fused(g2, rmat14, grid, lb):
+    for g, wmax in ((rmat14, 255), (grid, 1000)):
+        w = gg.pair_weights(g, wmax, seed=2)
+        src = 5
+        want = oracle.sssp_graph(g, w, src)
+        dg = g2.load_graph(g, w)
+        for delta in (1, 100, 4096):
+            dist = dev(g.n)
+            g2.g2_sssp_delta(dg, src, delta, dist, g2.schedule(lb, kernel_fusion=True))
+            assert np.array_equal(host(dist), want), (g.name, lb, delta)
+            assert g2.g2_last_stats()["launches"] == 1
+
+
+def test_sssp_dedup_variants_and_edge_cases(g2, rmat14):
+    w = gg.pair_weights(rmat14, 255, seed=3)
+    want = oracle.sssp_graph(rmat14, w, 7)
+    dg = g2.load_graph(rmat14, w)
+    for s in (g2.schedule("ETWC", dedup_type=g2.G2_DEDUP_BITMAP),
+              g2.schedule("WM", dedup_type=g2.G2_DEDUP_BOOLMAP),
+              g2.schedule("CM", dedup=False)):
+        dist = dev(rmat14.n)
+        g2.g2_sssp_delta(dg, 7, 50, dist, s)
+        assert np.array_equal(host(dist), want)
+    for g in edge_cases():
+        w = gg.pair_weights(g, 9, seed=1) if g.symmetric else \
+            (np.arange(g.m, dtype=np.int32) % 7 + 1).astype(np.int32)
+        want = oracle.sssp_graph(g, w, 0)
+        dg = g2.load_graph(g, w)
+        for s in (g2.schedule("TWC"), g2.schedule("VERTEX_BASED", kernel_fusion=True)):
+            dist = dev(g.n)
+            g2.g2_sssp_delta(dg, 0, 3, dist, s)
+            assert np.array_equal(host(dist), want), g.name
+
+
+# ------------------------------------------------------------------ PageRank
+def pr_scheds(g2):
+    out = [("default", None),
+           ("pull-edge-only", g2.schedule("EDGE_ONLY", direction=g2.G2_PULL))]
+    out += [(f"pull-{lb}", g2.schedule(lb, direction=g2.G2_PULL)) for lb in ("VERTEX_BASED", "WM", "CM")]
+    out += [(f"push-{lb}", g2.schedule(lb)) for lb in LBS + ["EDGE_ONLY"]]
+    out.append(("push-edge-only-blocked", g2.schedule("EDGE_ONLY", edge_blocking=True, blocking_size=1000)))
+    return out
+
+
+def test_pagerank(g2, rmat14, grid):
+    for g in (rmat14, grid, gg.gnp(300, 0.02, 9, symmetric=False), gg.from_arcs(5, [], [])):
+        ref = oracle.pagerank_graph(g, 0.85, 20)
+        dg = g2.load_graph(g)
+        for name, s in pr_scheds(g2):
+            rank = dev(g.n, torch.float32)
+            g2.g2_pagerank(dg, 0.85, 20, rank, s)
+            x = host(rank).astype(np.float64)
+            l1 = np.abs(x - ref).sum()
+            assert l1 <= PR_L1, (g.name, name, l1)
+
+
+def test_pagerank_iteration_counts(g2, rmat14):
+    dg = g2.load_graph(rmat14)
+    for iters in (0, 1, 2, 7):
+        ref = oracle.pagerank_graph(rmat14, 0.85, iters)
+        rank = dev(rmat14.n, torch.float32)
+        g2.g2_pagerank(dg, 0.85, iters, rank)
+        assert np.abs(host(rank) - ref).sum() <= PR_L1
+
+
+# ------------------------------------------------------------------------ BC
+def bc_close(got, want):
+    tol = BC_REL * np.abs(want) + BC_ABS * max(np.abs(want).max(), 1.0)
+    return np.all(np.abs(got - want) <= tol)
+
+
+def test_bc(g2, rmat14):
+    g = gg.rmat(12, seed=2)
+    srcs = gg.random_sources(g, 4, seed=3)
+    want = oracle.bc_graph(g, srcs)
+    dg = g2.load_graph(g)
+    for s in (None, g2.schedule("ETWC"), g2.schedule("VERTEX_BASED"),
+              g2.hybrid(g2.schedule("WM"), pull_sched(g2, "VERTEX_BASED", g2.G2_BITMAP, g2.G2_FUSED), 0.05)):
+        bc = dev(g.n, torch.float64)
+        g2.g2_bc(dg, srcs, bc, s)
+        assert bc_close(host(bc), want)
+    for g in edge_cases()[:9]:
+        srcs = np.arange(g.n, dtype=np.int32)[:50]
+        want = oracle.bc_graph(g, srcs)
+        bc = dev(g.n, torch.float64)
+        g2.g2_bc(g2.load_graph(g), srcs, bc, g2.schedule("CM"))
+        assert bc_close(host(bc), want), g.name
+
+
+def test_bc_path_counts_beyond_fp64(g2):
+    """Full 600x600 grid from a corner: path counts reach C(1198, 599) ~ 1e359,
+    past fp64; per-level power-of-two rescaling keeps the result exact to
+    rounding (the oracle counts in long double)."""
+    g = gg.full_grid(600, 600)
+    want = oracle.bc_graph(g, [0])
+    bc = dev(g.n, torch.float64)
+    g2.g2_bc(g2.load_graph(g), [0], bc, g2.schedule("WM"))
+    got = host(bc)
+    assert np.all(np.isfinite(got))
+    assert bc_close(got, want)
+
+
+# ----------------------------------------------------------- edgeset.apply
+def test_apply_pr_add_covers_each_arc_once(g2, rmat14):
+    """acc[v] = sum over in-arcs of contrib[u]: every load-balancing strategy
+    must visit each arc of the input vertexset exactly once."""
+    g = rmat14
+    rng = np.random.default_rng(0)
+    contrib = rng.integers(1, 64, g.n).astype(np.float32)  # small integers: exact float sums
+    active = np.sort(rng.choice(g.n, 3000, replace=False)).astype(np.int32)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    mask = np.isin(src, active)
+    want = np.bincount(g.col[mask], weights=contrib[src[mask]], minlength=g.n)
+    want_all = np.bincount(g.col, weights=contrib[src], minlength=g.n)
+    dg = g2.load_graph(g)
+    fin = g2.Frontier(dg, g2.G2_FRONTIER_SPARSE)
+    fin.set(active)
+    c = torch.from_numpy(contrib).cuda()
+    for lb in LBS + ["EDGE_ONLY"]:
+        acc = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+        if lb == "EDGE_ONLY":
+            g2.g2_edgeset_apply(dg, g2.G2_OP_PR_ADD, None, c, acc, g2.schedule(lb))
+            assert np.array_equal(host(acc), want_all.astype(np.float32)), lb
+            continue
+        g2.g2_edgeset_apply(dg, g2.G2_OP_PR_ADD, fin, c, acc, g2.schedule(lb))
+        assert np.array_equal(host(acc), want.astype(np.float32)), lb
+    for lb in ("VERTEX_BASED", "WM", "CM"):
+        for rep in (g2.G2_FRONTIER_BITMAP, g2.G2_FRONTIER_BOOLMAP):
+            f2 = g2.Frontier(dg, rep)
+            f2.set(active)
+            acc = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+            g2.g2_edgeset_apply(dg, g2.G2_OP_PR_ADD, f2, c, acc, g2.schedule(lb, direction=g2.G2_PULL))
+            assert np.array_equal(host(acc), want.astype(np.float32)), ("pull", lb, rep)
+
+
+def test_apply_bfs_round_and_frontier_formats(g2, rmat14):
+    """One applyModified round of the Fig. 1 program from a frontier: the
+    output vertexset is exactly the unvisited out-neighbours."""
+    g = rmat14
+    rng = np.random.default_rng(1)
+    depth0 = np.full(g.n, -1, np.int32)
+    front = np.sort(rng.choice(g.n, 500, replace=False)).astype(np.int32)
+    depth0[front] = 3
+    visited = rng.choice(g.n, 2000, replace=False)
+    depth0[visited] = np.where(depth0[visited] == -1, 2, depth0[visited])
+    src = np.repeat(np.arange(g.n), g.degrees())
+    hit = np.isin(src, front) & (depth0[g.col] == -1)
+    want_out = np.unique(g.col[hit])
+    want_depth = depth0.copy()
+    want_depth[want_out] = 4
+    dg = g2.load_graph(g)
+    for fmt_in, fmt_out, s in itertools.product(
+            (g2.G2_FRONTIER_SPARSE, g2.G2_FRONTIER_BITMAP, g2.G2_FRONTIER_BOOLMAP),
+            (g2.G2_FRONTIER_SPARSE, g2.G2_FRONTIER_BITMAP, g2.G2_FRONTIER_BOOLMAP),
+            (g2.schedule("ETWC"), g2.schedule("TWC", frontier_creation=g2.G2_UNFUSED_BOOLMAP),
+             pull_sched(g2, "WM", g2.G2_BOOLMAP, g2.G2_FUSED))):
+        fin = g2.Frontier(dg, fmt_in)
+        fin.set(front)
+        fout = g2.Frontier(dg, fmt_out)
+        d = torch.from_numpy(depth0).cuda()
+        k = g2.g2_edgeset_apply(dg, g2.G2_OP_BFS, fin, d, None, s, fout)
+        assert k == want_out.size
+        assert np.array_equal(host(d), want_depth)
+        lst = dev(g.n)
+        kk = fout.to_list(lst)
+        assert kk == k and np.array_equal(np.sort(host(lst)[:kk]), want_out)
+
+
+def test_apply_label_min_and_relax(g2, rmat14):
+    g = rmat14
+    rng = np.random.default_rng(2)
+    lab0 = rng.permutation(g.n).astype(np.int32)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    want = lab0.copy()
+    np.minimum.at(want, g.col, lab0[src])
+    changed = np.nonzero(want < lab0)[0]
+    dg = g2.load_graph(g, gg.pair_weights(g, 100))
+    for s in (g2.schedule("WM"), g2.schedule("STRICT", dedup_type=g2.G2_DEDUP_BITMAP),
+              g2.schedule("EDGE_ONLY"), pull_sched(g2, "CM", g2.G2_BOOLMAP, g2.G2_FUSED)):
+        lab = torch.from_numpy(lab0).cuda()
+        fout = g2.Frontier(dg, g2.G2_FRONTIER_SPARSE)
+        k = g2.g2_edgeset_apply(dg, g2.G2_OP_LABEL_MIN, None, lab, None, s, fout)
+        assert np.array_equal(host(lab), want)
+        lst = dev(g.n)
+        assert fout.to_list(lst) == k == changed.size
+        assert np.array_equal(np.sort(host(lst)[:k]), changed)
+
+
+# ---------------------------------------------------------------- EdgeBlocking
+@pytest.mark.parametrize("N", [1, 5, 1000, 16384])
+def test_edge_blocking_matches_algorithm1(g2, rmat14, N):
+    g = rmat14
+    src = np.repeat(np.arange(g.n, dtype=np.int32), g.degrees())
+    osrc, odst, oseg, ns = oracle.edgeblock(g.n, src, g.col, N)
+    dg = g2.load_graph(g)
+    assert g2.g2_edge_block(dg, N) == ns
+    s = dev(g.m)
+    d = dev(g.m)
+    seg = dev(ns + 1, torch.int64)
+    g2.g2_edge_block_export(dg, s, d, seg)
+    assert np.array_equal(host(s), osrc) and np.array_equal(host(d), odst)
+    assert np.array_equal(host(seg), oseg)
+
+
+# ------------------------------------------------------------------- batched
+def test_bfs_batch(g2):
+    g = gg.rmat(13, seed=4)
+    srcs = gg.random_sources(g, 64, seed=1)
+    dg = g2.load_graph(g)
+    want = np.stack([oracle.bfs_graph(g, s, want_parent=False)[0] for s in srcs])
+    for s in (None, g2.schedule("ETWC"), g2.schedule("WM"),
+              g2.hybrid(g2.schedule("CM"), g2.schedule("WM", direction=g2.G2_PULL), 0.05),
+              g2.schedule("VERTEX_BASED", direction=g2.G2_PULL)):
+        for k in (1, 17, 64):
+            depth = dev(k * g.n)
+            g2.g2_bfs_batch(dg, srcs[:k], depth, s)
+            assert np.array_equal(host(depth).reshape(k, g.n), want[:k]), k
+
+
+def test_sssp_batch(g2):
+    g = gg.rmat(12, seed=5)
+    w = gg.pair_weights(g, 255, seed=5)
+    srcs = gg.random_sources(g, 32, seed=2)
+    want = np.stack([oracle.sssp_graph(g, w, s) for s in srcs])
+    dg = g2.load_graph(g, w)
+    for delta in (0, 1, 40, 1000):
+        for lb in ("VERTEX_BASED", "WM", "CM", "ETWC"):
+            for k in (1, 32):
+                dist = dev(k * g.n)
+                g2.g2_sssp_batch(dg, srcs[:k], delta, dist, g2.schedule(lb))
+                assert np.array_equal(host(dist).reshape(k, g.n), want[:k]), (delta, lb, k)
+
+
+# ------------------------------------------------------------- errors, views
+def test_argument_errors(g2, rmat14):
+    dg = g2.load_graph(rmat14)
+    d = dev(rmat14.n)
+    with pytest.raises(g2.G2Error) as e:
+        g2.g2_bfs(dg, rmat14.n, d)
+    assert e.value.status == g2.G2_EINVAL
+    with pytest.raises(g2.G2Error) as e:
+        g2.g2_sssp_delta(dg, 0, 1, d)  # no weights
+    assert e.value.status == g2.G2_EINVAL
+    with pytest.raises(g2.G2Error) as e:
+        g2.g2_bfs(dg, 0, d, None, g2.schedule("EDGE_ONLY"))
+    assert e.value.status == g2.G2_EUNSUPPORTED
+    with pytest.raises(g2.G2Error) as e:  # unsorted adjacency list
+        g2.g2_load_csr(3, np.array([0, 2, 3, 4], np.int32), np.array([2, 1, 0, 0], np.int32))
+    assert e.value.status == g2.G2_EINVAL
+    with pytest.raises(g2.G2Error) as e:  # id out of range
+        g2.g2_load_csr(2, np.array([0, 1, 2], np.int32), np.array([1, 5], np.int32))
+    assert e.value.status == g2.G2_EINVAL
+
+
+def test_bounded_wait_times_out(g2):
+    """The bounded device-side wait used by grid barriers gives up after its
+    limit on a flag nothing sets, records G2_ETIMEOUT and returns; the context
+    stays usable afterwards."""
+    assert g2.g2_selftest_wait_timeout(2_000_000) == g2.G2_ETIMEOUT
+    x = torch.arange(10, device="cuda").sum().item()
+    assert x == 45
+
+
+def test_views_and_device_pointer_load(g2, rmat14):
+    g = rmat14
+    rp = torch.from_numpy(g.rowptr).cuda()
+    cl = torch.from_numpy(g.col).cuda()
+    dg = g2.g2_load_csr(g.n, rp, cl, None, True)
+    v = dg.view()
+    od, op = oracle.bfs_graph(g, 9)
+    for h in (dg, v):
+        d = dev(g.n)
+        p = dev(g.n)
+        g2.g2_bfs(h, 9, d, p, g2.schedule("ETWC"))
+        assert np.array_equal(host(d), od) and np.array_equal(host(p), op)
+    info = dg.info()
+    assert info["n"] == g.n and info["m"] == g.m and info["sm_count"] > 0
