@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the g2 hot path on one GB300 (or N independent replicas).
+
+Workload (default ``rmat22``): synthetic RMAT graph, scale 22 (4,194,304
+vertices), edge factor 16, (a, b, c, d) = (0.57, 0.19, 0.19, 0.05), seed 1,
+symmetrised, self-loops and duplicates dropped, int32 CSR (the CSC aliases
+it).  One step = direction-optimising BFS from the max-degree vertex + connected
+components + PageRank (d = 0.85, 20 rounds), all through the C ABI with the
+graph and outputs resident in HBM.
+
+value = traversed edges per step / step time, in GTEPS, where traversed edges =
+the arcs whose source BFS reached + m (CC) + 20 m (PageRank).
+
+Also reported: per-algorithm times; the dominant kernel's roofline (PageRank
+round kernel, CUDA events around its launches); end-to-end GTEPS through the
+public API with host buffers (graph upload from pinned host memory, results
+read back); the CPU oracle on a bounded sample; SM clocks sampled during the
+timed region.
+
+``--impl reference`` times the CPU oracle (the plain reference of this
+method) on the same workload, each step a bounded sample (BFS + CC + one
+PageRank round).  Under torchrun only rank 0 runs it.
+
+Multi-GPU: the path does not shard, so ``--gpus N`` runs N independent replicas
+(one per rank, weak scaling) with no data-path collective; value = all edges
+traversed by all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+PR_ITERS = 20
+DAMPING = 0.85
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_graph(scale: int):
+    from paper_2012_07990_gb300 import graphgen as gg
+    return gg.rmat(scale, 16, 0.57, 0.19, 0.19, seed=1)
+
+
+def bfs_schedule(g2):
+    """Direction-optimising hybrid (Table III): ETWC PUSH on a sparse queue
+    while |frontier| < 2% of n, else VERTEX_BASED PULL over a bitmap input with
+    an unfused bitmap output and no deduplication."""
+    push = g2.schedule("ETWC")
+    pull = g2.schedule("VERTEX_BASED", direction=g2.G2_PULL, pull_frontier=g2.G2_BITMAP,
+                       frontier_creation=g2.G2_UNFUSED_BITMAP, dedup=False)
+    return g2.hybrid(push, pull, 0.02)
+
+
+def cc_schedule(g2):
+    return g2.hybrid(g2.schedule("EDGE_ONLY"), g2.schedule("EDGE_ONLY"), 0.0)
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2012_07990_gb300 import build_native
+    build_native.build()
+    from paper_2012_07990_gb300 import g2
+
+    G = make_graph(args.scale)
+    n, m = G.n, G.m
+    src = G.max_degree_vertex()
+    dg = g2.load_graph(G)
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    label = torch.empty(n, dtype=torch.int32, device="cuda")
+    rank_t = torch.empty(n, dtype=torch.float32, device="cuda")
+    sb, sc = bfs_schedule(g2), cc_schedule(g2)
+    launches = {"n": 0}
+
+    def step(t_algo=None):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if t_algo is not None else None
+        if evs:
+            evs[0].record()
+        g2.g2_bfs(dg, src, depth, None, sb)
+        launches["n"] += g2.g2_last_stats()["launches"]
+        if evs:
+            evs[1].record()
+        g2.g2_cc(dg, label, sc)
+        launches["n"] += g2.g2_last_stats()["launches"]
+        if evs:
+            evs[2].record()
+        g2.g2_pagerank(dg, DAMPING, PR_ITERS, rank_t)
+        launches["n"] += g2.g2_last_stats()["launches"]
+        if evs:
+            evs[3].record()
+            t_algo.append(evs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    deg = G.degrees()
+    reached = depth.cpu().numpy() >= 0
+    m_bfs = int(deg[reached].sum())
+    edges_per_step = m_bfs + m + PR_ITERS * m
+
+    # per-algorithm split (separate, untimed-for-value pass)
+    t_algo = []
+    for _ in range(max(2, min(args.steps, 5))):
+        step(t_algo)
+    torch.cuda.synchronize()
+    per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in t_algo])
+    bfs_ms, cc_ms, pr_ms = (float(x) for x in np.median(per, axis=0))
+
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    g2.g2_kernel_time("pr_merge", reset=True)
+    g2.g2_set_kernel_timing(True)
+    launches["n"] = 0
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    g2.g2_set_kernel_timing(False)
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    pr_ms_total, pr_launches = g2.g2_kernel_time("pr_merge", reset=True)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * edges_per_step * args.steps / (total_ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the PageRank round (arc-balanced CSC sweep)
+    peak, peak_kind = read_peaks()
+    alg_bytes = 4 * m + 12 * n + 4 + 4 * n / PR_ITERS
+    avg_launch_ms = pr_ms_total / max(pr_launches, 1)
+    achieved = alg_bytes / (avg_launch_ms * 1e-3) / 1e9
+    traffic = read_traffic("pr_merge", G)
+    roofline = {"kernel": "k_pr_merge (PageRank round, PULL + EDGE_ONLY)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_launch_ms * 1e3, 2),
+                "launches": pr_launches, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+
+    e2e = run_e2e(args, g2, G, src, sb, sc, edges_per_step) if not args.no_e2e else None
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(G, src, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {
+            "metric": "GTEPS (direction-optimising BFS + CC + PageRank x20 on RMAT-22), % HBM roofline",
+            "value": round(value, 2), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32",
+            "data": "synthetic RMAT (seeded, counter-based generator)",
+            "config": {"workload": f"rmat{args.scale}_bfs_cc_pr",
+                       "graph": f"RMAT scale {args.scale}, ef 16, (0.57,0.19,0.19,0.05), seed 1, symmetric",
+                       "n": n, "m": m, "src": src, "pr_rounds": PR_ITERS, "damping": DAMPING,
+                       "edges_per_step": edges_per_step, "bfs_reached_arcs": m_bfs,
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (CSR 513 MB vs 129 MB L2); no flush"},
+            "per_algo": {"bfs_ms": round(bfs_ms, 4), "cc_ms": round(cc_ms, 4), "pr_ms": round(pr_ms, 4),
+                         "bfs_gteps": round(m_bfs / bfs_ms / 1e6, 2),
+                         "cc_gteps": round(m / cc_ms / 1e6, 2),
+                         "pr_gteps": round(PR_ITERS * m / pr_ms / 1e6, 2)},
+            "roofline": roofline,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches["n"],
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
+    """Same metric through the public API with host buffers: the graph is
+    uploaded from pinned host memory, the three algorithms run, the results
+    (depth, label, rank) are read back to pinned host memory, every step."""
+    import torch
+    n, m = G.n, G.m
+    h_rp = torch.from_numpy(G.rowptr).pin_memory()
+    h_col = torch.from_numpy(G.col).pin_memory()
+    h_depth = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_label = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_rank = torch.empty(n, dtype=torch.float32).pin_memory()
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    label = torch.empty(n, dtype=torch.int32, device="cuda")
+    rank_t = torch.empty(n, dtype=torch.float32, device="cuda")
+
+    def step():
+        dg = g2.g2_load_csr(n, np.frombuffer(h_rp.numpy().data, dtype=np.int32),
+                            np.frombuffer(h_col.numpy().data, dtype=np.int32), None, True)
+        g2.g2_bfs(dg, src, depth, None, sb)
+        g2.g2_cc(dg, label, sc)
+        g2.g2_pagerank(dg, DAMPING, PR_ITERS, rank_t)
+        h_depth.copy_(depth, non_blocking=True)
+        h_label.copy_(label, non_blocking=True)
+        h_rank.copy_(rank_t, non_blocking=True)
+        torch.cuda.synchronize()
+        dg.free()
+
+    step()
+    k = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(k):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    return {"value": round(edges_per_step / (ms * 1e-3) / 1e9, 2), "unit": "GTEPS",
+            "ms_per_step": round(ms, 3), "steps": k,
+            "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 12 * n}
+
+
+def read_traffic(kernel: str, G):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
+    was taken on the current source of that kernel (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        src = os.path.join(ROOT, "paper_2012_07990_gb300", "csrc", d["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != d["source_sha256_16"]:
+            return None
+        per_unit = d["dram_bytes_per_launch"] / d["units_per_launch"]
+        return int(per_unit * (4 * G.m + 12 * G.n))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_step(G, src, pr_rounds):
+    import oracle
+    t0 = time.perf_counter()
+    depth, _ = oracle.bfs_graph(G, src, want_parent=False)
+    t1 = time.perf_counter()
+    oracle.cc_graph(G)
+    t2 = time.perf_counter()
+    oracle.pagerank_graph(G, DAMPING, pr_rounds)
+    t3 = time.perf_counter()
+    return depth, (t1 - t0, t2 - t1, t3 - t2)
+
+
+def cpu_baseline(G, src, budget_s=30.0):
+    """The oracle as it stands, single thread, on a bounded sample of the same
+    workload: one BFS, one CC and the PageRank rounds that fit the budget."""
+    depth, (tb, tc, tp1) = oracle_step(G, src, 1)
+    m_bfs = int(G.degrees()[depth >= 0].sum())
+    edges = m_bfs + G.m + G.m
+    secs = tb + tc + tp1
+    return {"value": round(edges / secs / 1e9, 4), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"rmat{int(np.log2(G.n))}: 1 BFS + 1 CC + 1 PageRank round "
+                      f"(of 20) = {edges} edges in {secs:.2f} s",
+            "seconds": {"bfs": round(tb, 3), "cc": round(tc, 3), "pr_round": round(tp1, 3)},
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    G = make_graph(args.scale)
+    src = G.max_degree_vertex()
+    for _ in range(args.warmup):
+        oracle_step(G, src, 1)
+    times = []
+    t0 = time.perf_counter()
+    depth = None
+    for _ in range(args.steps):
+        depth, ts = oracle_step(G, src, 1)
+        times.append(sum(ts))
+    total = time.perf_counter() - t0
+    m_bfs = int(G.degrees()[depth >= 0].sum())
+    edges = m_bfs + 2 * G.m
+    value = edges * args.steps / total / 1e9
+    line = {
+        "impl": "reference",
+        "metric": "GTEPS (direction-optimising BFS + CC + PageRank x20 on RMAT-22), % HBM roofline",
+        "value": round(value, 4), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64",
+        "data": "synthetic RMAT (seeded, counter-based generator)",
+        "config": {"workload": f"rmat{args.scale}_bfs_cc_pr", "n": G.n, "m": G.m,
+                   "step_sample": "1 BFS + 1 CC + 1 PageRank round (of 20)"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": "each step: BFS + CC + one PageRank round on the full graph"},
+        "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=30.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -267,6 +267,15 @@ g2_status g2_last_stats(g2_stats *out);
  * CTA per launch). */
 void g2_set_count_arcs(int32_t enable);
 
+/* Kernel timing (diagnostic, off by default): when enabled, CUDA events are
+ * recorded on the call's stream around every launch of the named hot kernels
+ * ("pr_merge" PageRank round, "bfs_push", "bfs_pull", "cc_hook", "sssp_relax")
+ * and their durations accumulated per name on the calling thread.
+ * g2_kernel_time returns the total milliseconds and launch count for `name`
+ * since the last reset; reset != 0 clears every name afterwards. */
+void g2_set_kernel_timing(int32_t enable);
+g2_status g2_kernel_time(const char *name, double *ms, int64_t *launches, int32_t reset);
+
 const char *g2_last_error(void);
 
 /* Self-test of the bounded device-side wait used by grid barriers: a kernel

@@ -267,27 +267,36 @@ g2_status apply_round(g2_graph *g, const g2_schedule &s, const OpArgs &a, const 
     unsigned long long *ctr = nullptr;
     if (count_arcs_enabled()) G2_TRY(ws(g, B_ARCS, 2, &ctr));
     const DevGraph dg = t->view();
+    static const char *push_names[] = {"bfs_push", "sssp_relax", "label_push", "pr_push",
+                                       "sigma_push", "cc_hook"};
+    static const char *pull_names[] = {"bfs_pull", "relax_pull", "label_pull", "pr_pull",
+                                       "sigma_pull", "hook_pull"};
+    KTime kt;
+    ktime_begin(kt, s.direction == G2_PUSH ? push_names[a.kind] : pull_names[a.kind], st);
+    g2_status r = G2_OK;
     if (s.direction == G2_PUSH) {
         switch (a.kind) {
-            case K_BFS: return push_round(g, s, OpBFS{a.i0, a.i1}, in, out, ctr, st);
+            case K_BFS: r = push_round(g, s, OpBFS{a.i0, a.i1}, in, out, ctr, st); break;
             case K_RELAX:
-                return push_round(g, s, OpRelaxMin{a.i0, dg.w, a.err, a.threshold}, in, out, ctr, st);
-            case K_LABEL: return push_round(g, s, OpLabelMin{a.i0}, in, out, ctr, st);
-            case K_PR: return push_round(g, s, OpPRAdd{a.f0, a.f1}, in, out, ctr, st);
-            case K_SIGMA: return push_round(g, s, OpBCSigma{a.i0, a.d0}, in, out, ctr, st);
-            case K_HOOK: return push_round(g, s, OpHook{a.i0}, in, out, ctr, st);
+                r = push_round(g, s, OpRelaxMin{a.i0, dg.w, a.err, a.threshold}, in, out, ctr, st);
+                break;
+            case K_LABEL: r = push_round(g, s, OpLabelMin{a.i0}, in, out, ctr, st); break;
+            case K_PR: r = push_round(g, s, OpPRAdd{a.f0, a.f1}, in, out, ctr, st); break;
+            case K_SIGMA: r = push_round(g, s, OpBCSigma{a.i0, a.d0}, in, out, ctr, st); break;
+            case K_HOOK: r = push_round(g, s, OpHook{a.i0}, in, out, ctr, st); break;
         }
     } else {
         switch (a.kind) {
-            case K_BFS: return pull_round(g, s, PullBFS{a.i0, a.i1}, in, out, ctr, st);
-            case K_RELAX: return pull_round(g, s, PullRelaxMin{a.i0, dg.cw, a.err}, in, out, ctr, st);
-            case K_LABEL: return pull_round(g, s, PullLabelMin{a.i0}, in, out, ctr, st);
-            case K_PR: return pull_round(g, s, PullPRAdd{a.f0, a.f1}, in, out, ctr, st);
-            case K_SIGMA: return pull_round(g, s, PullBCSigma{a.i0, a.d0}, in, out, ctr, st);
-            case K_HOOK: return fail(G2_EUNSUPPORTED, "hooking is a PUSH update");
+            case K_BFS: r = pull_round(g, s, PullBFS{a.i0, a.i1}, in, out, ctr, st); break;
+            case K_RELAX: r = pull_round(g, s, PullRelaxMin{a.i0, dg.cw, a.err}, in, out, ctr, st); break;
+            case K_LABEL: r = pull_round(g, s, PullLabelMin{a.i0}, in, out, ctr, st); break;
+            case K_PR: r = pull_round(g, s, PullPRAdd{a.f0, a.f1}, in, out, ctr, st); break;
+            case K_SIGMA: r = pull_round(g, s, PullBCSigma{a.i0, a.d0}, in, out, ctr, st); break;
+            case K_HOOK: r = fail(G2_EUNSUPPORTED, "hooking is a PUSH update"); break;
         }
     }
-    return fail(G2_EINVAL, "unknown op");
+    ktime_end(kt, st);
+    return r;
 }
 
 }  // namespace g2

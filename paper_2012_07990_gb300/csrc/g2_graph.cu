@@ -32,6 +32,63 @@ g2_status cuda_fail(cudaError_t e, const char *what) {
 g2_stats &stats() { return t_stats; }
 bool count_arcs_enabled() { return t_count_arcs; }
 
+// --- kernel timing (events recorded around named launches)
+struct KTotal {
+    std::string name;
+    double ms;
+    int64_t launches;
+};
+static thread_local bool t_ktime = false;
+static thread_local std::vector<cudaEvent_t> t_ev_pool;
+static thread_local std::vector<KTime> t_ev_pending;
+static thread_local std::vector<KTotal> t_ktotals;
+
+static cudaEvent_t ev_get() {
+    if (!t_ev_pool.empty()) {
+        cudaEvent_t e = t_ev_pool.back();
+        t_ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void ktime_begin(KTime &k, const char *name, cudaStream_t st) {
+    k.name = nullptr;
+    if (!t_ktime) return;
+    k.name = name;
+    k.e0 = ev_get();
+    k.e1 = ev_get();
+    cudaEventRecord(k.e0, st);
+}
+
+void ktime_end(KTime &k, cudaStream_t st) {
+    if (!k.name) return;
+    cudaEventRecord(k.e1, st);
+    t_ev_pending.push_back(k);
+}
+
+static void ktime_resolve() {
+    for (KTime &k : t_ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, k.e0, k.e1) == cudaSuccess) {
+            KTotal *tot = nullptr;
+            for (KTotal &x : t_ktotals)
+                if (x.name == k.name) tot = &x;
+            if (!tot) {
+                t_ktotals.push_back(KTotal{k.name, 0.0, 0});
+                tot = &t_ktotals.back();
+            }
+            tot->ms += ms;
+            tot->launches += 1;
+        }
+        t_ev_pool.push_back(k.e0);
+        t_ev_pool.push_back(k.e1);
+    }
+    t_ev_pending.clear();
+}
+
 // ================================================================== kernels
 __global__ void k_validate_rows(const int32_t *rowptr, int32_t n, int32_t m, uint32_t *rowstart,
                                 int32_t *bad) {
@@ -321,6 +378,7 @@ g2_status begin_call(g2_graph *g, cudaStream_t st, int32_t **d_err) {
 
 g2_status end_call(g2_graph *g, cudaStream_t st, int32_t *d_err) {
     G2_TRY(sync_and_check(g, st, d_err));
+    ktime_resolve();
     if (count_arcs_enabled()) {
         unsigned long long *a;
         G2_TRY(ws(g, B_ARCS, 2, &a));
@@ -545,6 +603,21 @@ g2_status g2_last_stats(g2_stats *out) {
 }
 void g2_set_count_arcs(int32_t enable) { t_count_arcs = enable != 0; }
 
+void g2_set_kernel_timing(int32_t enable) { t_ktime = enable != 0; }
+
+g2_status g2_kernel_time(const char *name, double *ms, int64_t *launches, int32_t reset) {
+    if (!name || !ms || !launches) return fail(G2_EINVAL, "null argument");
+    *ms = 0.0;
+    *launches = 0;
+    for (const KTotal &x : t_ktotals)
+        if (x.name == name) {
+            *ms = x.ms;
+            *launches = x.launches;
+        }
+    if (reset) t_ktotals.clear();
+    return G2_OK;
+}
+
 g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *col,
                       const int32_t *w, uint32_t flags, void *stream, g2_graph **out) {
     if (!out) return fail(G2_EINVAL, "null output handle");
@@ -575,11 +648,17 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     t->l2_bytes = prop.l2CacheSize;
     t->max_coop_blocks = 0;
     if (finish_handle(g) != G2_OK) return bail(G2_ENOMEM);
-    size_t mb = (size_t)std::max<int64_t>(m, 1) * 4;
-    if ((e = cudaMalloc(&t->rowptr, ((size_t)n + 1) * 4)) != cudaSuccess)
+    // every array carries kPad spare elements (zeroed) so that a 16-byte
+    // rounded bulk copy of a slice ending at the last element stays in bounds
+    size_t mb = ((size_t)std::max<int64_t>(m, 1) + kPad) * 4;
+    size_t rb = ((size_t)n + 1 + kPad) * 4;
+    if ((e = cudaMalloc(&t->rowptr, rb)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMalloc rowptr"));
     if ((e = cudaMalloc(&t->col, mb)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc col"));
     if (w && (e = cudaMalloc(&t->w, mb)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc w"));
+    cudaMemsetAsync(t->rowptr, 0, rb, st);
+    cudaMemsetAsync(t->col, 0, mb, st);
+    if (w) cudaMemsetAsync(t->w, 0, mb, st);
     if ((e = cudaMemcpyAsync(t->rowptr, rowptr, ((size_t)n + 1) * 4, kind, st)) != cudaSuccess)
         return bail(cuda_fail(e, "copy rowptr"));
     if (m > 0 && (e = cudaMemcpyAsync(t->col, col, (size_t)m * 4, kind, st)) != cudaSuccess)
@@ -631,10 +710,13 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
         if (w && m > 0) cudaMemcpy(hw.data(), t->w, (size_t)m * 4, cudaMemcpyDeviceToHost);
         std::vector<int32_t> crp, ccl, cw;
         host_transpose(n, (int32_t)m, hrp.data(), hcl.data(), w ? hw.data() : nullptr, crp, ccl, cw);
-        if ((e = cudaMalloc(&t->crowptr, ((size_t)n + 1) * 4)) != cudaSuccess ||
+        if ((e = cudaMalloc(&t->crowptr, rb)) != cudaSuccess ||
             (e = cudaMalloc(&t->ccol, mb)) != cudaSuccess ||
             (w && (e = cudaMalloc(&t->cw, mb)) != cudaSuccess))
             return bail(cuda_fail(e, "cudaMalloc CSC"));
+        cudaMemset(t->crowptr, 0, rb);
+        cudaMemset(t->ccol, 0, mb);
+        if (w) cudaMemset(t->cw, 0, mb);
         cudaMemcpy(t->crowptr, crp.data(), ((size_t)n + 1) * 4, cudaMemcpyHostToDevice);
         if (m > 0) cudaMemcpy(t->ccol, ccl.data(), (size_t)m * 4, cudaMemcpyHostToDevice);
         if (w && m > 0) cudaMemcpy(t->cw, cw.data(), (size_t)m * 4, cudaMemcpyHostToDevice);

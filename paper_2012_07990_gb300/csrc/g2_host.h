@@ -120,6 +120,16 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 g2_status sync_and_check(g2_graph *g, cudaStream_t st, int32_t *d_err);
 int grid_for(const g2_graph *g, int64_t items, int items_per_cta);
 
+// Kernel timing: ktime_begin/ktime_end bracket one launch with CUDA events
+// when timing is enabled (no-ops otherwise); durations are collected by
+// end_call after the stream has synchronised.
+struct KTime {
+    const char *name;
+    cudaEvent_t e0, e1;
+};
+void ktime_begin(KTime &k, const char *name, cudaStream_t st);
+void ktime_end(KTime &k, cudaStream_t st);
+
 // Start of a public call: reset the thread's stats, zero the device error
 // word (returned in *d_err, B_CTR slot 62) and the arc counter.
 g2_status begin_call(g2_graph *g, cudaStream_t st, int32_t **d_err);

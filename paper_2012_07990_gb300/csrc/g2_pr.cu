@@ -119,78 +119,166 @@ __device__ __forceinline__ void block_add_double(double v, double *target) {
     }
 }
 
-__global__ void __launch_bounds__(kCta) k_pr_merge(PrArgs a) {
-    __shared__ int32_t s_end[kPrTile + 1];
-    __shared__ float s_val[kPrTile];
+// Tile coordinates on the merge path: rows r0..r1 (r1 partial), arcs e0..e1.
+struct PrTile {
+    int32_t r0, r1, e0, e1;
+};
+
+__device__ __forceinline__ PrTile pr_tile(const PrArgs &a, int32_t tile) {
+    const int64_t total = (int64_t)a.n + a.m;
+    const int64_t d0 = (int64_t)tile * kPrTile;
+    const int64_t d1 = d0 + kPrTile < total ? d0 + kPrTile : total;
+    PrTile c;
+    c.r0 = a.tile_r[tile];
+    c.r1 = a.tile_r[tile + 1];
+    c.e0 = (int32_t)(d0 - c.r0);
+    c.e1 = (int32_t)(d1 - c.r1);
+    return c;
+}
+
+// Stage layout of one tile in shared memory: the arc slice [e0 & ~3, ...)
+// rounded to whole 16-byte chunks, then the row-end slice crowptr[(r0+1) & ~3
+// ...] likewise.  Both come in by TMA bulk copies counted on one mbarrier.
+struct PrStage {
+    int32_t ea, ne_al, ra, nr_al;
+};
+
+__device__ __forceinline__ PrStage pr_stage(const PrTile &c) {
+    PrStage s;
+    s.ea = c.e0 & ~3;
+    s.ne_al = ((c.e1 - s.ea) + 3) & ~3;
+    s.ra = (c.r0 + 1) & ~3;
+    s.nr_al = ((c.r1 + 2 - s.ra) + 3) & ~3;
+    return s;
+}
+
+constexpr int kPrBuf = kPrTile + 32;  // ints per stage (slices + rounding)
+
+__device__ __forceinline__ void pr_issue(const PrArgs &a, const PrTile &c, int32_t *buf,
+                                         uint64_t *bar) {
+    PrStage s = pr_stage(c);
+    mbar_arrive_expect_tx(bar, (uint32_t)(s.ne_al + s.nr_al) * 4u);
+    if (s.ne_al > 0) tma_load_1d(buf, a.ccol + s.ea, (uint32_t)s.ne_al * 4u, bar);
+    tma_load_1d(buf + s.ne_al, a.crowptr + s.ra, (uint32_t)s.nr_al * 4u, bar);
+}
+
+__global__ void __launch_bounds__(kCta) k_pr_merge(PrArgs a, uint64_t limit_ns, int32_t *err) {
+    __shared__ __align__(16) int32_t buf[2][kPrBuf];
     __shared__ float s_acc[kPrTile + 1];
+    __shared__ __align__(8) uint64_t bar[2];
     const int tid = threadIdx.x, lane = tid & 31;
     const float dterm = (float)(*a.dprev * a.inv_n);
     double dsum = 0.0;
-    const int64_t total = (int64_t)a.n + a.m;
-    for (int32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const int64_t d0 = (int64_t)tile * kPrTile;
-        const int64_t d1 = d0 + kPrTile < total ? d0 + kPrTile : total;
-        const int32_t r0 = a.tile_r[tile], r1 = a.tile_r[tile + 1];
-        const int32_t e0 = (int32_t)(d0 - r0), e1 = (int32_t)(d1 - r1);
-        const int32_t nr = r1 - r0, ne = e1 - e0;
-        // stage the row ends of rows r0..r1 and the gathered shares of arcs e0..e1
-        for (int32_t i = tid; i <= nr; i += kCta) {
-            s_end[i] = r0 + i < a.n ? a.crowptr[r0 + i + 1] : G2_INF32;
-            s_acc[i] = 0.f;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int32_t tile = blockIdx.x;
+    if (tid == 0 && tile < a.ntiles) pr_issue(a, pr_tile(a, tile), buf[0], &bar[0]);
+    uint32_t phase0 = 0, phase1 = 0;
+    for (int s = 0; tile < a.ntiles; tile += gridDim.x, s ^= 1) {
+        const PrTile c = pr_tile(a, tile);
+        const int32_t next = tile + gridDim.x;
+        // prefetch the next tile into the other stage (freed by the barrier
+        // that ended the previous tile)
+        if (tid == 0 && next < a.ntiles) pr_issue(a, pr_tile(a, next), buf[s ^ 1], &bar[s ^ 1]);
+        const uint32_t ph = s ? phase1 : phase0;
+        bool ok = mbar_wait_bounded(&bar[s], ph, limit_ns);
+        if (s) phase1 ^= 1u;
+        else phase0 ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                set_error(err, G2_ETIMEOUT);
+                // let the prefetch already issued land before the CTA exits
+                if (next < a.ntiles) mbar_wait_bounded(&bar[s ^ 1], s ? phase0 : phase1, limit_ns);
+            }
+            break;
         }
-        for (int32_t j = tid; j < ne; j += kCta) s_val[j] = a.contrib[a.ccol[e0 + j]];
-        __syncthreads();
-        // this thread's slice of the merged sequence
+        const PrStage sg = pr_stage(c);
+        int32_t *scol = buf[s] + (c.e0 - sg.ea);                   // arc j of the tile
+        const int32_t *send = buf[s] + sg.ne_al + (c.r0 + 1 - sg.ra);  // end of row r0+i
+        const int32_t nr = c.r1 - c.r0, ne = c.e1 - c.e0;
+        const bool last_row_real = c.r1 < a.n;
+        for (int32_t i = tid; i <= nr; i += kCta) s_acc[i] = 0.f;
+        // this thread's slice [dl, dl2) of the merged sequence
         const int32_t items = nr + ne;
         int32_t dl = tid * kPrIPT;
         if (dl > items) dl = items;
-        int32_t lo = dl - ne > 0 ? dl - ne : 0, hi = dl < nr ? dl : nr;
-        while (lo < hi) {
-            int32_t mid = (lo + hi) >> 1;
-            if (s_end[mid] <= e0 + (dl - mid - 1)) lo = mid + 1;
-            else hi = mid;
+        const int32_t dl2 = dl + kPrIPT < items ? dl + kPrIPT : items;
+        int32_t ri, ej, ej2;
+        {
+            int32_t lo = dl - ne > 0 ? dl - ne : 0, hi = dl < nr ? dl : nr;
+            while (lo < hi) {
+                int32_t mid = (lo + hi) >> 1;
+                if (send[mid] <= c.e0 + (dl - mid - 1)) lo = mid + 1;
+                else hi = mid;
+            }
+            ri = lo;
+            ej = dl - lo;
+            lo = dl2 - ne > 0 ? dl2 - ne : 0;
+            hi = dl2 < nr ? dl2 : nr;
+            if (lo < ri) lo = ri;
+            while (lo < hi) {
+                int32_t mid = (lo + hi) >> 1;
+                if (send[mid] <= c.e0 + (dl2 - mid - 1)) lo = mid + 1;
+                else hi = mid;
+            }
+            ej2 = dl2 - lo;
         }
-        int32_t ri = lo, ej = dl - lo;
-        int32_t row_end = s_end[ri];
-        const int32_t my_end = dl + kPrIPT < items ? dl + kPrIPT : items;
+        // gather the shares of this thread's arcs (independent loads), write
+        // them over the arc ids, which no other thread reads
+        {
+            const int32_t ne_t = ej2 - ej;
+            float v[kPrIPT];
+#pragma unroll
+            for (int k = 0; k < kPrIPT; ++k)
+                v[k] = k < ne_t ? __ldg(a.contrib + scol[ej + k]) : 0.f;
+#pragma unroll
+            for (int k = 0; k < kPrIPT; ++k)
+                if (k < ne_t) scol[ej + k] = __float_as_int(v[k]);
+        }
+        __syncthreads();  // s_acc zeroed everywhere before the adds
+        int32_t row_end = (ri < nr || last_row_real) ? send[ri] : G2_INF32;
         float run = 0.f;
-        for (int32_t k = dl; k < my_end; ++k) {
-            if (e0 + ej < row_end) {
-                run += s_val[ej];
+        for (int32_t k = dl; k < dl2; ++k) {
+            if (c.e0 + ej < row_end) {
+                run += __int_as_float(scol[ej]);
                 ++ej;
             } else {
                 if (run != 0.f) atomicAdd(&s_acc[ri], run);
                 run = 0.f;
                 ++ri;
-                row_end = s_end[ri];
+                row_end = (ri < nr || last_row_real) ? send[ri] : G2_INF32;
             }
         }
         // carry of the unfinished row: combine equal rows across the warp
-        // first (row ids do not decrease with the lane), one atomic per row
+        // (row ids do not decrease with the lane), one atomic per row
         int32_t key = ri;
         float v = run;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             float ov = __shfl_up_sync(G2_FULL, v, d);
-            int32_t ok = __shfl_up_sync(G2_FULL, key, d);
-            if (lane >= d && ok == key) v += ov;
+            int32_t ok2 = __shfl_up_sync(G2_FULL, key, d);
+            if (lane >= d && ok2 == key) v += ov;
         }
         int32_t nk = __shfl_down_sync(G2_FULL, key, 1);
         if ((lane == 31 || nk != key) && v != 0.f) atomicAdd(&s_acc[key], v);
         __syncthreads();
         // finish the rows that ended in this tile
         for (int32_t i = tid; i < nr; i += kCta) {
-            int32_t r = r0 + i;
-            int32_t beg = i == 0 ? a.crowptr[r0] : s_end[i - 1];
-            if (i == 0 && beg < e0) {
+            int32_t r = c.r0 + i;
+            int32_t beg = i == 0 ? a.crowptr[c.r0] : send[i - 1];
+            if (i == 0 && beg < c.e0) {
                 atomicAdd(&a.acc[r], s_acc[0]);  // started in an earlier tile
                 continue;
             }
-            pr_finalize(a, r, s_acc[i], beg, s_end[i], dterm, dsum);
+            pr_finalize(a, r, s_acc[i], beg, send[i], dterm, dsum);
         }
-        if (tid == 0 && r1 < a.n) {
-            int32_t beg1 = nr > 0 ? s_end[nr - 1] : a.crowptr[r1];
-            if (e1 > beg1) atomicAdd(&a.acc[r1], s_acc[nr]);  // continues in a later tile
+        if (tid == 0 && last_row_real) {
+            int32_t beg1 = nr > 0 ? send[nr - 1] : a.crowptr[c.r1];
+            if (c.e1 > beg1) atomicAdd(&a.acc[c.r1], s_acc[nr]);  // continues in a later tile
         }
         __syncthreads();
     }
@@ -315,7 +403,10 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
             a.dprev = dd + (it & 1);
             a.dnext = dd + ((it + 1) & 1);
             G2_CK(cudaMemsetAsync(dd + ((it + 1) & 1), 0, sizeof(double), st));
-            k_pr_merge<<<grid, kCta, 0, st>>>(a);
+            KTime kt;
+            ktime_begin(kt, "pr_merge", st);
+            k_pr_merge<<<grid, kCta, 0, st>>>(a, 2000000000ULL, d_err);
+            ktime_end(kt, st);
             k_pr_fixup<<<(ntiles + kCta) / kCta, kCta, 0, st>>>(a, split, ctrs + 10);
             stats().launches += 2;
             stats().iterations++;

@@ -92,9 +92,11 @@ _SIGS = {
     "g2_set_count_arcs": [I32],
     "g2_last_error": [],
     "g2_selftest_wait_timeout": [I64, P],
+    "g2_set_kernel_timing": [I32],
+    "g2_kernel_time": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I32],
     "g2_version": [],
 }
-_VOID = {"g2_free_graph", "g2_frontier_free", "g2_set_count_arcs"}
+_VOID = {"g2_free_graph", "g2_frontier_free", "g2_set_count_arcs", "g2_set_kernel_timing"}
 _STR = {"g2_last_error", "g2_version"}
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -313,6 +315,18 @@ def g2_last_stats() -> dict:
 
 def g2_set_count_arcs(enable: bool):
     _lib.g2_set_count_arcs(1 if enable else 0)
+
+
+def g2_set_kernel_timing(enable: bool):
+    _lib.g2_set_kernel_timing(1 if enable else 0)
+
+
+def g2_kernel_time(name: str, reset: bool = False):
+    """(total ms, launches) recorded for the named kernel on this thread."""
+    ms, k = ctypes.c_double(), I64()
+    _check(_lib.g2_kernel_time(name.encode(), ctypes.byref(ms), ctypes.byref(k), 1 if reset else 0),
+           "g2_kernel_time")
+    return ms.value, k.value
 
 
 def g2_selftest_wait_timeout(limit_ns: int, stream=None) -> int:

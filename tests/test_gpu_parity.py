@@ -349,21 +349,34 @@ def test_apply_bfs_round_and_frontier_formats(g2, rmat14):
         assert kk == k and np.array_equal(np.sort(host(lst)[:kk]), want_out)
 
 
-def test_apply_label_min_and_relax(g2, rmat14):
+def test_apply_label_min_round_invariants(g2, rmat14):
+    """One LABEL_MIN round over all vertices.  Updates are in place (a source
+    may already carry a value lowered earlier in the same round), so the
+    round's result is bracketed: at or below one synchronous round from the
+    initial labels, at or above the fixpoint, and the output vertexset is
+    exactly the set of lowered labels."""
     g = rmat14
     rng = np.random.default_rng(2)
     lab0 = rng.permutation(g.n).astype(np.int32)
     src = np.repeat(np.arange(g.n), g.degrees())
-    want = lab0.copy()
-    np.minimum.at(want, g.col, lab0[src])
-    changed = np.nonzero(want < lab0)[0]
+    one = lab0.copy()
+    np.minimum.at(one, g.col, lab0[src])
+    fix = one.copy()
+    while True:
+        nxt = fix.copy()
+        np.minimum.at(nxt, g.col, fix[src])
+        if np.array_equal(nxt, fix):
+            break
+        fix = nxt
     dg = g2.load_graph(g, gg.pair_weights(g, 100))
     for s in (g2.schedule("WM"), g2.schedule("STRICT", dedup_type=g2.G2_DEDUP_BITMAP),
               g2.schedule("EDGE_ONLY"), pull_sched(g2, "CM", g2.G2_BOOLMAP, g2.G2_FUSED)):
         lab = torch.from_numpy(lab0).cuda()
         fout = g2.Frontier(dg, g2.G2_FRONTIER_SPARSE)
         k = g2.g2_edgeset_apply(dg, g2.G2_OP_LABEL_MIN, None, lab, None, s, fout)
-        assert np.array_equal(host(lab), want)
+        got = host(lab)
+        assert np.all(got <= one) and np.all(got >= fix)
+        changed = np.nonzero(got < lab0)[0]
         lst = dev(g.n)
         assert fout.to_list(lst) == k == changed.size
         assert np.array_equal(np.sort(host(lst)[:k]), changed)
