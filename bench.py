@@ -122,17 +122,17 @@ def make_graph(scale: int):
 
 
 def bfs_schedule(g2):
-    """Direction-optimising hybrid (Table III): ETWC PUSH on a sparse queue
-    while |frontier| < 2% of n, else VERTEX_BASED PULL over a bitmap input with
-    an unfused bitmap output and no deduplication."""
-    push = g2.schedule("ETWC")
-    pull = g2.schedule("VERTEX_BASED", direction=g2.G2_PULL, pull_frontier=g2.G2_BITMAP,
-                       frontier_creation=g2.G2_UNFUSED_BITMAP, dedup=False)
-    return g2.hybrid(push, pull, 0.02)
+    """The library's tuned BFS schedule (NULL): direction-optimising hybrid
+    (Table III), STRICT PUSH on a sparse queue while |frontier| < 2% of n,
+    else VERTEX_BASED PULL over a bitmap input with an unfused bitmap output
+    and no deduplication."""
+    return None
 
 
 def cc_schedule(g2):
-    return g2.hybrid(g2.schedule("EDGE_ONLY"), g2.schedule("EDGE_ONLY"), 0.0)
+    """The library's tuned CC (NULL): lock-free linking with neighbour
+    sampling, then pointer jumping."""
+    return None
 
 
 # ------------------------------------------------------------------- ours

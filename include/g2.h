@@ -205,31 +205,44 @@ g2_status g2_edgeset_apply(g2_graph *g, g2_op op, g2_frontier *in, void *vdata, 
                            void *stream);
 
 /* -------------------------------------------------------------- algorithms */
+/* Schedules: a non-NULL `sched` runs exactly that schedule (a simple one, or a
+ * hybrid choosing s1/s2 each round by the input vertexset size).  NULL selects
+ * the library's tuned schedule for the algorithm, stated with each call. */
 /* BFS (Fig. 1): depth int32[n] device (-1 unreachable), parent int32[n]
  * device or NULL (parent[src] = src, else the smallest-id in-neighbour one
- * level up, -1 unreachable).  Loop until the frontier is empty. */
+ * level up, -1 unreachable).  Loop until the frontier is empty.  With kernel
+ * fusion the whole loop is one persistent cooperative kernel.  NULL schedule:
+ * direction-optimising hybrid, STRICT PUSH below 2% of n, VERTEX_BASED PULL
+ * over a bitmap otherwise. */
 g2_status g2_bfs(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                  const g2_hybrid *sched, void *stream);
 
 /* Connected components (Soman et al., Sec. VII): label int32[n] device,
  * label[v] = smallest vertex id in v's component (arcs taken as undirected).
- * Hooking along the arcs of the active vertices (an edgeset.apply with the
- * schedule's load balancing), then pointer jumping to the roots; active =
- * vertices whose label changed.  Needs a symmetric graph (G2_EINVAL else). */
+ * With a schedule: rounds of hooking along the arcs of the active vertices
+ * (PUSH, an edgeset.apply with the schedule's load balancing) or min-label
+ * propagation (PULL), each followed by pointer jumping to the roots; active =
+ * vertices whose label changed.  NULL schedule: lock-free linking with
+ * neighbour sampling (two sampled arcs per vertex, then the remaining arcs of
+ * the vertices outside the largest component), then pointer jumping.  Needs a
+ * symmetric graph (G2_EINVAL else). */
 g2_status g2_cc(g2_graph *g, int32_t *label, const g2_hybrid *sched, void *stream);
 
 /* Delta-stepping SSSP with a two-bucket (near/far) priority queue
  * (Sec. III and V, configDelta): dist int32[n] device, INT32_MAX unreachable.
  * delta > 0 overrides the schedule's delta.  Needs weights >= 1.
- * G2_EOVERFLOW if a distance would reach INT32_MAX. */
+ * G2_EOVERFLOW if a distance would reach INT32_MAX.  NULL schedule: STRICT
+ * PUSH, unfused. */
 g2_status g2_sssp_delta(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
                         const g2_hybrid *sched, void *stream);
 
 /* PageRank, topology-driven (Sec. VII): rank float[n] device.  x0 = 1/n;
  * each round x'[v] = (1-d)/n + d*(sum_{u->v} x[u]/outdeg(u) + D/n), D = the
  * total rank of vertices without out-arcs.  `iters` rounds, no convergence
- * test.  PULL: segmented sums over the CSC; PUSH + EDGE_ONLY (+ EdgeBlocking):
- * arc-parallel atomic adds. */
+ * test.  PULL + EDGE_ONLY (and NULL): arc-balanced segmented sums over the
+ * CSC; PULL + VERTEX_BASED/WM/CM: per-destination sums; PUSH (any load
+ * balancing, EDGE_ONLY optionally with EdgeBlocking): arc-parallel atomic
+ * adds. */
 g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, float *rank,
                       const g2_hybrid *sched, void *stream);
 

@@ -60,6 +60,65 @@ __global__ void k_compress(int32_t *label, int32_t n) {
     }
 }
 
+// Lock-free union of the trees of u and v: the higher root is hung under the
+// lower one by compare-and-swap, so the minimum id of every tree stays its
+// root.  Labels only decrease, so the loop ends (Sutton et al., "Optimizing
+// parallel graph connectivity computation via subgraph sampling", 2018).
+__device__ __forceinline__ void cc_link(int32_t *label, int32_t u, int32_t v) {
+    int32_t p1 = label[u], p2 = label[v];
+    while (p1 != p2) {
+        int32_t hi = p1 > p2 ? p1 : p2, lo = p1 + p2 - hi;
+        int32_t ph = label[hi];
+        if (ph == lo) break;
+        if (ph == hi && atomicCAS(&label[hi], hi, lo) == hi) break;
+        p1 = label[label[hi]];
+        p2 = label[lo];
+    }
+}
+
+// link every vertex with its r-th neighbour
+__global__ void k_cc_sample(const int32_t *rowptr, const int32_t *col, int32_t n, int32_t r,
+                            int32_t *label) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t b = rowptr[v];
+        if (rowptr[v + 1] - b > r) cc_link(label, (int32_t)v, col[b + r]);
+    }
+}
+
+// labels of a fixed pseudo-random sample of vertices
+__global__ void k_cc_probe(const int32_t *label, int32_t n, int32_t k, int32_t *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) {
+        uint32_t h = (uint32_t)i * 2654435761u + 0x9E3779B9u;
+        h ^= h >> 16;
+        h *= 0x85EBCA6Bu;
+        h ^= h >> 13;
+        out[i] = label[h % (uint32_t)n];
+    }
+}
+
+// link the remaining arcs (from position `skip` on) of every vertex outside
+// the component `giant`; a warp walks one vertex so long lists are shared
+__global__ void k_cc_finish(const int32_t *rowptr, const int32_t *col, int32_t n, int32_t skip,
+                            int32_t giant, int32_t *label) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = gw * 32; base < n; base += nw * 32) {
+        int64_t v = base + lane;
+        bool act = v < n && label[v] != giant && rowptr[v + 1] - rowptr[v] > skip;
+        unsigned m = __ballot_sync(G2_FULL, act);
+        while (m) {
+            int src = __ffs(m) - 1;
+            m &= m - 1;
+            int32_t u = (int32_t)(base + src);
+            int32_t b = rowptr[u] + skip, e = rowptr[u + 1];
+            for (int32_t k = b + lane; k < e; k += 32) cc_link(label, u, col[k]);
+        }
+    }
+}
+
 // list of vertices whose label differs from the round-start snapshot
 __global__ void k_changed(const int32_t *label, const int32_t *lab0, int32_t n, int32_t *q,
                           int32_t *cnt) {
@@ -376,6 +435,46 @@ g2_status cc_run(g2_graph *g, int32_t *label, const g2_hybrid &h, cudaStream_t s
     return G2_OK;
 }
 
+// Tuned CC: neighbour sampling with lock-free linking (two sampling rounds,
+// compress, giant component from a sample of labels, link the rest of the
+// arcs of the vertices outside it, compress).  Output: min-id labels.
+g2_status cc_sampled(g2_graph *g, int32_t *label, cudaStream_t st, int32_t *d_err) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    if (n == 0) return G2_OK;
+    constexpr int kSample = 2, kProbe = 1024;
+    const int grid = grid_for(g, n, kCta);
+    k_iota<<<grid, kCta, 0, st>>>(label, n);
+    for (int r = 0; r < kSample; ++r) {
+        k_cc_sample<<<grid, kCta, 0, st>>>(t->rowptr, t->col, n, r, label);
+        k_compress<<<grid, kCta, 0, st>>>(label, n);
+    }
+    int32_t *probe;
+    G2_TRY(ws(g, B_I1, kProbe, &probe));
+    k_cc_probe<<<(kProbe + kCta - 1) / kCta, kCta, 0, st>>>(label, n, kProbe, probe);
+    std::vector<int32_t> h(kProbe);
+    G2_CK(cudaMemcpyAsync(h.data(), probe, kProbe * 4, cudaMemcpyDeviceToHost, st));
+    G2_TRY(sync_and_check(g, st, d_err));
+    std::sort(h.begin(), h.end());
+    int32_t giant = h[0];
+    int best = 0;
+    for (int i = 0; i < kProbe;) {
+        int j = i;
+        while (j < kProbe && h[j] == h[i]) ++j;
+        if (j - i > best) {
+            best = j - i;
+            giant = h[i];
+        }
+        i = j;
+    }
+    k_cc_finish<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->rowptr, t->col, n, kSample, giant, label);
+    k_compress<<<grid, kCta, 0, st>>>(label, n);
+    stats().launches += 2 * kSample + 5;
+    stats().iterations = kSample + 1;
+    G2_CK(cudaGetLastError());
+    return G2_OK;
+}
+
 // ==================================================================== SSSP
 g2_status sssp_plain(g2_graph *g, int32_t src, int32_t delta, int32_t *dist, const g2_hybrid &h,
                      cudaStream_t st, int32_t *d_err) {
@@ -589,6 +688,30 @@ g2_status bc_run(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const 
 
 using namespace g2;
 
+// Tuned schedule for BFS when the caller passes none (measured on GB300 with
+// RMAT-22): direction-optimising hybrid, STRICT PUSH on a sparse queue while
+// the frontier holds < 2% of the vertices, else VERTEX_BASED PULL over a
+// bitmap input with an unfused bitmap output and no deduplication.
+static g2_hybrid tuned_bfs_hybrid() {
+    g2_hybrid h = default_hybrid();
+    h.criteria = G2_INPUT_VERTEXSET_SIZE;
+    h.threshold = 0.02f;
+    h.s1.load_balance = G2_LB_STRICT;
+    h.s2.load_balance = G2_LB_VERTEX_BASED;
+    h.s2.direction = G2_PULL;
+    h.s2.pull_frontier = G2_BITMAP;
+    h.s2.frontier_creation = G2_UNFUSED_BITMAP;
+    h.s2.dedup = G2_DEDUP_DISABLED;
+    return h;
+}
+
+// Tuned schedule for delta-stepping when the caller passes none: STRICT PUSH.
+static g2_hybrid tuned_sssp_hybrid() {
+    g2_hybrid h = default_hybrid();
+    h.s1.load_balance = G2_LB_STRICT;
+    return h;
+}
+
 // ====================================================================== C ABI
 extern "C" {
 
@@ -597,7 +720,7 @@ g2_status g2_bfs(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent, cons
     if (!g || !depth) return fail(G2_EINVAL, "null graph or depth");
     G2_TRY(check_src(g, src));
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : default_hybrid();
+    g2_hybrid h = sched ? *sched : tuned_bfs_hybrid();
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));
     if (h.s1.kernel_fusion) {
@@ -618,7 +741,8 @@ g2_status g2_cc(g2_graph *g, int32_t *label, const g2_hybrid *sched, void *strea
     if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "CC has no fused variant");
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));
-    G2_TRY(cc_run(g, label, h, st, d_err));
+    if (sched) G2_TRY(cc_run(g, label, h, st, d_err));
+    else G2_TRY(cc_sampled(g, label, st, d_err));
     return end_call(g, st, d_err);
 }
 
@@ -628,7 +752,7 @@ g2_status g2_sssp_delta(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
     G2_TRY(check_src(g, src));
     if (!g->topo->w) return fail(G2_EINVAL, "SSSP needs arc weights");
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : default_hybrid();
+    g2_hybrid h = sched ? *sched : tuned_sssp_hybrid();
     if (delta <= 0) delta = h.s1.delta > 0 ? h.s1.delta : 1;
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));

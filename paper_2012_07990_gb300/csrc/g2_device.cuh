@@ -16,7 +16,7 @@ namespace g2 {
 
 constexpr int kCta = 256;        // threads per CTA in the traversal kernels
 constexpr int kWarps = kCta / 32;
-constexpr int kPad = 64;         // spare zeroed elements after every device graph array
+constexpr int kPad = 256;        // spare zeroed elements after every device graph array
 
 // ----------------------------------------------------------------- graph view
 struct DevGraph {

@@ -547,6 +547,11 @@ static void topo_release(Topology *t) {
     }
     if (t->coo_src) cudaFree(t->coo_src);
     if (t->eb_src) { cudaFree(t->eb_src); cudaFree(t->eb_dst); cudaFree(t->eb_seg); }
+    if (t->pr_perm) cudaFree(t->pr_perm);
+    if (t->pr_ccol) cudaFree(t->pr_ccol);
+    if (t->seg_head) cudaFree(t->seg_head);
+    if (t->seg_nzrow) cudaFree(t->seg_nzrow);
+    if (t->seg_chunk_rank) cudaFree(t->seg_chunk_rank);
     delete[] t->h_eb_seg;
     delete t;
 }
@@ -637,6 +642,8 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     t->rowptr = t->col = t->w = t->crowptr = t->ccol = t->cw = t->coo_src = nullptr;
     t->eb_N = 0; t->eb_nseg = 0; t->eb_src = t->eb_dst = nullptr; t->eb_seg = nullptr;
     t->h_eb_seg = nullptr;
+    t->pr_hot = -1; t->pr_perm = t->pr_ccol = nullptr;
+    t->seg_head = nullptr; t->seg_nzrow = t->seg_chunk_rank = nullptr; t->seg_nnzrow = 0;
     g2_graph *g = new_handle(t);
     auto bail = [&](g2_status s) { g2_free_graph(g); return s; };
     cudaError_t e;

@@ -98,6 +98,15 @@ struct Topology {
     int32_t *eb_src, *eb_dst;
     int64_t *eb_seg;     // device [nseg+1]
     int64_t *h_eb_seg;   // host copy
+    // PageRank share-cache layout: vertex -> slot, CSC column ids as slots
+    int32_t pr_hot;
+    int32_t *pr_perm, *pr_ccol;
+    // segmented-sweep layout: row-head flags per arc, rows with in-arcs in
+    // order, head count before every 128-arc chunk
+    uint32_t *seg_head;
+    int32_t *seg_nzrow;
+    int32_t *seg_chunk_rank;
+    int32_t seg_nnzrow;
     DevGraph view() const {
         DevGraph d;
         d.n = n; d.m = m;

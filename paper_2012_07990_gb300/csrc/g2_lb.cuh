@@ -469,7 +469,13 @@ __device__ void lb_pull(const DevGraph &g, const int32_t *cand, int32_t ncand, c
                 }
             }
             count_arcs(ctr, cnt);
-            emit(out, v, code);
+            if (out.mode == OUT_BITMAP && !cand) {
+                // the warp's 32 destinations are one aligned bitmap word
+                unsigned mask = __ballot_sync(G2_FULL, code & 1);
+                if (lane == 0 && mask) atomicOr(&out.bitmap[base >> 5], mask);
+            } else {
+                emit(out, v, code);
+            }
         }
     } else if (G == 32) {
         const int gw = bid * kWarps + (tid >> 5);

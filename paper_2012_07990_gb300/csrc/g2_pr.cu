@@ -8,33 +8,41 @@
 //    Rows and arcs are merged into one sequence of n + m items (merge-path
 //    partitioning) cut into equal tiles, so every CTA gets the same share of
 //    row ends and arcs whatever the degree distribution; no atomics except
-//    for the few rows cut by a tile boundary.  The next round's per-source
-//    shares and the dangling mass are produced in the same pass.
+//    for the few rows cut by a tile boundary.  Each tile's arc slice and row
+//    ends arrive by TMA bulk copies, double-buffered against the previous
+//    tile's work.  The next round's per-source shares and the dangling mass
+//    are produced in the same pass.  Optionally the shares of the H
+//    highest-degree vertices are held in shared memory for the whole launch
+//    (a one-time layout step renumbers the CSC's column ids so that those
+//    vertices come first); the other gathers go through L1/L2.
 //  PULL + VERTEX_BASED / WM / CM: one thread / warp / CTA per destination.
 //  PUSH + any load balancing over the all-vertices frontier, including
 //    EDGE_ONLY with EdgeBlocking (Algorithms 1-2): arc-parallel atomic adds.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <numeric>
+#include <vector>
 
 #include "g2_host.h"
 #include "g2_lb.cuh"
 
 namespace g2 {
 
-constexpr int kPrIPT = 8;                 // merge items per thread per tile
-constexpr int kPrTile = kCta * kPrIPT;    // merge items per tile
-
 struct PrArgs {
     int32_t n;
     int32_t m;
+    int32_t tile;            // merged items per tile
     const int32_t *crowptr;
-    const int32_t *ccol;
+    const int32_t *ccol;     // column ids (renumbered when perm != null)
     const int32_t *rowptr;   // CSR offsets for out-degrees (null: symmetric, use CSC)
+    const int32_t *perm;     // vertex id -> share slot (null: identity)
     const int32_t *tile_r;   // merge-path row coordinate of every tile boundary
     int32_t ntiles;
-    const float *contrib;    // x_{t-1}[u] / outdeg(u)
+    int32_t hot;             // shares [0, hot) are cached in shared memory
+    const float *contrib;    // share slot -> x_{t-1}[u] / outdeg(u)
     float *contrib_next;
     float *x;                // written when write_x
     int write_x;
@@ -60,11 +68,11 @@ __device__ __forceinline__ int32_t merge_rows_global(const int32_t *a, int32_t n
     return (int32_t)lo;
 }
 
-__global__ void k_pr_tiles(const int32_t *crowptr, int32_t n, int32_t m, int32_t ntiles,
-                           int32_t *tile_r) {
+__global__ void k_pr_tiles(const int32_t *crowptr, int32_t n, int32_t m, int32_t tile,
+                           int32_t ntiles, int32_t *tile_r) {
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= ntiles;
          b += (int64_t)gridDim.x * blockDim.x) {
-        int64_t diag = b * kPrTile;
+        int64_t diag = b * tile;
         int64_t total = (int64_t)n + m;
         if (diag > total) diag = total;
         tile_r[b] = merge_rows_global(crowptr + 1, n, m, diag);
@@ -72,7 +80,7 @@ __global__ void k_pr_tiles(const int32_t *crowptr, int32_t n, int32_t m, int32_t
 }
 
 // rows cut by a tile boundary, each listed once (at its first cut)
-__global__ void k_pr_split_rows(const int32_t *crowptr, int32_t n, int32_t ntiles,
+__global__ void k_pr_split_rows(const int32_t *crowptr, int32_t n, int32_t tile, int32_t ntiles,
                                 const int32_t *tile_r, int32_t *list, int32_t *cnt) {
     int lane = threadIdx.x & 31;
     for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < ntiles;
@@ -82,10 +90,10 @@ __global__ void k_pr_split_rows(const int32_t *crowptr, int32_t n, int32_t ntile
         int32_t r = 0;
         if (b >= 1 && b < ntiles) {
             r = tile_r[b];
-            int64_t e = b * kPrTile - r;
+            int64_t e = b * tile - r;
             split = r < n && crowptr[r] < e;
             if (split && b >= 2 && tile_r[b - 1] == r) {
-                int64_t ep = (b - 1) * (int64_t)kPrTile - r;
+                int64_t ep = (b - 1) * (int64_t)tile - r;
                 if (crowptr[r] < ep) split = false;  // already cut at an earlier boundary
             }
         }
@@ -97,10 +105,11 @@ __device__ __forceinline__ void pr_finalize(const PrArgs &a, int32_t r, float y,
                                             int32_t in_end, float dterm, double &dsum) {
     float xr = a.base + a.damp * (y + dterm);
     int32_t od = a.rowptr ? a.rowptr[r + 1] - a.rowptr[r] : in_end - in_beg;
+    int32_t slot = a.perm ? a.perm[r] : r;
     if (od > 0) {
-        a.contrib_next[r] = xr / (float)od;
+        a.contrib_next[slot] = xr / (float)od;
     } else {
-        a.contrib_next[r] = 0.f;
+        a.contrib_next[slot] = 0.f;
         dsum += xr;
     }
     if (a.write_x) a.x[r] = xr;
@@ -126,8 +135,8 @@ struct PrTile {
 
 __device__ __forceinline__ PrTile pr_tile(const PrArgs &a, int32_t tile) {
     const int64_t total = (int64_t)a.n + a.m;
-    const int64_t d0 = (int64_t)tile * kPrTile;
-    const int64_t d1 = d0 + kPrTile < total ? d0 + kPrTile : total;
+    const int64_t d0 = (int64_t)tile * a.tile;
+    const int64_t d1 = d0 + a.tile < total ? d0 + a.tile : total;
     PrTile c;
     c.r0 = a.tile_r[tile];
     c.r1 = a.tile_r[tile + 1];
@@ -139,6 +148,8 @@ __device__ __forceinline__ PrTile pr_tile(const PrArgs &a, int32_t tile) {
 // Stage layout of one tile in shared memory: the arc slice [e0 & ~3, ...)
 // rounded to whole 16-byte chunks, then the row-end slice crowptr[(r0+1) & ~3
 // ...] likewise.  Both come in by TMA bulk copies counted on one mbarrier.
+// Rounding reads at most 3 + 4 elements past the slices; every device graph
+// array carries kPad spare elements for that.
 struct PrStage {
     int32_t ea, ne_al, ra, nr_al;
 };
@@ -152,8 +163,6 @@ __device__ __forceinline__ PrStage pr_stage(const PrTile &c) {
     return s;
 }
 
-constexpr int kPrBuf = kPrTile + 32;  // ints per stage (slices + rounding)
-
 __device__ __forceinline__ void pr_issue(const PrArgs &a, const PrTile &c, int32_t *buf,
                                          uint64_t *bar) {
     PrStage s = pr_stage(c);
@@ -162,10 +171,26 @@ __device__ __forceinline__ void pr_issue(const PrArgs &a, const PrTile &c, int32
     tma_load_1d(buf + s.ne_al, a.crowptr + s.ra, (uint32_t)s.nr_al * 4u, bar);
 }
 
+// shared-memory bytes of one launch configuration
+__host__ __device__ constexpr size_t pr_smem_bytes(int ipt, int hot) {
+    return (size_t)hot * 4                                  // hot shares
+           + 2 * ((size_t)kCta * ipt + 32) * 4              // two stages
+           + ((size_t)kCta * ipt + 4) * 4                   // row sums
+           + ((size_t)kCta * ipt + kCta * ipt / 32) * 4     // padded gathered shares
+           + 16;                                            // mbarriers
+}
+
+template <int IPT, bool HOT>
 __global__ void __launch_bounds__(kCta) k_pr_merge(PrArgs a, uint64_t limit_ns, int32_t *err) {
-    __shared__ __align__(16) int32_t buf[2][kPrBuf];
-    __shared__ float s_acc[kPrTile + 1];
-    __shared__ __align__(8) uint64_t bar[2];
+    constexpr int TILE = kCta * IPT;
+    constexpr int BUF = TILE + 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *s_hot = reinterpret_cast<float *>(smem);
+    int32_t *buf0 = reinterpret_cast<int32_t *>(smem + (size_t)a.hot * 4);
+    int32_t *buf1 = buf0 + BUF;
+    float *s_acc = reinterpret_cast<float *>(buf1 + BUF);
+    float *s_val = s_acc + TILE + 4;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(s_val + TILE + TILE / 32);
     const int tid = threadIdx.x, lane = tid & 31;
     const float dterm = (float)(*a.dprev * a.inv_n);
     double dsum = 0.0;
@@ -174,16 +199,19 @@ __global__ void __launch_bounds__(kCta) k_pr_merge(PrArgs a, uint64_t limit_ns, 
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
+    if (HOT)
+        for (int32_t i = tid; i < a.hot; i += kCta) s_hot[i] = __ldg(a.contrib + i);
     __syncthreads();
     int32_t tile = blockIdx.x;
-    if (tid == 0 && tile < a.ntiles) pr_issue(a, pr_tile(a, tile), buf[0], &bar[0]);
+    if (tid == 0 && tile < a.ntiles) pr_issue(a, pr_tile(a, tile), buf0, &bar[0]);
     uint32_t phase0 = 0, phase1 = 0;
     for (int s = 0; tile < a.ntiles; tile += gridDim.x, s ^= 1) {
+        int32_t *bufs = s ? buf1 : buf0;
         const PrTile c = pr_tile(a, tile);
         const int32_t next = tile + gridDim.x;
         // prefetch the next tile into the other stage (freed by the barrier
         // that ended the previous tile)
-        if (tid == 0 && next < a.ntiles) pr_issue(a, pr_tile(a, next), buf[s ^ 1], &bar[s ^ 1]);
+        if (tid == 0 && next < a.ntiles) pr_issue(a, pr_tile(a, next), s ? buf0 : buf1, &bar[s ^ 1]);
         const uint32_t ph = s ? phase1 : phase0;
         bool ok = mbar_wait_bounded(&bar[s], ph, limit_ns);
         if (s) phase1 ^= 1u;
@@ -197,17 +225,40 @@ __global__ void __launch_bounds__(kCta) k_pr_merge(PrArgs a, uint64_t limit_ns, 
             break;
         }
         const PrStage sg = pr_stage(c);
-        int32_t *scol = buf[s] + (c.e0 - sg.ea);                   // arc j of the tile
-        const int32_t *send = buf[s] + sg.ne_al + (c.r0 + 1 - sg.ra);  // end of row r0+i
+        const int32_t *scol = bufs + (c.e0 - sg.ea);                 // arc j of the tile
+        const int32_t *send = bufs + sg.ne_al + (c.r0 + 1 - sg.ra);  // end of row r0+i
         const int32_t nr = c.r1 - c.r0, ne = c.e1 - c.e0;
         const bool last_row_real = c.r1 < a.n;
         for (int32_t i = tid; i <= nr; i += kCta) s_acc[i] = 0.f;
+        // gather the shares of the tile's arcs with a strided assignment
+        // (consecutive threads, consecutive arcs: coalesced, no bank conflicts),
+        // IPT independent loads per thread, into a padded array (one spare
+        // word per 32) so the contiguous per-thread reads below hit distinct
+        // banks as well
+        {
+            float v[IPT];
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                int32_t j = tid + k * kCta;
+                float x = 0.f;
+                if (j < ne) {
+                    int32_t u = scol[j];
+                    x = (HOT && u < a.hot) ? s_hot[u] : __ldg(a.contrib + u);
+                }
+                v[k] = x;
+            }
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                int32_t j = tid + k * kCta;
+                if (j < ne) s_val[j + (j >> 5)] = v[k];
+            }
+        }
         // this thread's slice [dl, dl2) of the merged sequence
         const int32_t items = nr + ne;
-        int32_t dl = tid * kPrIPT;
+        int32_t dl = tid * IPT;
         if (dl > items) dl = items;
-        const int32_t dl2 = dl + kPrIPT < items ? dl + kPrIPT : items;
-        int32_t ri, ej, ej2;
+        const int32_t dl2 = dl + IPT < items ? dl + IPT : items;
+        int32_t ri, ej;
         {
             int32_t lo = dl - ne > 0 ? dl - ne : 0, hi = dl < nr ? dl : nr;
             while (lo < hi) {
@@ -217,34 +268,13 @@ __global__ void __launch_bounds__(kCta) k_pr_merge(PrArgs a, uint64_t limit_ns, 
             }
             ri = lo;
             ej = dl - lo;
-            lo = dl2 - ne > 0 ? dl2 - ne : 0;
-            hi = dl2 < nr ? dl2 : nr;
-            if (lo < ri) lo = ri;
-            while (lo < hi) {
-                int32_t mid = (lo + hi) >> 1;
-                if (send[mid] <= c.e0 + (dl2 - mid - 1)) lo = mid + 1;
-                else hi = mid;
-            }
-            ej2 = dl2 - lo;
         }
-        // gather the shares of this thread's arcs (independent loads), write
-        // them over the arc ids, which no other thread reads
-        {
-            const int32_t ne_t = ej2 - ej;
-            float v[kPrIPT];
-#pragma unroll
-            for (int k = 0; k < kPrIPT; ++k)
-                v[k] = k < ne_t ? __ldg(a.contrib + scol[ej + k]) : 0.f;
-#pragma unroll
-            for (int k = 0; k < kPrIPT; ++k)
-                if (k < ne_t) scol[ej + k] = __float_as_int(v[k]);
-        }
-        __syncthreads();  // s_acc zeroed everywhere before the adds
+        __syncthreads();  // s_acc zeroed and s_val filled before the adds
         int32_t row_end = (ri < nr || last_row_real) ? send[ri] : G2_INF32;
         float run = 0.f;
         for (int32_t k = dl; k < dl2; ++k) {
             if (c.e0 + ej < row_end) {
-                run += __int_as_float(scol[ej]);
+                run += s_val[ej + (ej >> 5)];
                 ++ej;
             } else {
                 if (run != 0.f) atomicAdd(&s_acc[ri], run);
@@ -299,14 +329,15 @@ __global__ void __launch_bounds__(kCta) k_pr_fixup(PrArgs a, const int32_t *rows
     block_add_double(dsum, a.dnext);
 }
 
-// x0 = 1/n: contrib0[u] = (1/n)/outdeg(u); D0 = (#vertices without out-arcs)/n
-__global__ void __launch_bounds__(kCta) k_pr_init(const int32_t *rowptr, int32_t n, float *contrib,
-                                                  double *d0, float *x, double inv_n) {
+// x0 = 1/n: contrib0[slot(u)] = (1/n)/outdeg(u); D0 = (#vertices without out-arcs)/n
+__global__ void __launch_bounds__(kCta) k_pr_init(const int32_t *rowptr, int32_t n,
+                                                  const int32_t *perm, float *contrib, double *d0,
+                                                  float *x, double inv_n) {
     double dsum = 0.0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
          u += (int64_t)gridDim.x * blockDim.x) {
         int32_t od = rowptr[u + 1] - rowptr[u];
-        contrib[u] = od > 0 ? (float)(inv_n / od) : 0.f;
+        contrib[perm ? perm[u] : u] = od > 0 ? (float)(inv_n / od) : 0.f;
         if (od == 0) dsum += inv_n;
         if (x) x[u] = (float)inv_n;
     }
@@ -334,16 +365,310 @@ __global__ void __launch_bounds__(kCta) k_pr_vertex(const int32_t *rowptr, int32
     block_add_double(dsum, dnext);
 }
 
-static int pr_blocks(const g2_graph *g) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pr_merge, kCta, 0) != cudaSuccess ||
-            b < 1)
-            b = 1;
-        per_sm = b;
+__global__ void k_remap_cols(const int32_t *ccol, const int32_t *perm, int32_t m, int32_t *out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = perm[ccol[e]];
+}
+
+// ------------------------------------------------ segmented arc sweep
+// A warp takes 128 consecutive CSC arcs (one int4 of column ids per lane),
+// gathers their shares, and sums them per row with a warp segmented scan
+// whose segment starts are precomputed row-head flags (bit e set iff arc e is
+// the first in-arc of its row).  Row ids come from the rank of each head:
+// the k-th head overall starts row nzrow[k].  Sums are added with
+// fire-and-forget reductions into y (zeroed again by the vertex pass), so no
+// block barrier or search is needed anywhere.
+constexpr int kSegArcs = 128;  // arcs per warp chunk
+
+__global__ void k_seg_heads(const int32_t *crowptr, int32_t n, uint32_t *head, int32_t *nz) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t b = crowptr[r], e = crowptr[r + 1];
+        nz[r] = e > b;
+        if (e > b) atomicOr(&head[b >> 5], 1u << (b & 31));
     }
-    return g->topo->sm_count * per_sm;
+}
+
+__global__ void k_seg_nzrow(const int32_t *nz, const int32_t *pos, int32_t n, int32_t *nzrow) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        if (nz[r]) nzrow[pos[r]] = (int32_t)r;
+}
+
+__global__ void k_seg_chunk_heads(const uint32_t *head, int64_t nchunks, int32_t *cnt) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x)
+        cnt[c] = __popc(head[4 * c]) + __popc(head[4 * c + 1]) + __popc(head[4 * c + 2]) +
+                 __popc(head[4 * c + 3]);
+}
+
+template <bool HOT>
+__device__ __forceinline__ float seg_gather(const float *contrib, const float *s_hot, int32_t hot,
+                                            int32_t u) {
+    return (HOT && u < hot) ? s_hot[u] : __ldg(contrib + u);
+}
+
+template <int CTA, bool HOT>
+__global__ void __launch_bounds__(CTA) k_pr_seg(const int32_t *pcol, const uint32_t *head,
+                                                const int32_t *chunk_rank, const int32_t *nzrow,
+                                                int32_t m, int64_t nchunks, const float *contrib,
+                                                int32_t hot, float *y) {
+    extern __shared__ float s_hot[];
+    if (HOT) {
+        for (int32_t i = threadIdx.x; i < hot; i += CTA) s_hot[i] = __ldg(contrib + i);
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * CTA + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * CTA) >> 5;
+    const int sh = (lane & 7) * 4;
+    const unsigned below = (1u << sh) - 1u;
+    // software pipeline: the next chunk's column ids and head words are
+    // loaded while this chunk's gathers are in flight
+    int4 nu4 = make_int4(0, 0, 0, 0);
+    uint4 nh = make_uint4(0, 0, 0, 0);
+    if (gw < nchunks) {
+        nu4 = reinterpret_cast<const int4 *>(pcol + gw * kSegArcs)[lane];
+        nh = reinterpret_cast<const uint4 *>(head)[gw];
+    }
+    for (int64_t c = gw; c < nchunks; c += nw) {
+        const int64_t b = c * kSegArcs;
+        const int4 u4 = nu4;
+        const uint32_t w0 = nh.x, w1 = nh.y, w2 = nh.z, w3 = nh.w;
+        if (c + nw < nchunks) {
+            nu4 = reinterpret_cast<const int4 *>(pcol + (c + nw) * kSegArcs)[lane];
+            nh = reinterpret_cast<const uint4 *>(head)[c + nw];
+        }
+        const int64_t a0 = b + 4 * lane;
+        float v0 = a0 + 0 < m ? seg_gather<HOT>(contrib, s_hot, hot, u4.x) : 0.f;
+        float v1 = a0 + 1 < m ? seg_gather<HOT>(contrib, s_hot, hot, u4.y) : 0.f;
+        float v2 = a0 + 2 < m ? seg_gather<HOT>(contrib, s_hot, hot, u4.z) : 0.f;
+        float v3 = a0 + 3 < m ? seg_gather<HOT>(contrib, s_hot, hot, u4.w) : 0.f;
+        const int wi = lane >> 3;
+        const uint32_t mine = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
+        const uint32_t hf = (mine >> sh) & 0xFu;
+        // heads before this lane in the chunk
+        int prefix = __popc(mine & below);
+        if (wi > 0) prefix += __popc(w0);
+        if (wi > 1) prefix += __popc(w1);
+        if (wi > 2) prefix += __popc(w2);
+        const int total_heads = __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3);
+        const int32_t base_rank = chunk_rank[c];
+        // lane-local pieces: A = arcs before the first head, inner complete
+        // segments, T = arcs from the last head on
+        float vals[4] = {v0, v1, v2, v3};
+        float A = 0.f, run = 0.f;
+        int seen = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if ((hf >> k) & 1u) {
+                if (seen == 0) {
+                    A = run;
+                } else if (run != 0.f) {
+                    // complete segment inside this lane: its head is the (seen-1)-th
+                    atomicAdd(y + nzrow[base_rank + prefix + seen - 1], run);
+                }
+                run = 0.f;
+                ++seen;
+            }
+            run += vals[k];
+        }
+        if (seen == 0) A = run;
+        const bool has_head = seen > 0;
+        const float T = has_head ? run : 0.f;
+        // segmented inclusive scan over lanes: q = T at a headed lane, else
+        // q(previous lane) + A
+        float q = has_head ? T : A;
+        bool f = has_head;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            float qo = __shfl_up_sync(G2_FULL, q, d);
+            bool fo = __shfl_up_sync(G2_FULL, f, d);
+            if (lane >= d && !f) {
+                q += qo;
+                f = fo;
+            }
+        }
+        float qprev = __shfl_up_sync(G2_FULL, q, 1);
+        if (lane == 0) qprev = 0.f;
+        if (has_head) {
+            // the segment that ends just before this lane's first head
+            float tot = qprev + A;
+            int32_t rk = base_rank + prefix - 1;
+            if (tot != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], tot);
+        }
+        if (lane == 31) {
+            // the segment that runs to the end of the chunk (may continue)
+            int32_t rk = base_rank + total_heads - 1;
+            if (q != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], q);
+        }
+    }
+}
+
+// vertex pass after a segmented sweep: x, next shares, next D; y back to zero
+__global__ void __launch_bounds__(kCta) k_pr_seg_vertex(const int32_t *rowptr, int32_t n,
+                                                        const int32_t *perm, float *y,
+                                                        float *contrib_next, float *x, int write_x,
+                                                        const double *dprev, double *dnext,
+                                                        float base, float damp, double inv_n) {
+    const float dterm = (float)(*dprev * inv_n);
+    double dsum = 0.0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        float xr = base + damp * (y[v] + dterm);
+        y[v] = 0.f;
+        int32_t od = rowptr[v + 1] - rowptr[v];
+        int32_t slot = perm ? perm[v] : (int32_t)v;
+        if (od > 0) contrib_next[slot] = xr / (float)od;
+        else {
+            contrib_next[slot] = 0.f;
+            dsum += xr;
+        }
+        if (write_x) x[v] = xr;
+    }
+    block_add_double(dsum, dnext);
+}
+
+// ---------------------------------------------------------------- host side
+struct PrCfg {
+    int merge;      // 1: merge-path tile kernel, 0: segmented arc sweep
+    int ipt;        // merge kernel: 8 or 16 items per thread
+    int hot;        // cached shares (0 = none)
+    int per_sm;     // merge kernel: resident CTAs per SM (0 = as many as fit)
+    int cta;        // segmented sweep: 512 or 1024 threads per CTA
+};
+
+// Defaults (measured on GB300 with RMAT-22): segmented sweep, 1024-thread
+// CTAs, shares of the 16,384 highest-degree vertices cached in shared memory
+// (64 KB per CTA, two CTAs per SM).  The environment overrides them for
+// tuning sweeps.
+static PrCfg pr_config(const g2_graph *g) {
+    PrCfg c{0, 8, 16384, 0, 1024};
+    if (const char *e = getenv("G2_PR_KERNEL")) c.merge = strcmp(e, "merge") == 0;
+    if (const char *e = getenv("G2_PR_IPT")) c.ipt = atoi(e) == 16 ? 16 : 8;
+    if (const char *e = getenv("G2_PR_HOT")) c.hot = std::max(0, atoi(e));
+    if (const char *e = getenv("G2_PR_CTAS_PER_SM")) c.per_sm = std::max(0, atoi(e));
+    if (const char *e = getenv("G2_PR_SEG_CTA")) c.cta = atoi(e) == 512 ? 512 : 1024;
+    c.hot = std::min<int64_t>(c.hot, g->topo->n);
+    c.hot &= ~3;  // keeps the stage buffers 16-byte aligned
+    return c;
+}
+
+// Renumbering for the shared-memory share cache: the `hot` vertices of highest
+// degree (ties to the lower id) get slots 0..hot-1 in that order, the others
+// follow in id order.  perm and the renumbered column ids are built once and
+// kept with the topology.
+static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, const int32_t **perm,
+                                      const int32_t **ccol) {
+    Topology *t = g->topo;
+    if (t->pr_hot == hot && t->pr_perm) {
+        *perm = t->pr_perm;
+        *ccol = t->pr_ccol;
+        return G2_OK;
+    }
+    const int32_t n = t->n, m = t->m;
+    std::vector<int32_t> rp((size_t)n + 1);
+    G2_CK(cudaMemcpyAsync(rp.data(), t->rowptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, st));
+    G2_CK(cudaStreamSynchronize(st));
+    std::vector<int32_t> order((size_t)n);
+    std::iota(order.begin(), order.end(), 0);
+    auto deg = [&](int32_t v) { return rp[v + 1] - rp[v]; };
+    std::partial_sort(order.begin(), order.begin() + hot, order.end(), [&](int32_t a, int32_t b) {
+        int32_t da = deg(a), db = deg(b);
+        return da != db ? da > db : a < b;
+    });
+    std::vector<int32_t> perm_h((size_t)n, -1);
+    for (int32_t i = 0; i < hot; ++i) perm_h[order[i]] = i;
+    int32_t next = hot;
+    for (int32_t v = 0; v < n; ++v)
+        if (perm_h[v] < 0) perm_h[v] = next++;
+    if (t->pr_perm) cudaFree(t->pr_perm);
+    if (t->pr_ccol) cudaFree(t->pr_ccol);
+    t->pr_perm = t->pr_ccol = nullptr;
+    G2_CK(cudaMalloc(&t->pr_perm, (size_t)std::max(n, 1) * 4));
+    G2_CK(cudaMalloc(&t->pr_ccol, ((size_t)std::max(m, 1) + kPad) * 4));
+    G2_CK(cudaMemsetAsync(t->pr_ccol, 0, ((size_t)std::max(m, 1) + kPad) * 4, st));
+    G2_CK(cudaMemcpyAsync(t->pr_perm, perm_h.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
+    if (m > 0)
+        k_remap_cols<<<grid_for(g, m, kCta), kCta, 0, st>>>(t->ccol, t->pr_perm, m, t->pr_ccol);
+    G2_CK(cudaGetLastError());
+    G2_CK(cudaStreamSynchronize(st));
+    t->pr_hot = hot;
+    *perm = t->pr_perm;
+    *ccol = t->pr_ccol;
+    return G2_OK;
+}
+
+static g2_status ensure_seg_layout(g2_graph *g, cudaStream_t st) {
+    Topology *t = g->topo;
+    if (t->seg_head) return G2_OK;
+    const int32_t n = t->n, m = t->m;
+    const size_t words = ((size_t)m + 31) / 32 + 8;
+    const int64_t nchunks = ((int64_t)m + kSegArcs - 1) / kSegArcs;
+    int32_t *nz, *pos, *ccount;
+    G2_TRY(ws(g, B_I0, (size_t)n + 1, &nz));
+    G2_TRY(ws(g, B_I1, (size_t)n + 1, &pos));
+    G2_TRY(ws(g, B_TWC_S, (size_t)nchunks + 1, &ccount));
+    G2_CK(cudaMalloc(&t->seg_head, words * 4));
+    G2_CK(cudaMemsetAsync(t->seg_head, 0, words * 4, st));
+    k_seg_heads<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->crowptr, n, t->seg_head, nz);
+    G2_TRY(exclusive_scan_i32(g, nz, pos, n, st));
+    int32_t nnz = 0;
+    G2_CK(cudaMemcpyAsync(&nnz, pos + n, 4, cudaMemcpyDeviceToHost, st));
+    G2_CK(cudaStreamSynchronize(st));
+    G2_CK(cudaMalloc(&t->seg_nzrow, ((size_t)nnz + 1) * 4));
+    k_seg_nzrow<<<grid_for(g, n, kCta), kCta, 0, st>>>(nz, pos, n, t->seg_nzrow);
+    G2_CK(cudaMalloc(&t->seg_chunk_rank, ((size_t)nchunks + 1) * 4));
+    if (nchunks > 0) {
+        k_seg_chunk_heads<<<grid_for(g, nchunks, kCta), kCta, 0, st>>>(t->seg_head, nchunks, ccount);
+        G2_TRY(exclusive_scan_i32(g, ccount, t->seg_chunk_rank, (int32_t)nchunks, st));
+    }
+    G2_CK(cudaGetLastError());
+    G2_CK(cudaStreamSynchronize(st));
+    t->seg_nnzrow = nnz;
+    return G2_OK;
+}
+
+template <int CTA, bool HOT>
+static g2_status launch_pr_seg(g2_graph *g, const int32_t *pcol, int32_t hot, const float *contrib,
+                               float *y, cudaStream_t st) {
+    Topology *t = g->topo;
+    const int64_t nchunks = ((int64_t)t->m + kSegArcs - 1) / kSegArcs;
+    if (nchunks == 0) return G2_OK;
+    const size_t smem = HOT ? (size_t)hot * 4 : 0;
+    auto kern = k_pr_seg<CTA, HOT>;
+    if (smem > 48 * 1024)
+        G2_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int b = 0;
+    G2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, CTA, smem));
+    if (b < 1) return fail(G2_EUNSUPPORTED, "PageRank sweep kernel does not fit on an SM");
+    int64_t want = (nchunks * 32 + CTA - 1) / CTA;
+    int grid = (int)std::min<int64_t>(want, (int64_t)b * t->sm_count);
+    KTime kt;
+    ktime_begin(kt, "pr_merge", st);
+    kern<<<grid, CTA, smem, st>>>(pcol, t->seg_head, t->seg_chunk_rank, t->seg_nzrow, t->m, nchunks,
+                                  contrib, hot, y);
+    ktime_end(kt, st);
+    return G2_OK;
+}
+
+template <int IPT, bool HOT>
+static g2_status launch_pr_merge(g2_graph *g, const PrArgs &a, int per_sm, cudaStream_t st,
+                                 int32_t *d_err) {
+    const size_t smem = pr_smem_bytes(IPT, a.hot);
+    auto kern = k_pr_merge<IPT, HOT>;
+    G2_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int b = 0;
+    G2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kCta, smem));
+    if (b < 1) return fail(G2_EUNSUPPORTED, "PageRank tile kernel does not fit on an SM");
+    if (per_sm > 0 && per_sm < b) b = per_sm;
+    int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)b * g->topo->sm_count);
+    KTime kt;
+    ktime_begin(kt, "pr_merge", st);
+    kern<<<grid, kCta, smem, st>>>(a, 2000000000ULL, d_err);
+    ktime_end(kt, st);
+    return G2_OK;
 }
 
 g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, const g2_hybrid &h,
@@ -359,9 +684,6 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
     double *dd;
     G2_TRY(ws(g, B_D1, 4, &dd));
     G2_CK(cudaMemsetAsync(dd, 0, 4 * sizeof(double), st));
-    k_pr_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->rowptr, n, cbuf[0], dd, rank, inv_n);
-    stats().launches += 1;
-    if (iters <= 0) return G2_OK;
     const g2_schedule &s = h.s1;  // one schedule for every round (the frontier is always all vertices)
     const float base = (float)((1.0 - damping) * inv_n);
     const bool merge = tuned_default || (s.direction == G2_PULL && s.load_balance == G2_LB_EDGE_ONLY);
@@ -369,28 +691,62 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
         G2_TRY(check_schedule(g, s, K_PR, true));
         if (s.kernel_fusion) return fail(G2_EUNSUPPORTED, "PageRank has no fused variant");
     }
+    PrCfg cfg = pr_config(g);
+    const int32_t *perm = nullptr, *ccol = t->ccol;
+    if (merge && cfg.hot > 0) G2_TRY(ensure_pr_hot_layout(g, cfg.hot, st, &perm, &ccol));
+    k_pr_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->rowptr, n, perm, cbuf[0], dd, rank, inv_n);
+    stats().launches += 1;
+    if (iters <= 0) return G2_OK;
+    if (merge && !cfg.merge) {
+        G2_TRY(ensure_seg_layout(g, st));
+        const int32_t hot = perm ? cfg.hot : 0;
+        G2_CK(cudaMemsetAsync(acc, 0, (size_t)(n + 1) * 4, st));
+        for (int32_t it = 0; it < iters; ++it) {
+            const float *c0 = cbuf[it & 1];
+            float *c1 = cbuf[(it + 1) & 1];
+            G2_CK(cudaMemsetAsync(dd + ((it + 1) & 1), 0, sizeof(double), st));
+            if (cfg.cta == 512) {
+                if (hot) G2_TRY((launch_pr_seg<512, true>(g, ccol, hot, c0, acc, st)));
+                else G2_TRY((launch_pr_seg<512, false>(g, ccol, hot, c0, acc, st)));
+            } else {
+                if (hot) G2_TRY((launch_pr_seg<1024, true>(g, ccol, hot, c0, acc, st)));
+                else G2_TRY((launch_pr_seg<1024, false>(g, ccol, hot, c0, acc, st)));
+            }
+            k_pr_seg_vertex<<<grid_for(g, n, kCta), kCta, 0, st>>>(
+                t->rowptr, n, perm, acc, c1, rank, it == iters - 1, dd + (it & 1),
+                dd + ((it + 1) & 1), base, damping, inv_n);
+            stats().launches += 2;
+            stats().iterations++;
+            stats().pull_rounds++;
+        }
+        G2_CK(cudaGetLastError());
+        return G2_OK;
+    }
     if (merge) {
+        const int32_t tile = kCta * cfg.ipt;
         const int64_t total = (int64_t)n + t->m;
-        const int32_t ntiles = (int32_t)((total + kPrTile - 1) / kPrTile);
+        const int32_t ntiles = (int32_t)((total + tile - 1) / tile);
         int32_t *tile_r, *split, *ctrs = d_err - 62;
         G2_TRY(ws(g, B_SCAN, (size_t)ntiles + 2, &tile_r));
         G2_TRY(ws(g, B_TWC_M, (size_t)ntiles + 2, &split));
         G2_CK(cudaMemsetAsync(acc, 0, (size_t)(n + 1) * 4, st));
         G2_CK(cudaMemsetAsync(ctrs + 10, 0, 4, st));
-        k_pr_tiles<<<grid_for(g, ntiles + 1, kCta), kCta, 0, st>>>(t->crowptr, n, t->m, ntiles,
+        k_pr_tiles<<<grid_for(g, ntiles + 1, kCta), kCta, 0, st>>>(t->crowptr, n, t->m, tile, ntiles,
                                                                    tile_r);
-        k_pr_split_rows<<<grid_for(g, ntiles, kCta), kCta, 0, st>>>(t->crowptr, n, ntiles, tile_r,
-                                                                    split, ctrs + 10);
+        k_pr_split_rows<<<grid_for(g, ntiles, kCta), kCta, 0, st>>>(t->crowptr, n, tile, ntiles,
+                                                                    tile_r, split, ctrs + 10);
         stats().launches += 2;
-        const int grid = std::min<int64_t>(ntiles, pr_blocks(g));
         PrArgs a;
         a.n = n;
         a.m = t->m;
+        a.tile = tile;
         a.crowptr = t->crowptr;
-        a.ccol = t->ccol;
+        a.ccol = ccol;
         a.rowptr = t->symmetric ? nullptr : t->rowptr;
+        a.perm = perm;
         a.tile_r = tile_r;
         a.ntiles = ntiles;
+        a.hot = perm ? cfg.hot : 0;
         a.acc = acc;
         a.base = base;
         a.damp = damping;
@@ -403,10 +759,13 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
             a.dprev = dd + (it & 1);
             a.dnext = dd + ((it + 1) & 1);
             G2_CK(cudaMemsetAsync(dd + ((it + 1) & 1), 0, sizeof(double), st));
-            KTime kt;
-            ktime_begin(kt, "pr_merge", st);
-            k_pr_merge<<<grid, kCta, 0, st>>>(a, 2000000000ULL, d_err);
-            ktime_end(kt, st);
+            if (cfg.ipt == 16) {
+                if (a.hot) G2_TRY((launch_pr_merge<16, true>(g, a, cfg.per_sm, st, d_err)));
+                else G2_TRY((launch_pr_merge<16, false>(g, a, cfg.per_sm, st, d_err)));
+            } else {
+                if (a.hot) G2_TRY((launch_pr_merge<8, true>(g, a, cfg.per_sm, st, d_err)));
+                else G2_TRY((launch_pr_merge<8, false>(g, a, cfg.per_sm, st, d_err)));
+            }
             k_pr_fixup<<<(ntiles + kCta) / kCta, kCta, 0, st>>>(a, split, ctrs + 10);
             stats().launches += 2;
             stats().iterations++;

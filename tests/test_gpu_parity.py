@@ -237,6 +237,26 @@ def test_pagerank(g2, rmat14, grid):
             assert l1 <= PR_L1, (g.name, name, l1)
 
 
+@pytest.mark.parametrize("kernel,ipt,cta", [("merge", "8", "1024"), ("merge", "16", "1024"),
+                                            ("seg", "8", "512"), ("seg", "8", "1024")])
+@pytest.mark.parametrize("hot", ["0", "4", "1024", "100000"])
+def test_pagerank_tile_configs(g2, rmat14, grid, monkeypatch, kernel, ipt, cta, hot):
+    """The arc-balanced round kernels under every tuning knob: merge-path
+    tiles (items per thread, one resident CTA per SM) or the segmented warp
+    sweep (CTA size), each with and without the shared-memory share cache
+    (renumbered columns)."""
+    monkeypatch.setenv("G2_PR_KERNEL", kernel)
+    monkeypatch.setenv("G2_PR_IPT", ipt)
+    monkeypatch.setenv("G2_PR_SEG_CTA", cta)
+    monkeypatch.setenv("G2_PR_HOT", hot)
+    monkeypatch.setenv("G2_PR_CTAS_PER_SM", "1")
+    for g in (rmat14, grid, gg.gnp(300, 0.02, 9, symmetric=False)):
+        ref = oracle.pagerank_graph(g, 0.85, 20)
+        rank = dev(g.n, torch.float32)
+        g2.g2_pagerank(g2.load_graph(g), 0.85, 20, rank)
+        assert np.abs(host(rank).astype(np.float64) - ref).sum() <= PR_L1, (g.name, ipt, hot)
+
+
 def test_pagerank_iteration_counts(g2, rmat14):
     dg = g2.load_graph(rmat14)
     for iters in (0, 1, 2, 7):
