@@ -390,8 +390,33 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_profile_case(args):
+    """A short run of one algorithm for profilers: load RMAT at --scale, run
+    the algorithm --steps times with the tuned schedule, print a checksum."""
+    import torch
+    from paper_2012_07990_gb300 import build_native
+    build_native.build()
+    from paper_2012_07990_gb300 import g2
+    G = make_graph(args.scale)
+    dg = g2.load_graph(G)
+    src = G.max_degree_vertex()
+    out = torch.empty(G.n, dtype=torch.float32 if args.profile_case == "pr" else torch.int32,
+                      device="cuda")
+    for _ in range(args.steps):
+        if args.profile_case == "pr":
+            g2.g2_pagerank(dg, DAMPING, PR_ITERS, out)
+        elif args.profile_case == "bfs":
+            g2.g2_bfs(dg, src, out, None, None)
+        else:
+            g2.g2_cc(dg, out, None)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "scale": args.scale, "n": G.n, "m": G.m,
+                      "checksum": float(out.double().sum().item())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", choices=["pr", "bfs", "cc"], default=None)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -401,6 +426,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
