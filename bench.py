@@ -195,7 +195,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    g2.g2_kernel_time("pr_merge", reset=True)
+    g2.g2_kernel_time("pr_round", reset=True)
     g2.g2_set_kernel_timing(True)
     launches["n"] = 0
     if ws > 1:
@@ -214,7 +214,7 @@ def run_ours(args):
     g2.g2_set_kernel_timing(False)
     clk = clocks.stop()
     total_ms = e0.elapsed_time(e1)
-    pr_ms_total, pr_launches = g2.g2_kernel_time("pr_merge", reset=True)
+    pr_ms_total, pr_launches = g2.g2_kernel_time("pr_round", reset=True)
     if ws > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -222,13 +222,15 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = ws * edges_per_step * args.steps / (total_ms * 1e-3) / 1e9
 
-    # roofline of the dominant kernel: the PageRank round (arc-balanced CSC sweep)
+    # roofline of the dominant kernel: the PageRank arc sweep k_pr_seg (PULL +
+    # EDGE_ONLY), algorithmic bytes per launch = 4 m (CSC column ids) + 4 n
+    # (each vertex's share read once) + 4 n (row sums written)
     peak, peak_kind = read_peaks()
-    alg_bytes = 4 * m + 12 * n + 4 + 4 * n / PR_ITERS
+    alg_bytes = 4 * m + 8 * n
     avg_launch_ms = pr_ms_total / max(pr_launches, 1)
     achieved = alg_bytes / (avg_launch_ms * 1e-3) / 1e9
-    traffic = read_traffic("pr_merge", G)
-    roofline = {"kernel": "k_pr_merge (PageRank round, PULL + EDGE_ONLY)", "bound": "hbm",
+    traffic = read_traffic("pr_round", G)
+    roofline = {"kernel": "k_pr_seg (PageRank round: segmented CSC arc sweep)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_launch_ms * 1e3, 2),
@@ -322,8 +324,9 @@ def read_traffic(kernel: str, G):
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if h != d["source_sha256_16"]:
             return None
-        per_unit = d["dram_bytes_per_launch"] / d["units_per_launch"]
-        return int(per_unit * (4 * G.m + 12 * G.n))
+        # traffic grows with the arcs swept: scale the captured case by m
+        per_arc = d["dram_bytes_per_launch"] / d["arcs_per_launch"]
+        return int(per_arc * G.m)
     except Exception:
         return None
 

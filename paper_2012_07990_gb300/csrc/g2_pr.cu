@@ -646,7 +646,7 @@ static g2_status launch_pr_seg(g2_graph *g, const int32_t *pcol, int32_t hot, co
     int64_t want = (nchunks * 32 + CTA - 1) / CTA;
     int grid = (int)std::min<int64_t>(want, (int64_t)b * t->sm_count);
     KTime kt;
-    ktime_begin(kt, "pr_merge", st);
+    ktime_begin(kt, "pr_round", st);
     kern<<<grid, CTA, smem, st>>>(pcol, t->seg_head, t->seg_chunk_rank, t->seg_nzrow, t->m, nchunks,
                                   contrib, hot, y);
     ktime_end(kt, st);
@@ -665,7 +665,7 @@ static g2_status launch_pr_merge(g2_graph *g, const PrArgs &a, int per_sm, cudaS
     if (per_sm > 0 && per_sm < b) b = per_sm;
     int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)b * g->topo->sm_count);
     KTime kt;
-    ktime_begin(kt, "pr_merge", st);
+    ktime_begin(kt, "pr_round", st);
     kern<<<grid, kCta, smem, st>>>(a, 2000000000ULL, d_err);
     ktime_end(kt, st);
     return G2_OK;
@@ -694,7 +694,10 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
     PrCfg cfg = pr_config(g);
     const int32_t *perm = nullptr, *ccol = t->ccol;
     if (merge && cfg.hot > 0) G2_TRY(ensure_pr_hot_layout(g, cfg.hot, st, &perm, &ccol));
-    k_pr_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->rowptr, n, perm, cbuf[0], dd, rank, inv_n);
+    // vertex passes end with one fp64 atomic per CTA on a single address, and
+    // same-address atomics serialise: few CTAs, each striding over many vertices
+    const int vgrid = (int)std::min<int64_t>((n + kCta - 1) / kCta, (int64_t)t->sm_count * 2);
+    k_pr_init<<<vgrid, kCta, 0, st>>>(t->rowptr, n, perm, cbuf[0], dd, rank, inv_n);
     stats().launches += 1;
     if (iters <= 0) return G2_OK;
     if (merge && !cfg.merge) {
@@ -712,7 +715,7 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
                 if (hot) G2_TRY((launch_pr_seg<1024, true>(g, ccol, hot, c0, acc, st)));
                 else G2_TRY((launch_pr_seg<1024, false>(g, ccol, hot, c0, acc, st)));
             }
-            k_pr_seg_vertex<<<grid_for(g, n, kCta), kCta, 0, st>>>(
+            k_pr_seg_vertex<<<vgrid, kCta, 0, st>>>(
                 t->rowptr, n, perm, acc, c1, rank, it == iters - 1, dd + (it & 1),
                 dd + ((it + 1) & 1), base, damping, inv_n);
             stats().launches += 2;
@@ -788,7 +791,7 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
         G2_CK(cudaMemsetAsync(acc, 0, (size_t)n * 4, st));
         G2_CK(cudaMemsetAsync(dd + ((it + 1) & 1), 0, sizeof(double), st));
         G2_TRY(apply_round(g, s, a, all, none, st));
-        k_pr_vertex<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->rowptr, n, acc, cbuf[(it + 1) & 1],
+        k_pr_vertex<<<vgrid, kCta, 0, st>>>(t->rowptr, n, acc, cbuf[(it + 1) & 1],
                                                            rank, dd + (it & 1), dd + ((it + 1) & 1),
                                                            base, damping, inv_n);
         stats().launches += 1;
