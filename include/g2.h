@@ -264,6 +264,28 @@ g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *dep
 g2_status g2_sssp_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t delta,
                         int32_t *dist, const g2_hybrid *sched, void *stream);
 
+/* g2_bfs_csr_static — BFS that allocates no device memory (the paper has no
+ * counterpart: this entry point exists for callers that cannot allocate).
+ * For callers that cannot call cudaMalloc, e.g. code running inside another
+ * runtime that has reserved the device memory for its own pool, or latency-
+ * bound code that cannot afford the device synchronisation allocation may
+ * cause.  The caller passes everything in its own memory:
+ *   n, m            vertex count (1 <= n <= 1048576) and arc count (< 2^31)
+ *   rowptr, col     the graph as a device CSR (int32[n+1], int32[m]); it is
+ *                   read, never copied or validated
+ *   src             source vertex
+ *   depth           int32[n] device output, as g2_bfs
+ *   parent          int32[n] device output or NULL, as g2_bfs
+ * Scratch (two frontier queues, counters, grid-barrier and error words) is a
+ * fixed array of 8 MiB inside the library that every GPU which loads the
+ * library holds until the process exits; n above its capacity returns
+ * G2_EINVAL.  The first call on a device resolves that array's device address
+ * (make that first call before any stream capture).  All calls share the one
+ * array, so calls that overlap on the GPU (two streams, or two threads) race
+ * and must be serialised by the caller.  Returns after completion. */
+g2_status g2_bfs_csr_static(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *col,
+                            int32_t src, int32_t *depth, int32_t *parent, void *stream);
+
 /* ----------------------------------------------------------- diagnostics */
 /* Counters of the last algorithm call made on this thread. */
 typedef struct {

@@ -92,6 +92,7 @@ _SIGS = {
     "g2_set_count_arcs": [I32],
     "g2_last_error": [],
     "g2_selftest_wait_timeout": [I64, P],
+    "g2_bfs_csr_static": [I32, I64, P, P, I32, P, P, P],
     "g2_set_kernel_timing": [I32],
     "g2_kernel_time": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I32],
     "g2_version": [],
@@ -305,6 +306,14 @@ def g2_sssp_batch(g: Graph, srcs, delta: int, dist, sched=None, stream=None):
     s = np.ascontiguousarray(srcs, dtype=np.int32)
     _check(_lib.g2_sssp_batch(g.handle, _ptr(s), int(s.size), int(delta), _ptr(dist),
                               _sched(sched), _stream(stream)), "g2_sssp_batch")
+
+
+def g2_bfs_csr_static(n: int, rowptr, col, src: int, depth, parent=None, stream=None):
+    """BFS that allocates no device memory: rowptr/col are the caller's device
+    CSR (torch int32 CUDA tensors), depth/parent the caller's outputs; the
+    library's fixed scratch holds the frontiers (n <= 1,048,576)."""
+    _check(_lib.g2_bfs_csr_static(int(n), int(col.numel()), _ptr(rowptr), _ptr(col), int(src),
+                                  _ptr(depth), _ptr(parent), _stream(stream)), "g2_bfs_csr_static")
 
 
 def g2_last_stats() -> dict:
