@@ -506,28 +506,84 @@ __global__ void __launch_bounds__(CTA) k_pr_seg(const int32_t *pcol, const uint3
     }
 }
 
-// vertex pass after a segmented sweep: x, next shares, next D; y back to zero
+// The dangling mass D is accumulated in kDSlots slots (one per 128-byte line)
+// instead of one word, so the per-CTA atomics of a pass spread over many L2
+// lines instead of serialising on one address; readers add the slots up.
+constexpr int kDSlots = 64;
+constexpr int kDStride = 16;  // doubles between slots
+
+__device__ __forceinline__ float pr_dterm(const double *d, double inv_n) {
+    __shared__ float s_dterm;
+    if (threadIdx.x < 32) {
+        double v = d[threadIdx.x * kDStride] + d[(threadIdx.x + 32) * kDStride];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(G2_FULL, v, o);
+        if (threadIdx.x == 0) s_dterm = (float)(v * inv_n);
+    }
+    __syncthreads();
+    return s_dterm;
+}
+
+// vertex pass after a segmented sweep: x, next shares, next D; y back to zero.
+// Four consecutive vertices per thread with 16-byte loads, every vertex in
+// its own thread group, so the pass has the memory parallelism to stream.
 __global__ void __launch_bounds__(kCta) k_pr_seg_vertex(const int32_t *rowptr, int32_t n,
                                                         const int32_t *perm, float *y,
                                                         float *contrib_next, float *x, int write_x,
                                                         const double *dprev, double *dnext,
                                                         float base, float damp, double inv_n) {
-    const float dterm = (float)(*dprev * inv_n);
+    const float dterm = pr_dterm(dprev, inv_n);
     double dsum = 0.0;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        float xr = base + damp * (y[v] + dterm);
-        y[v] = 0.f;
-        int32_t od = rowptr[v + 1] - rowptr[v];
-        int32_t slot = perm ? perm[v] : (int32_t)v;
-        if (od > 0) contrib_next[slot] = xr / (float)od;
-        else {
-            contrib_next[slot] = 0.f;
-            dsum += xr;
+    const int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (v0 < n) {
+        float yv[4];
+        int32_t rp[5], sl[4];
+        if (v0 + 4 <= n) {
+            float4 y4 = *reinterpret_cast<const float4 *>(y + v0);
+            int4 r4 = __ldg(reinterpret_cast<const int4 *>(rowptr + v0));
+            yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
+            rp[0] = r4.x; rp[1] = r4.y; rp[2] = r4.z; rp[3] = r4.w;
+            rp[4] = __ldg(rowptr + v0 + 4);
+            if (perm) {
+                int4 p4 = __ldg(reinterpret_cast<const int4 *>(perm + v0));
+                sl[0] = p4.x; sl[1] = p4.y; sl[2] = p4.z; sl[3] = p4.w;
+            } else {
+                for (int k = 0; k < 4; ++k) sl[k] = (int32_t)(v0 + k);
+            }
+            *reinterpret_cast<float4 *>(y + v0) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            for (int k = 0; k < 4; ++k) {
+                bool in = v0 + k < n;
+                yv[k] = in ? y[v0 + k] : 0.f;
+                rp[k] = in ? rowptr[v0 + k] : 0;
+                sl[k] = in ? (perm ? perm[v0 + k] : (int32_t)(v0 + k)) : 0;
+                if (in) y[v0 + k] = 0.f;
+            }
+            rp[4] = 0;
+            for (int k = 0; k < 4; ++k)
+                if (v0 + k < n) rp[k + 1] = rowptr[v0 + k + 1];
         }
-        if (write_x) x[v] = xr;
+        float xs[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (v0 + k >= n) break;
+            float xr = base + damp * (yv[k] + dterm);
+            int32_t od = rp[k + 1] - rp[k];
+            if (od > 0) contrib_next[sl[k]] = xr / (float)od;
+            else {
+                contrib_next[sl[k]] = 0.f;
+                dsum += xr;
+            }
+            xs[k] = xr;
+        }
+        if (write_x) {
+            // x is the caller's array: vector stores only when 16-byte aligned
+            if (v0 + 4 <= n && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0))
+                *reinterpret_cast<float4 *>(x + v0) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            else
+                for (int k = 0; k < 4 && v0 + k < n; ++k) x[v0 + k] = xs[k];
+        }
     }
-    block_add_double(dsum, dnext);
+    block_add_double(dsum, dnext + (blockIdx.x % kDSlots) * kDStride);
 }
 
 // ---------------------------------------------------------------- host side
@@ -681,9 +737,13 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
     G2_TRY(ws(g, B_F0, (size_t)n, &cbuf[0]));
     G2_TRY(ws(g, B_F1, (size_t)n, &cbuf[1]));
     G2_TRY(ws(g, B_F2, (size_t)n + 1, &acc));
+    // D accumulators: dd[0], dd[1] for the merge and generic paths; two
+    // regions of kDSlots slots (dd[0..R), dd[R..2R)) for the segmented sweep,
+    // whose region A holds D0 in its slot 0 (= dd[0])
+    constexpr size_t R = (size_t)kDSlots * kDStride;
     double *dd;
-    G2_TRY(ws(g, B_D1, 4, &dd));
-    G2_CK(cudaMemsetAsync(dd, 0, 4 * sizeof(double), st));
+    G2_TRY(ws(g, B_D1, 2 * R, &dd));
+    G2_CK(cudaMemsetAsync(dd, 0, 2 * R * sizeof(double), st));
     const g2_schedule &s = h.s1;  // one schedule for every round (the frontier is always all vertices)
     const float base = (float)((1.0 - damping) * inv_n);
     const bool merge = tuned_default || (s.direction == G2_PULL && s.load_balance == G2_LB_EDGE_ONLY);
@@ -704,10 +764,12 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
         G2_TRY(ensure_seg_layout(g, st));
         const int32_t hot = perm ? cfg.hot : 0;
         G2_CK(cudaMemsetAsync(acc, 0, (size_t)(n + 1) * 4, st));
+        const int vblocks = (int)((((int64_t)n + 3) / 4 + kCta - 1) / kCta);
         for (int32_t it = 0; it < iters; ++it) {
             const float *c0 = cbuf[it & 1];
             float *c1 = cbuf[(it + 1) & 1];
-            G2_CK(cudaMemsetAsync(dd + ((it + 1) & 1), 0, sizeof(double), st));
+            double *dprev = dd + (it & 1) * R, *dnext = dd + ((it + 1) & 1) * R;
+            G2_CK(cudaMemsetAsync(dnext, 0, R * sizeof(double), st));
             if (cfg.cta == 512) {
                 if (hot) G2_TRY((launch_pr_seg<512, true>(g, ccol, hot, c0, acc, st)));
                 else G2_TRY((launch_pr_seg<512, false>(g, ccol, hot, c0, acc, st)));
@@ -715,9 +777,9 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
                 if (hot) G2_TRY((launch_pr_seg<1024, true>(g, ccol, hot, c0, acc, st)));
                 else G2_TRY((launch_pr_seg<1024, false>(g, ccol, hot, c0, acc, st)));
             }
-            k_pr_seg_vertex<<<vgrid, kCta, 0, st>>>(
-                t->rowptr, n, perm, acc, c1, rank, it == iters - 1, dd + (it & 1),
-                dd + ((it + 1) & 1), base, damping, inv_n);
+            k_pr_seg_vertex<<<vblocks, kCta, 0, st>>>(t->rowptr, n, perm, acc, c1, rank,
+                                                      it == iters - 1, dprev, dnext, base, damping,
+                                                      inv_n);
             stats().launches += 2;
             stats().iterations++;
             stats().pull_rounds++;
