@@ -393,6 +393,108 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _timed(fn, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def run_grid_workload(args):
+    """Road-like 4096 x 4096 grid (10% of lattice edges deleted, 1% local
+    shortcuts, weights U[1, 1000], seed 1): delta-stepping SSSP plain vs fused
+    across deltas, BFS plain vs fused, from vertex 0 (a corner)."""
+    import torch
+    from paper_2012_07990_gb300 import build_native
+    build_native.build()
+    from paper_2012_07990_gb300 import g2
+    from paper_2012_07990_gb300 import graphgen as gg
+    W = args.grid
+    G = gg.road_grid(W, seed=1)
+    w = gg.pair_weights(G, 1000, seed=1)
+    dg = g2.load_graph(G, w)
+    dist = torch.empty(G.n, dtype=torch.int32, device="cuda")
+    depth = torch.empty(G.n, dtype=torch.int32, device="cuda")
+    res = {"sssp": [], "bfs": []}
+    deg = G.degrees()
+    for delta in (16, 64, 256, 1024, 4096, 16384):
+        row = {"delta": delta}
+        for name, s in (("plain_strict", g2.schedule("STRICT")),
+                        ("fused_vertex", g2.schedule("VERTEX_BASED", kernel_fusion=True)),
+                        ("fused_wm", g2.schedule("WM", kernel_fusion=True))):
+            ms = _timed(lambda: g2.g2_sssp_delta(dg, 0, delta, dist, s), reps=2)
+            st = g2.g2_last_stats()
+            row[name + "_ms"] = round(ms, 3)
+            row[name + "_rounds"] = st["iterations"]
+        reached = int(deg[dist.cpu().numpy() < 2**31 - 1].sum())
+        row["gteps_best"] = round(reached / min(v for k, v in row.items() if k.endswith("_ms")) / 1e6, 3)
+        res["sssp"].append(row)
+    for name, s in (("plain_tuned", None), ("plain_strict", g2.schedule("STRICT")),
+                    ("fused_vertex", g2.schedule("VERTEX_BASED", kernel_fusion=True)),
+                    ("fused_wm", g2.schedule("WM", kernel_fusion=True))):
+        ms = _timed(lambda: g2.g2_bfs(dg, 0, depth, None, s))
+        st = g2.g2_last_stats()
+        reached = int(deg[depth.cpu().numpy() >= 0].sum())
+        res["bfs"].append({"schedule": name, "ms": round(ms, 3), "levels": st["iterations"],
+                           "launches": st["launches"], "gteps": round(reached / ms / 1e6, 3)})
+    print(json.dumps({"workload": f"grid{W}x{W}_sssp_bfs", "n": G.n, "m": G.m, **res}))
+
+
+def run_batched_workload(args):
+    """RMAT scale 21 (ef 16, symmetric): 64-source BFS in one traversal vs 64
+    single-source BFS calls (tuned and fixed TWC PUSH); 32-source SSSP (weights
+    U[1, 255]) vs 32 single calls; BC from 16 sources."""
+    import torch
+    from paper_2012_07990_gb300 import build_native
+    build_native.build()
+    from paper_2012_07990_gb300 import g2
+    from paper_2012_07990_gb300 import graphgen as gg
+    G = gg.rmat(args.batch_scale, seed=1)
+    w = gg.pair_weights(G, 255, seed=1)
+    dg = g2.load_graph(G, w)
+    srcs = gg.random_sources(G, 64, seed=1)
+    deg = G.degrees()
+    out = {}
+    depth64 = torch.empty(64 * G.n, dtype=torch.int32, device="cuda")
+    ms = _timed(lambda: g2.g2_bfs_batch(dg, srcs, depth64, None))
+    d = depth64.cpu().numpy().reshape(64, G.n)
+    edges = int(sum(deg[d[i] >= 0].sum() for i in range(64)))
+    out["msbfs64"] = {"ms": round(ms, 3), "gteps": round(edges / ms / 1e6, 2)}
+    one = torch.empty(G.n, dtype=torch.int32, device="cuda")
+    for name, s in (("tuned", None), ("twc_push", g2.schedule("TWC"))):
+        def loop():
+            for sv in srcs:
+                g2.g2_bfs(dg, int(sv), one, None, s)
+        ms1 = _timed(loop, reps=2)
+        out[f"bfs64_serial_{name}"] = {"ms": round(ms1, 3), "gteps": round(edges / ms1 / 1e6, 2)}
+    dist32 = torch.empty(32 * G.n, dtype=torch.int32, device="cuda")
+    ms = _timed(lambda: g2.g2_sssp_batch(dg, srcs[:32], 64, dist32, None))
+    dd = dist32.cpu().numpy().reshape(32, G.n)
+    edges32 = int(sum(deg[dd[i] < 2**31 - 1].sum() for i in range(32)))
+    out["mssssp32"] = {"ms": round(ms, 3), "gteps": round(edges32 / ms / 1e6, 2)}
+
+    def loop_sssp():
+        for sv in srcs[:32]:
+            g2.g2_sssp_delta(dg, int(sv), 64, one, None)
+    ms1 = _timed(loop_sssp, reps=2)
+    out["sssp32_serial"] = {"ms": round(ms1, 3), "gteps": round(edges32 / ms1 / 1e6, 2)}
+    bc = torch.empty(G.n, dtype=torch.float64, device="cuda")
+    ms = _timed(lambda: g2.g2_bc(dg, srcs[:16], bc, None), reps=2)
+    edges16 = int(sum(deg[d[i] >= 0].sum() for i in range(16)))
+    out["bc16"] = {"ms": round(ms, 3), "gteps": round(2 * edges16 / ms / 1e6, 2),
+                   "note": "forward + backward sweeps counted"}
+    print(json.dumps({"workload": f"rmat{args.batch_scale}_batched", "n": G.n, "m": G.m, **out}))
+
+
 def run_profile_case(args):
     """A short run of one algorithm for profilers: load RMAT at --scale, run
     the algorithm --steps times with the tuned schedule, print a checksum."""
@@ -420,6 +522,11 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", choices=["pr", "bfs", "cc"], default=None)
+    ap.add_argument("--workload", choices=["rmat22", "grid", "batched"], default="rmat22",
+                    help="rmat22: the default step (the JSON line the driver reads); grid and "
+                         "batched: the road-grid and multi-source configurations")
+    ap.add_argument("--grid", type=int, default=4096)
+    ap.add_argument("--batch-scale", type=int, default=21)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -431,6 +538,12 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.workload == "grid":
+        run_grid_workload(args)
+        return
+    if args.workload == "batched":
+        run_batched_workload(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
