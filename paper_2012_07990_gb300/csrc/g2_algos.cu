@@ -232,11 +232,11 @@ __global__ void __launch_bounds__(kCta) k_pull_list(DevGraph g, const int32_t *c
 template <class P>
 static void launch_pull_list(g2_graph *g, int lb, const P &op, const int32_t *cand, int32_t ncand,
                              cudaStream_t st) {
+    // A level list can hold hubs, so a destination gets at least a warp (a
+    // thread per destination would walk a hub's in-arcs alone); CM gives a CTA.
     if (ncand <= 0) return;
     const DevGraph dg = g->topo->view();
-    if (lb == G2_LB_VERTEX_BASED)
-        k_pull_list<P, 1><<<grid_for(g, ncand, kCta), kCta, 0, st>>>(dg, cand, ncand, op);
-    else if (lb == G2_LB_CM)
+    if (lb == G2_LB_CM)
         k_pull_list<P, kCta><<<grid_for(g, (int64_t)ncand * kCta, kCta), kCta, 0, st>>>(dg, cand,
                                                                                         ncand, op);
     else
@@ -769,7 +769,7 @@ g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
     if (!g || !bc || (k > 0 && !srcs) || k < 0) return fail(G2_EINVAL, "bad BC arguments");
     for (int32_t i = 0; i < k; ++i) G2_TRY(check_src(g, srcs[i]));
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : default_hybrid();
+    g2_hybrid h = sched ? *sched : tuned_bfs_hybrid();
     if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "BC has no fused variant yet");
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));

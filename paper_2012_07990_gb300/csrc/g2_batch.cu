@@ -11,6 +11,7 @@
 
 #include "g2_host.h"
 #include "g2_lb.cuh"
+#include "g2_push.cuh"
 
 namespace g2 {
 
@@ -120,12 +121,14 @@ __global__ void __launch_bounds__(kCta) k_ms_pull(DevGraph g, P op, OutCtx out,
 }
 
 static g2_status batch_lb(const g2_schedule &s) {
-    switch (s.load_balance) {
-        case G2_LB_VERTEX_BASED: case G2_LB_WM: case G2_LB_CM: case G2_LB_ETWC: return G2_OK;
-        default:
-            return fail(G2_EUNSUPPORTED,
-                        "multi-source traversals support VERTEX_BASED, WM, CM and ETWC");
-    }
+    if (s.load_balance < G2_LB_VERTEX_BASED || s.load_balance > G2_LB_TWC)
+        return fail(G2_EINVAL, "bad load_balance");
+    if (s.load_balance == G2_LB_EDGE_ONLY)
+        return fail(G2_EUNSUPPORTED, "multi-source traversals are frontier-driven (no EDGE_ONLY)");
+    if (s.direction == G2_PULL && s.load_balance != G2_LB_VERTEX_BASED &&
+        s.load_balance != G2_LB_WM)
+        return fail(G2_EUNSUPPORTED, "multi-source PULL supports VERTEX_BASED and WM");
+    return G2_OK;
 }
 
 g2_status bfs_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
@@ -168,10 +171,8 @@ g2_status bfs_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *de
         out.err = d_err;
         G2_CK(cudaMemsetAsync(ctrs + q, 0, 4, st));
         if (s.direction == G2_PUSH) {
-            FrontierIn fin{list[p], size, nullptr};
-            OpMsBfs op{visit, F[p], F[q]};
-            k_ms_push<<<grid_for(g, size, kCta), kCta, 0, st>>>(dg, fin, size, op, out,
-                                                               s.load_balance, ctr);
+            VSet in{OUT_SPARSE, list[p], n, ctrs + p, nullptr, nullptr, size};
+            G2_TRY(push_round(g, s, OpMsBfs{visit, F[p], F[q]}, in, out, ctr, st));
             G2_TRY(read_counters(g, ctrs, 4, st, d_err));
             int32_t nt = g->h_ctr[q];
             if (nt > 0)
@@ -362,11 +363,10 @@ g2_status sssp_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t de
             out.cap2 = n;
             out.err = d_err;
             G2_CK(cudaMemsetAsync(ctrs + q, 0, 4, st));
-            FrontierIn fin{nl[p], size, nullptr};
+            VSet in{OUT_SPARSE, nl[p], n, ctrs + p, nullptr, nullptr, size};
             OpMsRelax op{dist, t->w, M[p], M[q], far, n, (int32_t)std::min<int64_t>(T, G2_INF32),
                          d_err};
-            k_ms_push<<<grid_for(g, size, kCta), kCta, 0, st>>>(dg, fin, size, op, out,
-                                                               s.load_balance, ctr);
+            G2_TRY(push_round(g, s, op, in, out, ctr, st));
             k_msr_clear<<<grid_for(g, size, kCta), kCta, 0, st>>>(nl[p], size, M[p]);
             stats().launches += 2;
             stats().push_rounds++;
@@ -406,6 +406,25 @@ g2_status sssp_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t de
 
 using namespace g2;
 
+// Tuned schedules when the caller passes none: multi-source BFS switches from
+// STRICT PUSH to VERTEX_BASED PULL once the union frontier holds 2% of the
+// vertices; multi-source SSSP relaxes with STRICT PUSH.
+static g2_hybrid tuned_batch_bfs() {
+    g2_hybrid h = default_hybrid();
+    h.criteria = G2_INPUT_VERTEXSET_SIZE;
+    h.threshold = 0.02f;
+    h.s1.load_balance = G2_LB_STRICT;
+    h.s2.load_balance = G2_LB_VERTEX_BASED;
+    h.s2.direction = G2_PULL;
+    return h;
+}
+
+static g2_hybrid tuned_batch_sssp() {
+    g2_hybrid h = default_hybrid();
+    h.s1.load_balance = G2_LB_STRICT;
+    return h;
+}
+
 extern "C" {
 
 g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
@@ -415,7 +434,7 @@ g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *dep
         if (srcs[i] < 0 || srcs[i] >= g->topo->n) return fail(G2_EINVAL, "source out of range");
     if ((int64_t)k * g->topo->n >= (int64_t)1 << 40) return fail(G2_EINVAL, "output too large");
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : default_hybrid();
+    g2_hybrid h = sched ? *sched : tuned_batch_bfs();
     if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "batched BFS runs unfused rounds");
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));
@@ -430,7 +449,7 @@ g2_status g2_sssp_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t del
     for (int32_t i = 0; i < k; ++i)
         if (srcs[i] < 0 || srcs[i] >= g->topo->n) return fail(G2_EINVAL, "source out of range");
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : default_hybrid();
+    g2_hybrid h = sched ? *sched : tuned_batch_sssp();
     if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "batched SSSP runs unfused rounds");
     if (delta <= 0 && h.s1.delta > 0) delta = h.s1.delta;
     int32_t *d_err;

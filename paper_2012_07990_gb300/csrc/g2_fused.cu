@@ -197,6 +197,14 @@ static g2_status launch_coop(g2_graph *g, K kernel, A &args, cudaStream_t st) {
     int per_sm = 0;
     G2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCta, 0));
     if (per_sm < 1) return fail(G2_EUNSUPPORTED, "fused kernel does not fit on an SM");
+    // fewer resident CTAs make every grid barrier cheaper; the round's work
+    // is spread over the virtual CTAs either way (G2_FUSED_CTAS_PER_SM tunes)
+    static int cap = -1;
+    if (cap < 0) {
+        const char *e = getenv("G2_FUSED_CTAS_PER_SM");
+        cap = e ? atoi(e) : 0;
+    }
+    if (cap > 0 && cap < per_sm) per_sm = cap;
     int grid = per_sm * g->topo->sm_count;
     void *params[] = {&args};
     G2_CK(cudaLaunchCooperativeKernel((const void *)kernel, dim3(grid), dim3(kCta), params, 0, st));
