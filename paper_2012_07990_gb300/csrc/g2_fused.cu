@@ -198,11 +198,12 @@ static g2_status launch_coop(g2_graph *g, K kernel, A &args, cudaStream_t st) {
     G2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCta, 0));
     if (per_sm < 1) return fail(G2_EUNSUPPORTED, "fused kernel does not fit on an SM");
     // fewer resident CTAs make every grid barrier cheaper; the round's work
-    // is spread over the virtual CTAs either way (G2_FUSED_CTAS_PER_SM tunes)
+    // is spread over the virtual CTAs either way.  One CTA per SM measured
+    // best on road grids (G2_FUSED_CTAS_PER_SM overrides for sweeps).
     static int cap = -1;
     if (cap < 0) {
         const char *e = getenv("G2_FUSED_CTAS_PER_SM");
-        cap = e ? atoi(e) : 0;
+        cap = e ? atoi(e) : 1;
     }
     if (cap > 0 && cap < per_sm) per_sm = cap;
     int grid = per_sm * g->topo->sm_count;
