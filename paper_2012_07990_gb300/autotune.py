@@ -1,0 +1,269 @@
+"""Schedule autotuner (the role OpenTuner plays in Sec. VI-E of the paper).
+
+The space is the scheduling language's (Table II fields and the Table III
+hybrid threshold) plus the integer parameters the paper names: the delta of
+delta-stepping and the EdgeBlocking segment size.  Search: random sampling of
+the space (plus known-good seeds), then successive halving -- every surviving
+candidate is timed again with more repetitions and the slower part dropped --
+until one remains.  Results are cached in a JSON file keyed by a fingerprint of
+the graph and the algorithm.
+
+The evaluator is a callable ``cost(schedule_dict) -> milliseconds`` so the
+search logic runs without a GPU; ``gpu_evaluator`` builds one that times the
+CUDA library with CUDA events.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import math
+import os
+import random
+from dataclasses import dataclass, field
+
+LBS = ["VERTEX_BASED", "CM", "WM", "STRICT", "EDGE_ONLY", "ETWC", "TWC"]
+PUSH_FRONTIER_LBS = ["VERTEX_BASED", "CM", "WM", "STRICT", "ETWC", "TWC"]
+PULL_LBS = ["VERTEX_BASED", "WM", "CM"]
+
+
+# ----------------------------------------------------------------- space
+def _simple(**kw):
+    d = {"lb": "VERTEX_BASED", "direction": 0, "pull_frontier": 0, "frontier_creation": 0,
+         "dedup": True, "dedup_type": 0, "delta": 0, "kernel_fusion": False,
+         "edge_blocking": False, "blocking_size": 0}
+    d.update(kw)
+    return d
+
+
+def sample_schedule(algo: str, rng: random.Random) -> dict:
+    """One random point of the schedule space for `algo`."""
+    if algo in ("bfs", "bc"):
+        push = _simple(lb=rng.choice(PUSH_FRONTIER_LBS), dedup=rng.random() < 0.5,
+                       dedup_type=rng.randrange(3))
+        if algo == "bfs" and rng.random() < 0.15:
+            push.update(lb=rng.choice(["VERTEX_BASED", "WM", "CM", "ETWC"]), kernel_fusion=True)
+            return {"criteria": 0, "threshold": 0.0, "s1": push, "s2": push}
+        pull = _simple(lb=rng.choice(PULL_LBS), direction=1, pull_frontier=rng.randrange(2),
+                       frontier_creation=rng.randrange(3), dedup=False)
+        tau = rng.choice([0.0, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 1e9])
+        return {"criteria": 1, "threshold": tau, "s1": push, "s2": pull}
+    if algo == "sssp":
+        delta = 2 ** rng.randrange(0, 15)
+        fused = rng.random() < 0.3
+        lb = rng.choice(["VERTEX_BASED", "WM", "CM", "ETWC"] if fused else PUSH_FRONTIER_LBS)
+        s = _simple(lb=lb, delta=delta, kernel_fusion=fused,
+                    dedup_type=0 if fused else rng.randrange(3))
+        return {"criteria": 0, "threshold": 0.0, "s1": s, "s2": s}
+    if algo == "cc":
+        if rng.random() < 0.3:
+            return {"tuned_default": True}
+        if rng.random() < 0.5:
+            s = _simple(lb=rng.choice(LBS))
+        else:
+            s = _simple(lb=rng.choice(PULL_LBS), direction=1, pull_frontier=rng.randrange(2))
+        return {"criteria": 0, "threshold": 0.0, "s1": s, "s2": s}
+    if algo == "pr":
+        r = rng.random()
+        if r < 0.4:
+            return {"tuned_default": True}
+        if r < 0.6:
+            s = _simple(lb="EDGE_ONLY", direction=1)
+        elif r < 0.8:
+            s = _simple(lb=rng.choice(PULL_LBS), direction=1)
+        else:
+            eb = rng.random() < 0.5
+            s = _simple(lb="EDGE_ONLY", edge_blocking=eb,
+                        blocking_size=rng.choice([0, 1 << 16, 1 << 18, 1 << 20, 1 << 22]) if eb else 0)
+        return {"criteria": 0, "threshold": 0.0, "s1": s, "s2": s}
+    if algo == "bfs_batch":
+        push = _simple(lb=rng.choice(PUSH_FRONTIER_LBS))
+        pull = _simple(lb=rng.choice(["VERTEX_BASED", "WM"]), direction=1)
+        return {"criteria": 1, "threshold": rng.choice([0.0, 0.005, 0.02, 0.05, 1e9]), "s1": push,
+                "s2": pull}
+    raise ValueError(f"unknown algorithm {algo}")
+
+
+def seeds(algo: str) -> list[dict]:
+    """Known-good starting points always included in the sample."""
+    if algo in ("bfs", "bc"):
+        return [{"criteria": 1, "threshold": 0.02, "s1": _simple(lb="STRICT"),
+                 "s2": _simple(lb="VERTEX_BASED", direction=1, pull_frontier=1, frontier_creation=2,
+                               dedup=False)},
+                {"criteria": 0, "threshold": 0.0, "s1": _simple(lb="WM", kernel_fusion=True),
+                 "s2": _simple(lb="WM", kernel_fusion=True)}]
+    if algo == "sssp":
+        return [{"criteria": 0, "threshold": 0.0, "s1": _simple(lb="STRICT", delta=d),
+                 "s2": _simple(lb="STRICT", delta=d)} for d in (64, 1024)] + \
+               [{"criteria": 0, "threshold": 0.0, "s1": _simple(lb="WM", delta=4096, kernel_fusion=True),
+                 "s2": _simple(lb="WM", delta=4096, kernel_fusion=True)}]
+    if algo in ("cc", "pr"):
+        return [{"tuned_default": True}]
+    if algo == "bfs_batch":
+        return [{"criteria": 1, "threshold": 0.02, "s1": _simple(lb="STRICT"),
+                 "s2": _simple(lb="VERTEX_BASED", direction=1)}]
+    return []
+
+
+def key_of(d: dict) -> str:
+    return json.dumps(d, sort_keys=True)
+
+
+# ------------------------------------------------------------ the search
+@dataclass
+class TuneResult:
+    best: dict
+    best_ms: float
+    evaluated: int
+    history: list = field(default_factory=list)
+
+
+def successive_halving(cost, candidates: list[dict], reps0: int = 1, eta: int = 3,
+                       max_evals: int | None = None) -> TuneResult:
+    """Time every candidate with reps0 repetitions, keep the best 1/eta, time
+    the survivors with eta-times more repetitions, ... until one is left.
+    Candidates whose evaluation raises are dropped (unsupported combinations)."""
+    alive = []
+    seen = set()
+    for c in candidates:
+        k = key_of(c)
+        if k not in seen:
+            seen.add(k)
+            alive.append(c)
+    history = []
+    evals = 0
+    reps = reps0
+    scores: dict[str, float] = {}
+    while alive:
+        scored = []
+        for c in alive:
+            if max_evals is not None and evals >= max_evals:
+                break
+            try:
+                t = min(cost(c) for _ in range(reps))
+            except Exception as e:  # unsupported / invalid: drop it
+                history.append({"schedule": c, "error": str(e)[:120]})
+                evals += 1
+                continue
+            evals += reps
+            scores[key_of(c)] = t
+            scored.append((t, c))
+            history.append({"schedule": c, "ms": t, "reps": reps})
+        if not scored:
+            break
+        scored.sort(key=lambda x: x[0])
+        if len(scored) == 1 or (max_evals is not None and evals >= max_evals):
+            best_ms, best = scored[0]
+            return TuneResult(best, best_ms, evals, history)
+        keep = max(1, int(math.ceil(len(scored) / eta)))
+        alive = [c for _, c in scored[:keep]]
+        reps *= eta
+    raise RuntimeError("no schedule could be evaluated")
+
+
+def tune(algo: str, cost, n_samples: int = 24, seed: int = 1, eta: int = 3,
+         max_evals: int | None = None) -> TuneResult:
+    rng = random.Random(seed)
+    cands = seeds(algo) + [sample_schedule(algo, rng) for _ in range(n_samples)]
+    return successive_halving(cost, cands, eta=eta, max_evals=max_evals)
+
+
+# ----------------------------------------------------------------- cache
+def graph_fingerprint(n: int, rowptr, col) -> str:
+    """Stable fingerprint of a CSR graph: sizes and a strided sample of arrays."""
+    import numpy as np
+    h = hashlib.sha256()
+    h.update(np.int64([n, len(col)]).tobytes())
+    rp = np.asarray(rowptr)
+    cl = np.asarray(col)
+    step_r = max(1, rp.size // 4096)
+    step_c = max(1, cl.size // 65536)
+    h.update(np.ascontiguousarray(rp[::step_r]).tobytes())
+    h.update(np.ascontiguousarray(cl[::step_c]).tobytes())
+    return h.hexdigest()[:24]
+
+
+class TuneCache:
+    def __init__(self, path: str):
+        self.path = path
+        self.data = {}
+        if os.path.exists(path):
+            with open(path) as f:
+                self.data = json.load(f)
+
+    def get(self, fp: str, algo: str):
+        return self.data.get(f"{fp}:{algo}")
+
+    def put(self, fp: str, algo: str, result: TuneResult):
+        self.data[f"{fp}:{algo}"] = {"schedule": result.best, "ms": result.best_ms,
+                                      "evaluated": result.evaluated}
+        tmp = self.path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(self.data, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+
+def tune_cached(cache: TuneCache, fp: str, algo: str, cost, **kw) -> dict:
+    hit = cache.get(fp, algo)
+    if hit is not None:
+        return hit["schedule"]
+    res = tune(algo, cost, **kw)
+    cache.put(fp, algo, res)
+    return res.best
+
+
+# --------------------------------------------------------- GPU binding
+def to_hybrid(g2, d: dict):
+    """Schedule dict -> g2_hybrid (None for the library's tuned default)."""
+    if d.get("tuned_default"):
+        return None
+
+    def mk(s):
+        return g2.schedule(s["lb"], direction=s["direction"], pull_frontier=s["pull_frontier"],
+                           frontier_creation=s["frontier_creation"], dedup=s["dedup"],
+                           dedup_type=s["dedup_type"], delta=s["delta"],
+                           kernel_fusion=s["kernel_fusion"], edge_blocking=s["edge_blocking"],
+                           blocking_size=s["blocking_size"])
+
+    h = g2.g2_hybrid()
+    h.criteria = d["criteria"]
+    h.threshold = float(min(d["threshold"], 3.0e38))
+    h.s1 = mk(d["s1"])
+    h.s2 = mk(d["s2"])
+    return h
+
+
+def gpu_evaluator(g2, dg, algo: str, src: int = 0, srcs=None, n: int | None = None):
+    """cost(schedule) in milliseconds, timed with CUDA events on the current
+    stream, for algorithm `algo` on the loaded graph `dg`."""
+    import torch
+    n = dg.n if n is None else n
+    out_i = torch.empty(n * (64 if algo == "bfs_batch" else 1), dtype=torch.int32, device="cuda")
+    out_f = torch.empty(n, dtype=torch.float32, device="cuda")
+    out_d = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def run(d):
+        h = to_hybrid(g2, d)
+        if algo == "bfs":
+            g2.g2_bfs(dg, src, out_i, None, h)
+        elif algo == "sssp":
+            g2.g2_sssp_delta(dg, src, 0, out_i, h)
+        elif algo == "cc":
+            g2.g2_cc(dg, out_i, h)
+        elif algo == "pr":
+            g2.g2_pagerank(dg, 0.85, 20, out_f, h)
+        elif algo == "bc":
+            g2.g2_bc(dg, [src], out_d, h)
+        elif algo == "bfs_batch":
+            g2.g2_bfs_batch(dg, srcs, out_i, h)
+
+    def cost(d):
+        run(d)  # warm (layouts, workspace)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run(d)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    return cost

@@ -1,0 +1,108 @@
+"""Autotuner: search logic on CPU with synthetic cost functions; on the GPU,
+tuned schedules must reproduce the oracle's results."""
+import random
+
+import numpy as np
+import pytest
+
+from paper_2012_07990_gb300 import autotune as at
+
+
+def test_samples_are_valid_points():
+    rng = random.Random(0)
+    for algo in ("bfs", "sssp", "cc", "pr", "bc", "bfs_batch"):
+        for _ in range(200):
+            d = at.sample_schedule(algo, rng)
+            if d.get("tuned_default"):
+                continue
+            for s in (d["s1"], d["s2"]):
+                assert s["lb"] in at.LBS
+                assert s["direction"] in (0, 1)
+                if s["direction"] == 1:
+                    # PageRank's PULL + EDGE_ONLY is the arc-balanced CSC sweep
+                    assert s["lb"] in at.PULL_LBS or (algo == "pr" and s["lb"] == "EDGE_ONLY")
+                if s["kernel_fusion"]:
+                    assert s["lb"] in ("VERTEX_BASED", "WM", "CM", "ETWC") and s["direction"] == 0
+                if s["edge_blocking"]:
+                    assert s["lb"] == "EDGE_ONLY"
+            if algo == "sssp":
+                assert d["s1"]["delta"] >= 1
+
+
+def test_successive_halving_finds_the_minimum_under_noise():
+    rng = random.Random(3)
+    cands = [{"x": i} for i in range(40)]
+    true = {i: 10.0 + abs(i - 17) for i in range(40)}
+
+    def cost(d):
+        return true[d["x"]] + rng.random() * 0.5  # noise below the gap between neighbours
+
+    res = at.successive_halving(cost, cands, eta=3)
+    assert res.best == {"x": 17}
+    assert res.evaluated >= 40
+
+
+def test_failing_candidates_are_dropped_and_budget_respected():
+    def cost(d):
+        if d["x"] % 2:
+            raise RuntimeError("unsupported")
+        return float(d["x"])
+
+    res = at.successive_halving(cost, [{"x": i} for i in range(1, 30)], eta=2)
+    assert res.best == {"x": 2}
+    assert any("error" in h for h in res.history)
+    res2 = at.successive_halving(lambda d: float(d["x"]), [{"x": i} for i in range(100)],
+                                 max_evals=10)
+    assert res2.evaluated <= 10 and res2.best["x"] <= 9
+
+
+def test_cache_roundtrip(tmp_path):
+    from paper_2012_07990_gb300 import graphgen as gg
+    g = gg.rmat(8)
+    fp = at.graph_fingerprint(g.n, g.rowptr, g.col)
+    assert fp == at.graph_fingerprint(g.n, g.rowptr.copy(), g.col.copy())
+    assert fp != at.graph_fingerprint(g.n, g.rowptr, np.roll(g.col, 1))
+    cache = at.TuneCache(str(tmp_path / "tune.json"))
+    calls = []
+
+    def cost(d):
+        calls.append(1)
+        return 1.0 if d.get("tuned_default") else 2.0
+
+    best = at.tune_cached(cache, fp, "pr", cost, n_samples=5)
+    assert best == {"tuned_default": True}
+    n_calls = len(calls)
+    again = at.TuneCache(str(tmp_path / "tune.json"))
+    assert at.tune_cached(again, fp, "pr", cost) == best
+    assert len(calls) == n_calls  # served from the cache
+
+
+@pytest.mark.gpu
+def test_tuned_schedules_reproduce_the_oracle():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_2012_07990_gb300 import build_native
+    from paper_2012_07990_gb300 import graphgen as gg
+    build_native.build()
+    from paper_2012_07990_gb300 import g2
+    g = gg.rmat(12, seed=7)
+    w = gg.pair_weights(g, 255, seed=7)
+    dg = g2.load_graph(g, w)
+    src = g.max_degree_vertex()
+    for algo in ("bfs", "sssp", "cc"):
+        res = at.tune(algo, at.gpu_evaluator(g2, dg, algo, src=src), n_samples=10, seed=2)
+        h = at.to_hybrid(g2, res.best)
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        if algo == "bfs":
+            g2.g2_bfs(dg, src, out, None, h)
+            want = oracle.bfs_graph(g, src, want_parent=False)[0]
+        elif algo == "sssp":
+            g2.g2_sssp_delta(dg, src, 0, out, h)
+            want = oracle.sssp_graph(g, w, src)
+        else:
+            g2.g2_cc(dg, out, h)
+            want = oracle.cc_graph(g)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), want), (algo, res.best)
