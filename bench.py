@@ -495,6 +495,36 @@ def run_batched_workload(args):
     print(json.dumps({"workload": f"rmat{args.batch_scale}_batched", "n": G.n, "m": G.m, **out}))
 
 
+def run_serve_workload(args):
+    """Serving: Poisson stream (BFS 60% / SSSP 30% / single-source BC 10%) over
+    a resident pool (full: RMAT 16/18/20/22 + grids 512^2..4096^2; small: RMAT
+    16/18/20 + grids 512^2, 1024^2), continuous batching on 4 slots vs the same
+    trace served serially with one plain launch per query."""
+    from paper_2012_07990_gb300 import build_native
+    build_native.build()
+    from paper_2012_07990_gb300 import g2
+    from paper_2012_07990_gb300 import serve
+    if args.serve_pool == "full":
+        specs = serve.default_pool_specs()
+    else:
+        specs = serve.default_pool_specs(scales=(16, 18, 20), grids=(512, 1024))
+    t = time.time()
+    pool = serve.GraphPool(g2, specs)
+    load_s = time.time() - t
+    trace = serve.make_trace(pool, rate=args.serve_rate, duration=args.serve_duration, seed=1)
+    ex = serve.GpuExecutor(g2, pool, slots=4)
+    srv = serve.Server(ex, pool)
+    srv.run(trace[: min(64, len(trace))])  # warm views and workspaces
+    batched = srv.run(trace)
+    ex1 = serve.GpuExecutor(g2, pool, slots=1)
+    serial = serve.Server(ex1, pool, max_batch=dict(bfs=1, sssp=1, bc=1)).run(trace)
+    print(json.dumps({"workload": f"serve_{args.serve_pool}", "graphs": [s.name for s in specs],
+                      "pool_load_s": round(load_s, 2), "rate_per_s": args.serve_rate,
+                      "duration_s": args.serve_duration, "requests": len(trace),
+                      "continuous_batching_4_slots": batched.summary(),
+                      "serial_plain": serial.summary()}))
+
+
 def run_profile_case(args):
     """A short run of one algorithm for profilers: load RMAT at --scale, run
     the algorithm --steps times with the tuned schedule, print a checksum."""
@@ -522,7 +552,10 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", choices=["pr", "bfs", "cc"], default=None)
-    ap.add_argument("--workload", choices=["rmat22", "grid", "batched"], default="rmat22",
+    ap.add_argument("--serve-pool", choices=["full", "small"], default="full")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-duration", type=float, default=1.0)
+    ap.add_argument("--workload", choices=["rmat22", "grid", "batched", "serve"], default="rmat22",
                     help="rmat22: the default step (the JSON line the driver reads); grid and "
                          "batched: the road-grid and multi-source configurations")
     ap.add_argument("--grid", type=int, default=4096)
@@ -544,6 +577,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched_workload(args)
+        return
+    if args.workload == "serve":
+        run_serve_workload(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
