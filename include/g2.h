@@ -248,8 +248,11 @@ g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, float *rank,
 
 /* Betweenness centrality (Brandes) summed over the k sources srcs (host
  * int32[k]): bc double[n] device, no normalisation, no halving.  Path counts
- * in fp64 with per-level power-of-two rescaling, so they do not overflow on
- * high-diameter graphs. */
+ * are extended-range floats (fp64 mantissa, int32 exponent per vertex), so
+ * they neither overflow nor underflow on high-diameter graphs.  Each level's
+ * discovery follows the (hybrid) schedule; with kernel fusion each source
+ * runs in one persistent cooperative kernel.  NULL schedule: the
+ * direction-optimising hybrid of g2_bfs. */
 g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc,
                 const g2_hybrid *sched, void *stream);
 

@@ -170,80 +170,6 @@ __global__ void k_far_split(const int32_t *far, int32_t nfar, const int32_t *dis
     (void)lane;
 }
 
-// BC: max sigma over a level (positive doubles order like their bit patterns)
-__global__ void k_level_max(const int32_t *lvl, int32_t cnt, const double *sigma,
-                            unsigned long long *out) {
-    unsigned long long best = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long b = (unsigned long long)__double_as_longlong(sigma[lvl[i]]);
-        if (b > best) best = b;
-    }
-    for (int d = 16; d > 0; d >>= 1) {
-        unsigned long long o = __shfl_xor_sync(G2_FULL, best, d);
-        if (o > best) best = o;
-    }
-    if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
-}
-
-__global__ void k_level_scale(const int32_t *lvl, int32_t cnt, double *sigma, int e) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
-         i += (int64_t)gridDim.x * blockDim.x)
-        sigma[lvl[i]] = ldexp(sigma[lvl[i]], -e);
-}
-
-// Backward (dependency) step of Brandes for the vertices of one level:
-// delta[v] = sigma[v] * sum_{w: v->w, depth[w] = depth[v]+1} (1 + delta[w]) / sigma[w]
-// times 2^(E_d - E_{d+1}) for the per-level scale exponents.
-struct PullBCDelta {
-    const int32_t *depth;
-    const double *sigma;
-    double *delta;
-    double *bc;
-    int32_t src;
-    double ratio;  // 2^(E_d - E_{d+1})
-    typedef int32_t Ctx;
-    typedef double Acc;
-    __device__ __forceinline__ Ctx ctx(int32_t v) const { return depth[v]; }
-    __device__ __forceinline__ bool filter(Ctx) const { return true; }
-    __device__ __forceinline__ Acc identity() const { return 0.0; }
-    __device__ __forceinline__ Acc edge(Ctx dv, int32_t w, int32_t) const {
-        return depth[w] == dv + 1 ? (1.0 + delta[w]) / sigma[w] : 0.0;
-    }
-    __device__ __forceinline__ Acc combine(Acc a, Acc b) const { return a + b; }
-    __device__ __forceinline__ bool stop(Acc) const { return false; }
-    __device__ __forceinline__ int finish(int32_t v, Ctx, Acc a) const {
-        double dv = sigma[v] * a * ratio;
-        delta[v] = dv;
-        if (v != src) bc[v] += dv;
-        return 0;
-    }
-};
-
-template <class P, int G>
-__global__ void __launch_bounds__(kCta) k_pull_list(DevGraph g, const int32_t *cand, int32_t ncand,
-                                                    P op) {
-    OutCtx none;
-    memset(&none, 0, sizeof(none));
-    Member all{MEM_ALL, nullptr, nullptr};
-    lb_pull<P, G>(g, cand, ncand, all, op, none, blockIdx.x, gridDim.x, nullptr);
-}
-
-template <class P>
-static void launch_pull_list(g2_graph *g, int lb, const P &op, const int32_t *cand, int32_t ncand,
-                             cudaStream_t st) {
-    // A level list can hold hubs, so a destination gets at least a warp (a
-    // thread per destination would walk a hub's in-arcs alone); CM gives a CTA.
-    if (ncand <= 0) return;
-    const DevGraph dg = g->topo->view();
-    if (lb == G2_LB_CM)
-        k_pull_list<P, kCta><<<grid_for(g, (int64_t)ncand * kCta, kCta), kCta, 0, st>>>(dg, cand,
-                                                                                        ncand, op);
-    else
-        k_pull_list<P, 32><<<grid_for(g, (int64_t)ncand * 32, kCta), kCta, 0, st>>>(dg, cand, ncand,
-                                                                                   op);
-    stats().launches += 1;
-}
 
 // --------------------------------------------------------------- helpers
 struct Ping {
@@ -583,107 +509,6 @@ g2_status sssp_plain(g2_graph *g, int32_t src, int32_t delta, int32_t *dist, con
     return G2_OK;
 }
 
-// ====================================================================== BC
-g2_status bc_run(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const g2_hybrid &h,
-                 cudaStream_t st, int32_t *d_err) {
-    Topology *t = g->topo;
-    const int32_t n = t->n;
-    int32_t *ctrs = d_err - 62;
-    int32_t *depth, *lvl;
-    double *sigma, *delta;
-    Ping pp;
-    G2_TRY(get_ping(g, pp, true, true));
-    G2_TRY(ws(g, B_I0, (size_t)std::max(n, 1), &depth));
-    G2_TRY(ws(g, B_LVL, (size_t)std::max(n, 1), &lvl));
-    G2_TRY(ws(g, B_D0, (size_t)std::max(n, 1), &sigma));
-    G2_TRY(ws(g, B_D1, (size_t)std::max(n, 1), &delta));
-    unsigned long long *d_max;
-    G2_TRY(ws(g, B_ARCS, 2, &d_max));
-    d_max += 1;  // slot 0 counts arcs; slot 1 holds the level maximum
-    G2_CK(cudaMemsetAsync(bc, 0, (size_t)n * 8, st));
-    std::vector<int32_t> off;
-    std::vector<int> E;
-    for (int32_t i = 0; i < k; ++i) {
-        int32_t s0 = srcs[i];
-        k_bfs_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(depth, nullptr, n, s0, lvl, ctrs + 3);
-        G2_CK(cudaMemsetAsync(sigma, 0, (size_t)n * 8, st));
-        G2_CK(cudaMemsetAsync(delta, 0, (size_t)n * 8, st));
-        double one = 1.0;
-        G2_CK(cudaMemcpyAsync(sigma + s0, &one, 8, cudaMemcpyHostToDevice, st));
-        off.assign(1, 0);
-        off.push_back(1);
-        E.assign(1, 0);
-        // forward: level-synchronous BFS; every level's list is appended to lvl
-        for (int d = 0;; ++d) {
-            int32_t b = off[d], e = off[d + 1];
-            int32_t size = e - b;
-            if (size == 0) break;
-            const g2_schedule &s = pick_schedule(h, size, n);
-            G2_TRY(check_schedule(g, s, K_BFS, false));
-            if (s.load_balance == G2_LB_EDGE_ONLY)
-                return fail(G2_EUNSUPPORTED, "BC's BFS is frontier-driven; EDGE_ONLY is for full sweeps");
-            VSet in{OUT_SPARSE, lvl + b, size, nullptr, nullptr, nullptr, size};
-            if (s.direction == G2_PULL) {
-                int want = s.pull_frontier == G2_BITMAP ? OUT_BITMAP : OUT_BOOLMAP;
-                VSet tt{want, nullptr, 0, nullptr, pp.bm[0], pp.bo[0], size};
-                G2_TRY(vset_convert(g, in, want, tt, st));
-                in = tt;
-            }
-            OpArgs a;
-            memset(&a, 0, sizeof(a));
-            a.kind = K_BFS;
-            a.i0 = depth;
-            a.err = d_err;
-            a.threshold = G2_INF32;
-            OutArgs o;
-            memset(&o, 0, sizeof(o));
-            o.rep = OUT_SPARSE;  // the level lists are needed for the backward pass
-            o.q = lvl + e;
-            o.qcap = n - e;
-            o.cnt = ctrs + 3;
-            o.dedup = DD_NONE;
-            G2_CK(cudaMemsetAsync(o.cnt, 0, 4, st));
-            G2_TRY(apply_round(g, s, a, in, o, st));
-            s.direction == G2_PUSH ? stats().push_rounds++ : stats().pull_rounds++;
-            G2_TRY(read_counters(g, ctrs, 4, st, d_err));
-            int32_t nn = g->h_ctr[3];
-            if (nn == 0) break;
-            // sigma of the new level: sum over in-neighbours one level up
-            PullBCSigma ps{depth, sigma};
-            launch_pull_list(g, s.load_balance, ps, lvl + e, nn, st);
-            // rescale the level by a power of two when its counts grow large
-            G2_CK(cudaMemsetAsync(d_max, 0, 8, st));
-            k_level_max<<<grid_for(g, nn, kCta), kCta, 0, st>>>(lvl + e, nn, sigma, d_max);
-            unsigned long long hm = 0;
-            G2_CK(cudaMemcpyAsync(&hm, d_max, 8, cudaMemcpyDeviceToHost, st));
-            G2_CK(cudaStreamSynchronize(st));
-            double mx;
-            memcpy(&mx, &hm, 8);
-            int ex = 0;
-            if (mx > 0) frexp(mx, &ex);
-            int shift = (ex > 256 || ex < -256) ? ex : 0;
-            if (shift) {
-                k_level_scale<<<grid_for(g, nn, kCta), kCta, 0, st>>>(lvl + e, nn, sigma, shift);
-                stats().launches += 1;
-            }
-            E.push_back(E.back() + shift);
-            off.push_back(e + nn);
-            stats().launches += 2;
-            stats().iterations++;
-        }
-        // backward: deepest level first
-        int D = (int)off.size() - 1;  // number of levels
-        for (int d = D - 2; d >= 0; --d) {
-            int32_t b = off[d], cnt = off[d + 1] - b;
-            const g2_schedule &s = pick_schedule(h, cnt, n);
-            PullBCDelta pd{depth, sigma, delta, bc, s0, ldexp(1.0, E[d] - E[d + 1])};
-            launch_pull_list(g, s.load_balance, pd, lvl + b, cnt, st);
-        }
-        G2_TRY(sync_and_check(g, st, d_err));
-    }
-    return G2_OK;
-}
-
 }  // namespace g2
 
 using namespace g2;
@@ -761,19 +586,6 @@ g2_status g2_sssp_delta(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
     } else {
         G2_TRY(sssp_plain(g, src, delta, dist, h, st, d_err));
     }
-    return end_call(g, st, d_err);
-}
-
-g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const g2_hybrid *sched,
-                void *stream) {
-    if (!g || !bc || (k > 0 && !srcs) || k < 0) return fail(G2_EINVAL, "bad BC arguments");
-    for (int32_t i = 0; i < k; ++i) G2_TRY(check_src(g, srcs[i]));
-    cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : tuned_bfs_hybrid();
-    if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "BC has no fused variant yet");
-    int32_t *d_err;
-    G2_TRY(begin_call(g, st, &d_err));
-    G2_TRY(bc_run(g, srcs, k, bc, h, st, d_err));
     return end_call(g, st, d_err);
 }
 

@@ -1,0 +1,405 @@
+// g2_bc.cu — betweenness centrality (Sec. VII; Brandes, "A faster algorithm
+// for betweenness centrality", 2001) summed over a list of sources.
+//
+// Per source: a level-synchronous BFS whose levels are appended to one list,
+// path counts sigma for each new level (pull over in-neighbours one level up),
+// then dependencies delta level by level from the deepest (pull over
+// out-neighbours one level down), bc[v] += delta[v] for v != source.
+//
+// Path counts grow like binomials on grids (C(2k, k) after 2k levels) and two
+// vertices of one level can differ by more than the fp64 range, so sigma is an
+// extended-range float: an fp64 mantissa in [0.5, 1) and an int32 exponent per
+// vertex.  Dependency ratios sigma_v / sigma_w are <= 1 and are formed as
+// ldexp(m_v / m_w, e_v - e_w).
+//
+// Schedules: each level's discovery is one edgeset.apply round (PUSH or PULL
+// per the hybrid schedule); with kernel fusion the whole source runs in one
+// persistent cooperative kernel with three grid barriers per level.  The
+// sigma and delta pulls give a warp to every vertex and a whole CTA to the
+// vertices with at least kBigDeg arcs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "g2_host.h"
+#include "g2_lb.cuh"
+
+namespace g2 {
+
+constexpr int32_t kBigDeg = 4096;
+
+struct BigF {
+    double m;  // 0 or in [0.5, 1)
+    int e;
+};
+
+__device__ __forceinline__ BigF bf_make(double m, int e) {
+    if (m == 0.0) return BigF{0.0, 0};
+    int k;
+    double f = frexp(m, &k);
+    return BigF{f, e + k};
+}
+
+__device__ __forceinline__ BigF bf_add(BigF a, BigF b) {
+    if (a.m == 0.0) return b;
+    if (b.m == 0.0) return a;
+    if (a.e < b.e) {
+        BigF t = a;
+        a = b;
+        b = t;
+    }
+    int d = a.e - b.e;
+    double s = a.m + (d > 1100 ? 0.0 : ldexp(b.m, -d));
+    return bf_make(s, a.e);
+}
+
+__device__ __forceinline__ BigF bf_shfl_xor(BigF a, int d) {
+    return BigF{__shfl_xor_sync(G2_FULL, a.m, d), __shfl_xor_sync(G2_FULL, a.e, d)};
+}
+
+struct BcState {
+    DevGraph g;
+    int32_t *depth;
+    double *sm;  // sigma mantissas
+    int32_t *se; // sigma exponents
+    double *delta;
+    double *bc;
+    int32_t *lvl;  // all levels, in order
+    int32_t src;
+};
+
+// sigma of vertex w at level d+1: sum over in-neighbours u at level d
+__device__ __forceinline__ BigF bc_sigma_part(const BcState &s, int32_t w, int32_t d, int32_t b,
+                                              int32_t e, int32_t step, int32_t off) {
+    BigF acc{0.0, 0};
+    for (int32_t k = b + off; k < e; k += step) {
+        int32_t u = s.g.ccol[k];
+        if (s.depth[u] == d) acc = bf_add(acc, BigF{s.sm[u], s.se[u]});
+    }
+    return acc;
+}
+
+// delta of vertex v at level d: sum over out-neighbours w at level d+1
+__device__ __forceinline__ double bc_delta_part(const BcState &s, int32_t v, int32_t d, int32_t b,
+                                                int32_t e, int32_t step, int32_t off) {
+    const double mv = s.sm[v];
+    const int ev = s.se[v];
+    double acc = 0.0;
+    for (int32_t k = b + off; k < e; k += step) {
+        int32_t w = s.g.col[k];
+        if (s.depth[w] == d + 1) acc += ldexp(mv / s.sm[w], ev - s.se[w]) * (1.0 + s.delta[w]);
+    }
+    return acc;
+}
+
+// Level pass over list[0, cnt): small vertices one per warp, big ones one per
+// CTA.  `bid`/`nb` as in the load-balancing library (plain or fused).
+template <bool SIGMA>
+__device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt, int32_t d,
+                              int bid, int nb) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gw = bid * kWarps + wid, nw = nb * kWarps;
+    // warps: vertices with fewer than kBigDeg arcs
+    for (int32_t i = gw; i < cnt; i += nw) {
+        int32_t v = list[i];
+        int32_t b = SIGMA ? s.g.crowptr[v] : s.g.rowptr[v];
+        int32_t e = SIGMA ? s.g.crowptr[v + 1] : s.g.rowptr[v + 1];
+        if (e - b >= kBigDeg) continue;
+        if (SIGMA) {
+            BigF a = bc_sigma_part(s, v, d, b, e, 32, lane);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a = bf_add(a, bf_shfl_xor(a, o));
+            if (lane == 0) {
+                s.sm[v] = a.m;
+                s.se[v] = a.e;
+            }
+        } else {
+            double a = bc_delta_part(s, v, d, b, e, 32, lane);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(G2_FULL, a, o);
+            if (lane == 0) {
+                s.delta[v] = a;
+                if (v != s.src) s.bc[v] += a;
+            }
+        }
+    }
+    // CTAs: vertices with at least kBigDeg arcs
+    __shared__ double s_m[kWarps];
+    __shared__ int s_e[kWarps];
+    for (int32_t i = bid; i < cnt; i += nb) {
+        int32_t v = list[i];
+        int32_t b = SIGMA ? s.g.crowptr[v] : s.g.rowptr[v];
+        int32_t e = SIGMA ? s.g.crowptr[v + 1] : s.g.rowptr[v + 1];
+        if (e - b < kBigDeg) continue;
+        if (SIGMA) {
+            BigF a = bc_sigma_part(s, v, d, b, e, kCta, threadIdx.x);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a = bf_add(a, bf_shfl_xor(a, o));
+            if (lane == 0) {
+                s_m[wid] = a.m;
+                s_e[wid] = a.e;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                BigF t{0.0, 0};
+                for (int k = 0; k < kWarps; ++k) t = bf_add(t, BigF{s_m[k], s_e[k]});
+                s.sm[v] = t.m;
+                s.se[v] = t.e;
+            }
+        } else {
+            double a = bc_delta_part(s, v, d, b, e, kCta, threadIdx.x);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(G2_FULL, a, o);
+            if (lane == 0) s_m[wid] = a;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int k = 0; k < kWarps; ++k) t += s_m[k];
+                s.delta[v] = t;
+                if (v != s.src) s.bc[v] += t;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <bool SIGMA>
+__global__ void __launch_bounds__(kCta) k_bc_level(BcState s, const int32_t *list, int32_t cnt,
+                                                   int32_t d) {
+    bc_level_pass<SIGMA>(s, list, cnt, d, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_bc_init(BcState s, int32_t n, int32_t *cnt3) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        bool is_src = v == s.src;
+        s.depth[v] = is_src ? 0 : -1;
+        s.sm[v] = is_src ? 0.5 : 0.0;  // sigma(src) = 1 = 0.5 * 2^1
+        s.se[v] = is_src ? 1 : 0;
+        s.delta[v] = 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s.lvl[0] = s.src;
+        if (cnt3) {
+            cnt3[0] = cnt3[1] = cnt3[2] = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------ fused source
+struct BcFusedArgs {
+    BcState s;
+    int32_t *off;    // level offsets into lvl (off[0] = 0, off[1] = 1)
+    int32_t *cnt3;   // rotating append counters
+    int32_t *levels; // out: number of levels
+    GridBarrier bar;
+    int32_t *err;
+    uint64_t limit_ns;
+};
+
+template <int LB>
+__global__ void __launch_bounds__(kCta) k_bc_fused(BcFusedArgs a) {
+    const BcState &s = a.s;
+    OpBFS op{s.depth, nullptr};
+    OutCtx out;
+    memset(&out, 0, sizeof(out));
+    out.mode = OUT_SPARSE;
+    out.dedup = DD_NONE;
+    out.err = a.err;
+    int32_t b = 0, e = 1, d = 0;
+    // forward: discovery, barrier, sigma of the new level, barrier
+    for (;; ++d) {
+        FrontierIn fin{s.lvl + b, e - b, nullptr};
+        out.q = s.lvl + e;
+        out.cnt = a.cnt3 + d % 3;
+        out.cap = s.g.n - e;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt3[(d + 1) % 3] = 0;
+        if (LB == G2_LB_WM) lb_warp(s.g, fin, e - b, op, out, blockIdx.x, gridDim.x, nullptr);
+        else if (LB == G2_LB_CM) lb_cta(s.g, fin, e - b, op, out, blockIdx.x, gridDim.x, nullptr);
+        else if (LB == G2_LB_ETWC) lb_etwc(s.g, fin, e - b, op, out, blockIdx.x, gridDim.x, nullptr);
+        else lb_vertex(s.g, fin, e - b, op, out, blockIdx.x, gridDim.x, nullptr);
+        if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+        const int32_t nn = ld_relaxed_i32(a.cnt3 + d % 3);
+        if (nn == 0) break;
+        bc_level_pass<true>(s, s.lvl + e, nn, d, blockIdx.x, gridDim.x);
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.off[d + 2] = e + nn;
+        if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+        b = e;
+        e += nn;
+    }
+    // levels 0..d, lists off[0..d+1]; backward from the deepest but one
+    for (int32_t L = d - 1; L >= 0; --L) {
+        const int32_t lb0 = ld_relaxed_i32(a.off + L), lb1 = ld_relaxed_i32(a.off + L + 1);
+        bc_level_pass<false>(s, s.lvl + lb0, lb1 - lb0, L, blockIdx.x, gridDim.x);
+        if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.levels = d + 1;
+}
+
+// ------------------------------------------------------------------- host
+static g2_status bc_one_plain(g2_graph *g, const BcState &s, const g2_hybrid &h,
+                              std::vector<int32_t> &off, cudaStream_t st, int32_t *d_err) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    int32_t *ctrs = d_err - 62;
+    uint32_t *bm;
+    uint8_t *bo;
+    G2_TRY(ws(g, B_BM0, (size_t)(n + 31) / 32 + 1, &bm));
+    G2_TRY(ws(g, B_BOOL0, (size_t)std::max(n, 1), &bo));
+    k_bc_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(s, n, nullptr);
+    stats().launches += 1;
+    off.assign(1, 0);
+    off.push_back(1);
+    for (int d = 0;; ++d) {
+        int32_t b = off[d], e = off[d + 1];
+        int32_t size = e - b;
+        const g2_schedule &sc = pick_schedule(h, size, n);
+        G2_TRY(check_schedule(g, sc, K_BFS, false));
+        if (sc.load_balance == G2_LB_EDGE_ONLY)
+            return fail(G2_EUNSUPPORTED, "BC's BFS is frontier-driven; EDGE_ONLY is for full sweeps");
+        VSet in{OUT_SPARSE, s.lvl + b, size, nullptr, nullptr, nullptr, size};
+        if (sc.direction == G2_PULL) {
+            int want = sc.pull_frontier == G2_BITMAP ? OUT_BITMAP : OUT_BOOLMAP;
+            VSet tt{want, nullptr, 0, nullptr, bm, bo, size};
+            G2_TRY(vset_convert(g, in, want, tt, st));
+            in = tt;
+        }
+        OpArgs a;
+        memset(&a, 0, sizeof(a));
+        a.kind = K_BFS;
+        a.i0 = s.depth;
+        a.err = d_err;
+        a.threshold = G2_INF32;
+        OutArgs o;
+        memset(&o, 0, sizeof(o));
+        o.rep = OUT_SPARSE;  // the level lists are needed for the backward pass
+        o.q = s.lvl + e;
+        o.qcap = n - e;
+        o.cnt = ctrs + 3;
+        o.dedup = DD_NONE;
+        G2_CK(cudaMemsetAsync(o.cnt, 0, 4, st));
+        G2_TRY(apply_round(g, sc, a, in, o, st));
+        sc.direction == G2_PUSH ? stats().push_rounds++ : stats().pull_rounds++;
+        G2_TRY(read_counters(g, ctrs, 4, st, d_err));
+        int32_t nn = g->h_ctr[3];
+        if (nn == 0) break;
+        k_bc_level<true><<<grid_for(g, (int64_t)nn * 32, kCta), kCta, 0, st>>>(s, s.lvl + e, nn, d);
+        stats().launches += 1;
+        stats().iterations++;
+        off.push_back(e + nn);
+    }
+    const int D = (int)off.size() - 1;  // number of levels
+    for (int L = D - 2; L >= 0; --L) {
+        int32_t cnt = off[L + 1] - off[L];
+        k_bc_level<false><<<grid_for(g, (int64_t)cnt * 32, kCta), kCta, 0, st>>>(s, s.lvl + off[L],
+                                                                                cnt, L);
+        stats().launches += 1;
+    }
+    G2_CK(cudaGetLastError());
+    return G2_OK;
+}
+
+static g2_status bc_one_fused(g2_graph *g, const BcState &s, const g2_schedule &sc, cudaStream_t st,
+                              int32_t *d_err) {
+    switch (sc.load_balance) {
+        case G2_LB_VERTEX_BASED: case G2_LB_WM: case G2_LB_CM: case G2_LB_ETWC: break;
+        default:
+            return fail(G2_EUNSUPPORTED, "fused BC supports VERTEX_BASED, WM, CM and ETWC");
+    }
+    if (sc.direction != G2_PUSH) return fail(G2_EUNSUPPORTED, "fused BC runs PUSH discovery");
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    int32_t *ctrs = d_err - 62;
+    int32_t *off;
+    G2_TRY(ws(g, B_I1, (size_t)n + 2, &off));
+    BcFusedArgs a;
+    a.s = s;
+    a.off = off;
+    a.cnt3 = ctrs + 20;
+    a.levels = ctrs + 24;
+    a.bar = GridBarrier{reinterpret_cast<unsigned *>(ctrs + 28), reinterpret_cast<unsigned *>(ctrs + 29)};
+    a.err = d_err;
+    a.limit_ns = 2000000000ULL;
+    k_bc_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(s, n, ctrs + 20);
+    int32_t init_off[2] = {0, 1};
+    G2_CK(cudaMemcpyAsync(off, init_off, 8, cudaMemcpyHostToDevice, st));
+    G2_CK(cudaMemsetAsync(ctrs + 28, 0, 8, st));  // barrier words
+    auto launch = [&](auto kern) -> g2_status {
+        int per_sm = 0;
+        G2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCta, 0));
+        if (per_sm < 1) return fail(G2_EUNSUPPORTED, "fused BC kernel does not fit on an SM");
+        void *params[] = {&a};
+        G2_CK(cudaLaunchCooperativeKernel((const void *)kern, dim3(t->sm_count), dim3(kCta), params, 0,
+                                          st));
+        return G2_OK;
+    };
+    switch (sc.load_balance) {
+        case G2_LB_WM: G2_TRY(launch(k_bc_fused<G2_LB_WM>)); break;
+        case G2_LB_CM: G2_TRY(launch(k_bc_fused<G2_LB_CM>)); break;
+        case G2_LB_ETWC: G2_TRY(launch(k_bc_fused<G2_LB_ETWC>)); break;
+        default: G2_TRY(launch(k_bc_fused<G2_LB_VERTEX_BASED>)); break;
+    }
+    stats().launches += 2;
+    G2_TRY(read_counters(g, ctrs + 24, 1, st, d_err));
+    stats().iterations += g->h_ctr[0];
+    stats().barriers += 3 * g->h_ctr[0];
+    return G2_OK;
+}
+
+g2_status bc_run(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const g2_hybrid &h,
+                 cudaStream_t st, int32_t *d_err) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    BcState s;
+    s.g = t->view();
+    s.bc = bc;
+    G2_TRY(ws(g, B_I0, (size_t)std::max(n, 1), &s.depth));
+    G2_TRY(ws(g, B_LVL, (size_t)std::max(n, 1), &s.lvl));
+    G2_TRY(ws(g, B_D0, (size_t)std::max(n, 1), &s.sm));
+    G2_TRY(ws(g, B_D1, (size_t)std::max(n, 1), &s.delta));
+    G2_TRY(ws(g, B_F2, (size_t)std::max(n, 1), &s.se));
+    G2_CK(cudaMemsetAsync(bc, 0, (size_t)n * 8, st));
+    std::vector<int32_t> off;
+    for (int32_t i = 0; i < k; ++i) {
+        s.src = srcs[i];
+        if (h.s1.kernel_fusion) G2_TRY(bc_one_fused(g, s, h.s1, st, d_err));
+        else G2_TRY(bc_one_plain(g, s, h, off, st, d_err));
+        G2_TRY(sync_and_check(g, st, d_err));
+    }
+    return G2_OK;
+}
+
+}  // namespace g2
+
+using namespace g2;
+
+// Tuned schedule when the caller passes none: the direction-optimising
+// hybrid of BFS (STRICT PUSH below 2% of n, VERTEX_BASED PULL over a bitmap).
+static g2_hybrid tuned_bc_hybrid() {
+    g2_hybrid h = default_hybrid();
+    h.criteria = G2_INPUT_VERTEXSET_SIZE;
+    h.threshold = 0.02f;
+    h.s1.load_balance = G2_LB_STRICT;
+    h.s2.load_balance = G2_LB_VERTEX_BASED;
+    h.s2.direction = G2_PULL;
+    h.s2.pull_frontier = G2_BITMAP;
+    h.s2.dedup = G2_DEDUP_DISABLED;
+    return h;
+}
+
+extern "C" g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc,
+                           const g2_hybrid *sched, void *stream) {
+    if (!g || !bc || (k > 0 && !srcs) || k < 0) return fail(G2_EINVAL, "bad BC arguments");
+    for (int32_t i = 0; i < k; ++i)
+        if (srcs[i] < 0 || srcs[i] >= g->topo->n) return fail(G2_EINVAL, "source vertex out of range");
+    cudaStream_t st = as_stream(stream);
+    g2_hybrid h = sched ? *sched : tuned_bc_hybrid();
+    if (h.s1.kernel_fusion && h.criteria != G2_CRITERIA_NONE && !h.s2.kernel_fusion)
+        return fail(G2_EUNSUPPORTED, "kernel fusion must be set on both hybrid schedules");
+    int32_t *d_err;
+    G2_TRY(begin_call(g, st, &d_err));
+    G2_TRY(bc_run(g, srcs, k, bc, h, st, d_err));
+    return end_call(g, st, d_err);
+}

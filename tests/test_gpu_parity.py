@@ -278,7 +278,9 @@ def test_bc(g2, rmat14):
     want = oracle.bc_graph(g, srcs)
     dg = g2.load_graph(g)
     for s in (None, g2.schedule("ETWC"), g2.schedule("VERTEX_BASED"),
-              g2.hybrid(g2.schedule("WM"), pull_sched(g2, "VERTEX_BASED", g2.G2_BITMAP, g2.G2_FUSED), 0.05)):
+              g2.hybrid(g2.schedule("WM"), pull_sched(g2, "VERTEX_BASED", g2.G2_BITMAP, g2.G2_FUSED), 0.05),
+              g2.schedule("VERTEX_BASED", kernel_fusion=True), g2.schedule("WM", kernel_fusion=True),
+              g2.schedule("CM", kernel_fusion=True), g2.schedule("ETWC", kernel_fusion=True)):
         bc = dev(g.n, torch.float64)
         g2.g2_bc(dg, srcs, bc, s)
         assert bc_close(host(bc), want)
@@ -288,6 +290,22 @@ def test_bc(g2, rmat14):
         bc = dev(g.n, torch.float64)
         g2.g2_bc(g2.load_graph(g), srcs, bc, g2.schedule("CM"))
         assert bc_close(host(bc), want), g.name
+
+
+def test_bc_level_spread_beyond_fp64(g2):
+    """Full 1200 x 1200 grid from a corner: on level k the path counts run
+    from 1 (the border) to about C(k, k/2), more than 2^1074 apart near k = 1199,
+    so no common scale per level keeps all of them in fp64; per-vertex
+    exponents do.  Plain and fused against the long double oracle."""
+    g = gg.full_grid(1200, 1200)
+    want = oracle.bc_graph(g, [0])
+    dg = g2.load_graph(g)
+    for s in (None, g2.schedule("WM", kernel_fusion=True)):
+        bc = dev(g.n, torch.float64)
+        g2.g2_bc(dg, [0], bc, s)
+        got = host(bc)
+        assert np.all(np.isfinite(got))
+        assert bc_close(got, want)
 
 
 def test_bc_path_counts_beyond_fp64(g2):
