@@ -186,7 +186,7 @@ class GpuExecutor:
                     g2.g2_sssp_batch(view, srcs, pg.spec.delta, out, None)
             else:
                 out = torch.empty(n, dtype=torch.float64, device="cuda")
-                g2.g2_bc(view, srcs, out, None)
+                g2.g2_bc(view, srcs, out, single)
             if self.keep_results:
                 host = out.cpu().numpy()
                 rows = host.reshape(k, n) if r0.kind != "bc" else host.reshape(1, n)
