@@ -414,15 +414,16 @@ __device__ __forceinline__ float ld_no_allocate(const float *p) {
     return v;
 }
 
-// Share of slot u: the hottest slots from shared memory, the next tier
-// [hot, warm) through L1 with evict-last priority, the rest without L1
-// allocation so that the cold stream does not evict the warm tier.
+// Share of slot u: the hottest slots from shared memory, an optional next
+// tier [hot, warm) through L1 with evict-last priority, the rest through the
+// read-only path.  (Loading the cold rest without L1 allocation was measured
+// to lower the L2 hit rate and raise DRAM reads by half, so it is not used.)
 template <bool HOT>
 __device__ __forceinline__ float seg_gather(const float *contrib, const float *s_hot, int32_t hot,
                                             int32_t warm, int32_t u) {
     if (HOT && u < hot) return s_hot[u];
     if (u < warm) return ld_evict_last(contrib + u);
-    return HOT ? ld_no_allocate(contrib + u) : __ldg(contrib + u);
+    return __ldg(contrib + u);
 }
 
 template <int CTA, bool HOT>
@@ -717,9 +718,9 @@ static g2_status launch_pr_seg(g2_graph *g, const int32_t *pcol, int32_t hot, co
     if (b < 1) return fail(G2_EUNSUPPORTED, "PageRank sweep kernel does not fit on an SM");
     int64_t want = (nchunks * 32 + CTA - 1) / CTA;
     int grid = (int)std::min<int64_t>(want, (int64_t)b * t->sm_count);
-    // slots [hot, warm) are loaded with L1 evict-last priority; 131,072 slots
-    // measured best on RMAT-22 (about 3% over plain loads; G2_PR_WARM overrides)
-    int32_t warm = std::max<int32_t>(hot, 131072);
+    // slots [hot, warm) are loaded with L1 evict-last priority (off by
+    // default: warm = hot; G2_PR_WARM sets it for sweeps)
+    int32_t warm = hot;
     if (const char *e = getenv("G2_PR_WARM")) warm = std::max<int32_t>(hot, atoi(e));
     KTime kt;
     ktime_begin(kt, "pr_round", st);
