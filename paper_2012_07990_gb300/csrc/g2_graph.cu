@@ -648,11 +648,13 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     auto bail = [&](g2_status s) { g2_free_graph(g); return s; };
     cudaError_t e;
     if ((e = cudaGetDevice(&t->device)) != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
-    cudaDeviceProp prop;
-    if ((e = cudaGetDeviceProperties(&prop, t->device)) != cudaSuccess)
-        return bail(cuda_fail(e, "cudaGetDeviceProperties"));
-    t->sm_count = prop.multiProcessorCount;
-    t->l2_bytes = prop.l2CacheSize;
+    // two attribute queries (the full property query costs milliseconds)
+    int sms = 0, l2 = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, t->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, t->device)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
+    t->sm_count = sms;
+    t->l2_bytes = l2;
     t->max_coop_blocks = 0;
     if (finish_handle(g) != G2_OK) return bail(G2_ENOMEM);
     // every array carries kPad spare elements (zeroed) so that a 16-byte
@@ -663,9 +665,11 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
         return bail(cuda_fail(e, "cudaMalloc rowptr"));
     if ((e = cudaMalloc(&t->col, mb)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc col"));
     if (w && (e = cudaMalloc(&t->w, mb)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc w"));
-    cudaMemsetAsync(t->rowptr, 0, rb, st);
-    cudaMemsetAsync(t->col, 0, mb, st);
-    if (w) cudaMemsetAsync(t->w, 0, mb, st);
+    // zero the padding past the copied elements (the copies below fill the rest)
+    const size_t mcopy = (size_t)m * 4, rcopy = ((size_t)n + 1) * 4;
+    cudaMemsetAsync(reinterpret_cast<char *>(t->rowptr) + rcopy, 0, rb - rcopy, st);
+    cudaMemsetAsync(reinterpret_cast<char *>(t->col) + mcopy, 0, mb - mcopy, st);
+    if (w) cudaMemsetAsync(reinterpret_cast<char *>(t->w) + mcopy, 0, mb - mcopy, st);
     if ((e = cudaMemcpyAsync(t->rowptr, rowptr, ((size_t)n + 1) * 4, kind, st)) != cudaSuccess)
         return bail(cuda_fail(e, "copy rowptr"));
     if (m > 0 && (e = cudaMemcpyAsync(t->col, col, (size_t)m * 4, kind, st)) != cudaSuccess)

@@ -4,17 +4,17 @@
 // D = total rank of the vertices without out-arcs (spread uniformly).
 //
 // Schedules:
-//  PULL + EDGE_ONLY (the default): arc-balanced segmented sums over the CSC.
-//    Rows and arcs are merged into one sequence of n + m items (merge-path
-//    partitioning) cut into equal tiles, so every CTA gets the same share of
-//    row ends and arcs whatever the degree distribution; no atomics except
-//    for the few rows cut by a tile boundary.  Each tile's arc slice and row
-//    ends arrive by TMA bulk copies, double-buffered against the previous
-//    tile's work.  The next round's per-source shares and the dangling mass
-//    are produced in the same pass.  Optionally the shares of the H
-//    highest-degree vertices are held in shared memory for the whole launch
+//  PULL + EDGE_ONLY (the default): arc-balanced sums over the CSC.  The tuned
+//    kernel is a segmented sweep (g2_pr_seg.cuh): every warp takes 128
+//    consecutive arcs, gathers their shares and adds them per row with a
+//    warp segmented scan over precomputed row-head flags; a vertex pass then
+//    forms x_t, the next shares and the next dangling mass.  The shares of the
+//    H highest-degree vertices are held in shared memory for the whole launch
 //    (a one-time layout step renumbers the CSC's column ids so that those
-//    vertices come first); the other gathers go through L1/L2.
+//    vertices come first); the other gathers go through L1/L2.  A merge-path
+//    tile kernel (rows and arcs merged into one sequence of n + m items cut
+//    into equal tiles, arc slices and row ends brought in by TMA bulk copies,
+//    double-buffered) is kept as the alternative (G2_PR_KERNEL=merge).
 //  PULL + VERTEX_BASED / WM / CM: one thread / warp / CTA per destination.
 //  PUSH + any load balancing over the all-vertices frontier, including
 //    EDGE_ONLY with EdgeBlocking (Algorithms 1-2): arc-parallel atomic adds.
@@ -28,6 +28,7 @@
 
 #include "g2_host.h"
 #include "g2_lb.cuh"
+#include "g2_pr_seg.cuh"
 
 namespace g2 {
 
@@ -329,19 +330,63 @@ __global__ void __launch_bounds__(kCta) k_pr_fixup(PrArgs a, const int32_t *rows
     block_add_double(dsum, a.dnext);
 }
 
-// x0 = 1/n: contrib0[slot(u)] = (1/n)/outdeg(u); D0 = (#vertices without out-arcs)/n
-__global__ void __launch_bounds__(kCta) k_pr_init(const int32_t *rowptr, int32_t n,
-                                                  const int32_t *perm, float *contrib, double *d0,
-                                                  float *x, double inv_n) {
-    double dsum = 0.0;
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        int32_t od = rowptr[u + 1] - rowptr[u];
-        contrib[perm ? perm[u] : u] = od > 0 ? (float)(inv_n / od) : 0.f;
-        if (od == 0) dsum += inv_n;
-        if (x) x[u] = (float)inv_n;
+// The dangling mass D is accumulated in kDSlots slots (one per 128-byte line)
+// instead of one word, so the per-CTA atomics of a pass spread over many L2
+// lines instead of serialising on one address; readers add the slots up.
+constexpr int kDSlots = 64;
+constexpr int kDStride = 16;  // doubles between slots
+
+// Out-degrees of the four vertices v0..v0+3 and their share slots (slot =
+// perm[v], or v without a hot layout); 16-byte loads for a full quad.
+struct PrQuad {
+    int32_t od[4], sl[4];
+};
+
+__device__ __forceinline__ void pr_load_quad(const int32_t *rowptr, const int32_t *perm, int32_t n,
+                                             int64_t v0, PrQuad &q) {
+    if (v0 + 4 <= n) {
+        int4 r4 = __ldg(reinterpret_cast<const int4 *>(rowptr + v0));
+        int32_t r5 = __ldg(rowptr + v0 + 4);
+        q.od[0] = r4.y - r4.x;
+        q.od[1] = r4.z - r4.y;
+        q.od[2] = r4.w - r4.z;
+        q.od[3] = r5 - r4.w;
+        if (perm) {
+            int4 p4 = __ldg(reinterpret_cast<const int4 *>(perm + v0));
+            q.sl[0] = p4.x; q.sl[1] = p4.y; q.sl[2] = p4.z; q.sl[3] = p4.w;
+        } else {
+            for (int k = 0; k < 4; ++k) q.sl[k] = (int32_t)(v0 + k);
+        }
+    } else {
+        for (int k = 0; k < 4; ++k) {
+            const bool in = v0 + k < n;
+            q.od[k] = in ? rowptr[v0 + k + 1] - rowptr[v0 + k] : 0;
+            q.sl[k] = in ? (perm ? perm[v0 + k] : (int32_t)(v0 + k)) : 0;
+        }
     }
-    block_add_double(dsum, d0);
+}
+
+// x0 = 1/n: contrib0[slot(u)] = (1/n)/outdeg(u); D0 = (#vertices without
+// out-arcs)/n, added into slot (block & dmask) of d0 (dmask 0: one word).
+// Grid-stride over quads of four consecutive vertices.
+__global__ void __launch_bounds__(kCta) k_pr_init(const int32_t *rowptr, int32_t n,
+                                                    const int32_t *perm, float *contrib, double *d0,
+                                                    int dmask, float *x, double inv_n) {
+    double dsum = 0.0;
+    const float x0 = (float)inv_n;
+    for (int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; v0 < n;
+         v0 += (int64_t)gridDim.x * blockDim.x * 4) {
+        PrQuad q;
+        pr_load_quad(rowptr, perm, n, v0, q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (v0 + k >= n) break;
+            contrib[q.sl[k]] = q.od[k] > 0 ? (float)(inv_n / q.od[k]) : 0.f;
+            if (q.od[k] == 0) dsum += inv_n;
+            if (x) x[v0 + k] = x0;
+        }
+    }
+    block_add_double(dsum, d0 + (blockIdx.x & dmask) * kDStride);
 }
 
 // generic schedules: x from the accumulated sums, next shares, next D
@@ -371,16 +416,6 @@ __global__ void k_remap_cols(const int32_t *ccol, const int32_t *perm, int32_t m
         out[e] = perm[ccol[e]];
 }
 
-// ------------------------------------------------ segmented arc sweep
-// A warp takes 128 consecutive CSC arcs (one int4 of column ids per lane),
-// gathers their shares, and sums them per row with a warp segmented scan
-// whose segment starts are precomputed row-head flags (bit e set iff arc e is
-// the first in-arc of its row).  Row ids come from the rank of each head:
-// the k-th head overall starts row nzrow[k].  Sums are added with
-// fire-and-forget reductions into y (zeroed again by the vertex pass), so no
-// block barrier or search is needed anywhere.
-constexpr int kSegArcs = 128;  // arcs per warp chunk
-
 __global__ void k_seg_heads(const int32_t *crowptr, int32_t n, uint32_t *head, int32_t *nz) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -403,194 +438,59 @@ __global__ void k_seg_chunk_heads(const uint32_t *head, int64_t nchunks, int32_t
                  __popc(head[4 * c + 3]);
 }
 
-__device__ __forceinline__ float ld_evict_last(const float *p) {
-    float v;
-    asm volatile("ld.global.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ float ld_no_allocate(const float *p) {
-    float v;
-    asm volatile("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
-
-// Share of slot u: the hottest slots from shared memory, an optional next
-// tier [hot, warm) through L1 with evict-last priority, the rest through the
-// read-only path.  (Loading the cold rest without L1 allocation was measured
-// to lower the L2 hit rate and raise DRAM reads by half, so it is not used.)
-template <bool HOT>
-__device__ __forceinline__ float seg_gather(const float *contrib, const float *s_hot, int32_t hot,
-                                            int32_t warm, int32_t u) {
-    if (HOT && u < hot) return s_hot[u];
-    if (u < warm) return ld_evict_last(contrib + u);
-    return __ldg(contrib + u);
-}
-
-template <int CTA, bool HOT>
-__global__ void __launch_bounds__(CTA) k_pr_seg(const int32_t *pcol, const uint32_t *head,
-                                                const int32_t *chunk_rank, const int32_t *nzrow,
-                                                int32_t m, int64_t nchunks, const float *contrib,
-                                                int32_t hot, int32_t warm, float *y) {
-    extern __shared__ float s_hot[];
-    if (HOT) {
-        for (int32_t i = threadIdx.x; i < hot; i += CTA) s_hot[i] = __ldg(contrib + i);
-        __syncthreads();
-    }
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * CTA + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * CTA) >> 5;
-    const int sh = (lane & 7) * 4;
-    const unsigned below = (1u << sh) - 1u;
-    // software pipeline: the next chunk's column ids and head words are
-    // loaded while this chunk's gathers are in flight
-    int4 nu4 = make_int4(0, 0, 0, 0);
-    uint4 nh = make_uint4(0, 0, 0, 0);
-    if (gw < nchunks) {
-        nu4 = reinterpret_cast<const int4 *>(pcol + gw * kSegArcs)[lane];
-        nh = reinterpret_cast<const uint4 *>(head)[gw];
-    }
-    for (int64_t c = gw; c < nchunks; c += nw) {
-        const int64_t b = c * kSegArcs;
-        const int4 u4 = nu4;
-        const uint32_t w0 = nh.x, w1 = nh.y, w2 = nh.z, w3 = nh.w;
-        if (c + nw < nchunks) {
-            nu4 = reinterpret_cast<const int4 *>(pcol + (c + nw) * kSegArcs)[lane];
-            nh = reinterpret_cast<const uint4 *>(head)[c + nw];
-        }
-        const int64_t a0 = b + 4 * lane;
-        float v0 = a0 + 0 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.x) : 0.f;
-        float v1 = a0 + 1 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.y) : 0.f;
-        float v2 = a0 + 2 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.z) : 0.f;
-        float v3 = a0 + 3 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.w) : 0.f;
-        const int wi = lane >> 3;
-        const uint32_t mine = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
-        const uint32_t hf = (mine >> sh) & 0xFu;
-        // heads before this lane in the chunk
-        int prefix = __popc(mine & below);
-        if (wi > 0) prefix += __popc(w0);
-        if (wi > 1) prefix += __popc(w1);
-        if (wi > 2) prefix += __popc(w2);
-        const int total_heads = __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3);
-        const int32_t base_rank = chunk_rank[c];
-        // lane-local pieces: A = arcs before the first head, inner complete
-        // segments, T = arcs from the last head on
-        float vals[4] = {v0, v1, v2, v3};
-        float A = 0.f, run = 0.f;
-        int seen = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if ((hf >> k) & 1u) {
-                if (seen == 0) {
-                    A = run;
-                } else if (run != 0.f) {
-                    // complete segment inside this lane: its head is the (seen-1)-th
-                    atomicAdd(y + nzrow[base_rank + prefix + seen - 1], run);
-                }
-                run = 0.f;
-                ++seen;
-            }
-            run += vals[k];
-        }
-        if (seen == 0) A = run;
-        const bool has_head = seen > 0;
-        const float T = has_head ? run : 0.f;
-        // segmented inclusive scan over lanes: q = T at a headed lane, else
-        // q(previous lane) + A
-        float q = has_head ? T : A;
-        bool f = has_head;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            float qo = __shfl_up_sync(G2_FULL, q, d);
-            bool fo = __shfl_up_sync(G2_FULL, f, d);
-            if (lane >= d && !f) {
-                q += qo;
-                f = fo;
-            }
-        }
-        float qprev = __shfl_up_sync(G2_FULL, q, 1);
-        if (lane == 0) qprev = 0.f;
-        if (has_head) {
-            // the segment that ends just before this lane's first head
-            float tot = qprev + A;
-            int32_t rk = base_rank + prefix - 1;
-            if (tot != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], tot);
-        }
-        if (lane == 31) {
-            // the segment that runs to the end of the chunk (may continue)
-            int32_t rk = base_rank + total_heads - 1;
-            if (q != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], q);
-        }
-    }
-}
-
-// The dangling mass D is accumulated in kDSlots slots (one per 128-byte line)
-// instead of one word, so the per-CTA atomics of a pass spread over many L2
-// lines instead of serialising on one address; readers add the slots up.
-constexpr int kDSlots = 64;
-constexpr int kDStride = 16;  // doubles between slots
-
+// D/n for this round, added up from the kDSlots slots by every warp on its
+// own (no block barrier, so a warp's vertex loads are not held back by it).
+// Every lane of the warp must call it.
 __device__ __forceinline__ float pr_dterm(const double *d, double inv_n) {
-    __shared__ float s_dterm;
-    if (threadIdx.x < 32) {
-        double v = d[threadIdx.x * kDStride] + d[(threadIdx.x + 32) * kDStride];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(G2_FULL, v, o);
-        if (threadIdx.x == 0) s_dterm = (float)(v * inv_n);
-    }
-    __syncthreads();
-    return s_dterm;
+    const int lane = threadIdx.x & 31;
+    double v = d[lane * kDStride] + d[(lane + 32) * kDStride];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(G2_FULL, v, o);
+    return (float)(v * inv_n);
 }
 
 // vertex pass after a segmented sweep: x, next shares, next D; y back to zero.
 // Four consecutive vertices per thread with 16-byte loads, every vertex in
-// its own thread group, so the pass has the memory parallelism to stream.
+// its own thread group, so the pass has the memory parallelism to stream; a
+// thread issues its loads before it reads D, and no block barrier comes
+// before the stores.
 __global__ void __launch_bounds__(kCta) k_pr_seg_vertex(const int32_t *rowptr, int32_t n,
                                                         const int32_t *perm, float *y,
                                                         float *contrib_next, float *x, int write_x,
                                                         const double *dprev, double *dnext,
                                                         float base, float damp, double inv_n) {
-    const float dterm = pr_dterm(dprev, inv_n);
     double dsum = 0.0;
     const int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    float yv[4] = {0.f, 0.f, 0.f, 0.f};
+    PrQuad q;
     if (v0 < n) {
-        float yv[4];
-        int32_t rp[5], sl[4];
+        pr_load_quad(rowptr, perm, n, v0, q);
         if (v0 + 4 <= n) {
             float4 y4 = *reinterpret_cast<const float4 *>(y + v0);
-            int4 r4 = __ldg(reinterpret_cast<const int4 *>(rowptr + v0));
             yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
-            rp[0] = r4.x; rp[1] = r4.y; rp[2] = r4.z; rp[3] = r4.w;
-            rp[4] = __ldg(rowptr + v0 + 4);
-            if (perm) {
-                int4 p4 = __ldg(reinterpret_cast<const int4 *>(perm + v0));
-                sl[0] = p4.x; sl[1] = p4.y; sl[2] = p4.z; sl[3] = p4.w;
-            } else {
-                for (int k = 0; k < 4; ++k) sl[k] = (int32_t)(v0 + k);
-            }
-            *reinterpret_cast<float4 *>(y + v0) = make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
-            for (int k = 0; k < 4; ++k) {
-                bool in = v0 + k < n;
-                yv[k] = in ? y[v0 + k] : 0.f;
-                rp[k] = in ? rowptr[v0 + k] : 0;
-                sl[k] = in ? (perm ? perm[v0 + k] : (int32_t)(v0 + k)) : 0;
-                if (in) y[v0 + k] = 0.f;
-            }
-            rp[4] = 0;
             for (int k = 0; k < 4; ++k)
-                if (v0 + k < n) rp[k + 1] = rowptr[v0 + k + 1];
+                if (v0 + k < n) yv[k] = y[v0 + k];
         }
+    }
+    const float dterm = pr_dterm(dprev, inv_n);
+    if (v0 < n) {
         float xs[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (v0 + k >= n) break;
             float xr = base + damp * (yv[k] + dterm);
-            int32_t od = rp[k + 1] - rp[k];
-            if (od > 0) contrib_next[sl[k]] = xr / (float)od;
+            if (q.od[k] > 0) contrib_next[q.sl[k]] = xr / (float)q.od[k];
             else {
-                contrib_next[sl[k]] = 0.f;
+                contrib_next[q.sl[k]] = 0.f;
                 dsum += xr;
             }
             xs[k] = xr;
+        }
+        if (v0 + 4 <= n) {
+            *reinterpret_cast<float4 *>(y + v0) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            for (int k = 0; k < 4; ++k)
+                if (v0 + k < n) y[v0 + k] = 0.f;
         }
         if (write_x) {
             // x is the caller's array: vector stores only when 16-byte aligned
@@ -628,10 +528,154 @@ static PrCfg pr_config(const g2_graph *g) {
     return c;
 }
 
-// Renumbering for the shared-memory share cache: the `hot` vertices of highest
-// degree (ties to the lower id) get slots 0..hot-1 in that order, the others
-// follow in id order.  perm and the renumbered column ids are built once and
-// kept with the topology.
+// ------------------------------------------------ hot-vertex selection
+// The shared-memory share cache holds the slots 0..hot-1: the `hot` vertices
+// of highest out-degree get them (ties to the lower ids), the others follow in
+// id order.  The selection runs on the device: a 256-bin histogram of the
+// degrees (exact below 16, then 8 bins per power of two) finds the bin that
+// holds the hot-th largest degree, a second histogram of up to 4,096 bins
+// inside that bin narrows it to one degree (one bin of 2^shift degrees above
+// 2^15), and two scans give each vertex its slot.  Which vertices share a
+// slot range does not change any sum: the sweep adds each row's arcs in CSC
+// order whatever the slot numbers are.
+constexpr int kHotBins1 = 256;
+constexpr int kHotBins2 = 4096;
+
+__host__ __device__ inline int hot_bin(int32_t d) {
+    if (d < 16) return d;
+#ifdef __CUDA_ARCH__
+    const int e = 31 - __clz(d);  // floor(log2 d), 4..30
+#else
+    const int e = 31 - __builtin_clz((unsigned)d);
+#endif
+    return 16 + 8 * (e - 4) + ((d >> (e - 3)) & 7);
+}
+
+// first degree of coarse bin b and its width (a power of two)
+static inline void hot_bin_range(int b, int64_t *lo, int64_t *width) {
+    if (b < 16) {
+        *lo = b;
+        *width = 1;
+        return;
+    }
+    const int e = 4 + (b - 16) / 8, k = (b - 16) % 8;
+    *width = (int64_t)1 << (e - 3);
+    *lo = ((int64_t)1 << e) + k * *width;
+}
+
+__global__ void __launch_bounds__(kCta) k_hot_hist1(const int32_t *rowptr, int32_t n, int32_t *hist) {
+    __shared__ int32_t s[kHotBins1];
+    for (int i = threadIdx.x; i < kHotBins1; i += blockDim.x) s[i] = 0;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        atomicAdd(&s[hot_bin(__ldg(rowptr + v + 1) - __ldg(rowptr + v))], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHotBins1; i += blockDim.x)
+        if (s[i]) atomicAdd(hist + i, s[i]);
+}
+
+// histogram of (d - lo) >> shift over the degrees d in [lo, lo + width)
+__global__ void __launch_bounds__(kCta) k_hot_hist2(const int32_t *rowptr, int32_t n, int64_t lo,
+                                                    int64_t width, int shift, int32_t *hist) {
+    __shared__ int32_t s[kHotBins2];
+    for (int i = threadIdx.x; i < kHotBins2; i += blockDim.x) s[i] = 0;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = __ldg(rowptr + v + 1) - __ldg(rowptr + v);
+        if (d >= lo && d < lo + width) atomicAdd(&s[(int)((d - lo) >> shift)], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHotBins2; i += blockDim.x)
+        if (s[i]) atomicAdd(hist + i, s[i]);
+}
+
+// tie[v] = 1 iff tlo <= deg(v) < thi
+__global__ void k_hot_ties(const int32_t *rowptr, int32_t n, int64_t tlo, int64_t thi,
+                           int32_t *tie) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = rowptr[v + 1] - rowptr[v];
+        tie[v] = d >= tlo && d < thi;
+    }
+}
+
+// hot[v] = deg(v) >= thi, or a tie among the first `need` ties by id
+__global__ void k_hot_flags(const int32_t *rowptr, int32_t n, int64_t tlo, int64_t thi,
+                            const int32_t *tie_rank, int32_t need, int32_t *hot) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = rowptr[v + 1] - rowptr[v];
+        hot[v] = d >= thi || (d >= tlo && tie_rank[v] < need);
+    }
+}
+
+// slot of v: its rank among the hot vertices, or hot + its rank among the rest
+__global__ void k_hot_perm(const int32_t *hotf, int32_t n, int32_t hot, int32_t *perm) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = perm[v];  // hot vertices before v
+        perm[v] = hotf[v] ? r : hot + (int32_t)v - r;
+    }
+}
+
+// Slot map perm (n entries, plus one spare for the scan total) of the `hot`
+// highest-degree vertices; 0 < hot <= n.
+static g2_status select_hot(g2_graph *g, int32_t hot, int32_t *perm, cudaStream_t st) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    int32_t *hist, *a, *b;
+    G2_TRY(ws(g, B_TWC_M, kHotBins1 + kHotBins2, &hist));
+    G2_TRY(ws(g, B_I0, (size_t)n + 1, &a));
+    G2_TRY(ws(g, B_I1, (size_t)n + 1, &b));
+    G2_CK(cudaMemsetAsync(hist, 0, (kHotBins1 + kHotBins2) * sizeof(int32_t), st));
+    const int grid = grid_for(g, n, kCta);
+    k_hot_hist1<<<grid, kCta, 0, st>>>(t->rowptr, n, hist);
+    std::vector<int32_t> h1(kHotBins1);
+    G2_CK(cudaMemcpyAsync(h1.data(), hist, kHotBins1 * 4, cudaMemcpyDeviceToHost, st));
+    G2_CK(cudaStreamSynchronize(st));
+    // coarse bin holding the hot-th largest degree; c_above = vertices above it
+    int bsel = 0;
+    int64_t c_above = 0;
+    for (int k = kHotBins1 - 1; k >= 0; --k) {
+        if (c_above + h1[k] >= hot) {
+            bsel = k;
+            break;
+        }
+        c_above += h1[k];
+    }
+    int64_t lo, width;
+    hot_bin_range(bsel, &lo, &width);
+    int shift = 0;
+    while ((width >> shift) > kHotBins2) ++shift;
+    const int nb2 = (int)(width >> shift);
+    k_hot_hist2<<<grid, kCta, 0, st>>>(t->rowptr, n, lo, width, shift, hist + kHotBins1);
+    std::vector<int32_t> h2(nb2);
+    G2_CK(cudaMemcpyAsync(h2.data(), hist + kHotBins1, (size_t)nb2 * 4, cudaMemcpyDeviceToHost, st));
+    G2_CK(cudaStreamSynchronize(st));
+    int jsel = 0;
+    for (int k = nb2 - 1; k >= 0; --k) {
+        if (c_above + h2[k] >= hot) {
+            jsel = k;
+            break;
+        }
+        c_above += h2[k];
+    }
+    // degrees >= thi are hot; of those in [tlo, thi), the first `need` by id
+    const int64_t tlo = lo + ((int64_t)jsel << shift), thi = lo + ((int64_t)(jsel + 1) << shift);
+    const int32_t need = (int32_t)(hot - c_above);
+    k_hot_ties<<<grid, kCta, 0, st>>>(t->rowptr, n, tlo, thi, a);
+    G2_TRY(exclusive_scan_i32(g, a, b, n, st));
+    k_hot_flags<<<grid, kCta, 0, st>>>(t->rowptr, n, tlo, thi, b, need, a);
+    G2_TRY(exclusive_scan_i32(g, a, perm, n, st));
+    k_hot_perm<<<grid, kCta, 0, st>>>(a, n, hot, perm);
+    stats().launches += 6;
+    G2_CK(cudaGetLastError());
+    return G2_OK;
+}
+
 static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, const int32_t **perm,
                                       const int32_t **ccol) {
     Topology *t = g->topo;
@@ -641,28 +685,15 @@ static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, con
         return G2_OK;
     }
     const int32_t n = t->n, m = t->m;
-    std::vector<int32_t> rp((size_t)n + 1);
-    G2_CK(cudaMemcpyAsync(rp.data(), t->rowptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, st));
-    G2_CK(cudaStreamSynchronize(st));
-    std::vector<int32_t> order((size_t)n);
-    std::iota(order.begin(), order.end(), 0);
-    auto deg = [&](int32_t v) { return rp[v + 1] - rp[v]; };
-    std::partial_sort(order.begin(), order.begin() + hot, order.end(), [&](int32_t a, int32_t b) {
-        int32_t da = deg(a), db = deg(b);
-        return da != db ? da > db : a < b;
-    });
-    std::vector<int32_t> perm_h((size_t)n, -1);
-    for (int32_t i = 0; i < hot; ++i) perm_h[order[i]] = i;
-    int32_t next = hot;
-    for (int32_t v = 0; v < n; ++v)
-        if (perm_h[v] < 0) perm_h[v] = next++;
     if (t->pr_perm) cudaFree(t->pr_perm);
     if (t->pr_ccol) cudaFree(t->pr_ccol);
     t->pr_perm = t->pr_ccol = nullptr;
-    G2_CK(cudaMalloc(&t->pr_perm, (size_t)std::max(n, 1) * 4));
+    t->pr_hot = -1;
+    G2_CK(cudaMalloc(&t->pr_perm, ((size_t)std::max(n, 1) + 1) * 4));
     G2_CK(cudaMalloc(&t->pr_ccol, ((size_t)std::max(m, 1) + kPad) * 4));
-    G2_CK(cudaMemsetAsync(t->pr_ccol, 0, ((size_t)std::max(m, 1) + kPad) * 4, st));
-    G2_CK(cudaMemcpyAsync(t->pr_perm, perm_h.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
+    G2_TRY(select_hot(g, hot, t->pr_perm, st));
+    // only the padding past the last arc needs zeroing; the arcs are all written
+    G2_CK(cudaMemsetAsync(t->pr_ccol + m, 0, ((size_t)std::max(m, 1) - m + kPad) * 4, st));
     if (m > 0)
         k_remap_cols<<<grid_for(g, m, kCta), kCta, 0, st>>>(t->ccol, t->pr_perm, m, t->pr_ccol);
     G2_CK(cudaGetLastError());
@@ -778,7 +809,13 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
     // vertex passes end with one fp64 atomic per CTA on a single address, and
     // same-address atomics serialise: few CTAs, each striding over many vertices
     const int vgrid = (int)std::min<int64_t>((n + kCta - 1) / kCta, (int64_t)t->sm_count * 2);
-    k_pr_init<<<vgrid, kCta, 0, st>>>(t->rowptr, n, perm, cbuf[0], dd, rank, inv_n);
+    // the segmented sweep's rounds read D over kDSlots slots, so its x0 pass
+    // runs on a full grid of quads and spreads D0 over them; the other paths
+    // read dd[0] alone
+    const bool seg = merge && !cfg.merge;
+    const int igrid = seg ? (int)((((int64_t)n + 3) / 4 + kCta - 1) / kCta) : vgrid;
+    k_pr_init<<<std::max(igrid, 1), kCta, 0, st>>>(t->rowptr, n, perm, cbuf[0], dd,
+                                                   seg ? kDSlots - 1 : 0, rank, inv_n);
     stats().launches += 1;
     if (iters <= 0) return G2_OK;
     if (merge && !cfg.merge) {

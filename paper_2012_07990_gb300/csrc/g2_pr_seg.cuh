@@ -1,0 +1,139 @@
+// g2_pr_seg.cuh — the PageRank arc sweep (Sec. VII: one PULL + EDGE_ONLY
+// round over the CSC; the vertex pass in g2_pr.cu finishes the rank update).
+// Kept in a file of its own so that a profile of this kernel can name the
+// exact source it was taken on.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "g2_device.cuh"
+
+namespace g2 {
+
+// ------------------------------------------------ segmented arc sweep
+// A warp takes 128 consecutive CSC arcs (one int4 of column ids per lane),
+// gathers their shares, and sums them per row with a warp segmented scan
+// whose segment starts are precomputed row-head flags (bit e set iff arc e is
+// the first in-arc of its row).  Row ids come from the rank of each head:
+// the k-th head overall starts row nzrow[k].  Sums are added with
+// fire-and-forget reductions into y (zeroed again by the vertex pass), so no
+// block barrier or search is needed anywhere.
+constexpr int kSegArcs = 128;  // arcs per warp chunk
+
+__device__ __forceinline__ float ld_evict_last(const float *p) {
+    float v;
+    asm volatile("ld.global.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+// Share of slot u: the hottest slots from shared memory, an optional next
+// tier [hot, warm) through L1 with evict-last priority, the rest through the
+// read-only path.  (Loading the cold rest without L1 allocation was measured
+// to lower the L2 hit rate and raise DRAM reads by half, so it is not used.)
+template <bool HOT>
+__device__ __forceinline__ float seg_gather(const float *contrib, const float *s_hot, int32_t hot,
+                                            int32_t warm, int32_t u) {
+    if (HOT && u < hot) return s_hot[u];
+    if (u < warm) return ld_evict_last(contrib + u);
+    return __ldg(contrib + u);
+}
+
+template <int CTA, bool HOT>
+__global__ void __launch_bounds__(CTA) k_pr_seg(const int32_t *pcol, const uint32_t *head,
+                                                const int32_t *chunk_rank, const int32_t *nzrow,
+                                                int32_t m, int64_t nchunks, const float *contrib,
+                                                int32_t hot, int32_t warm, float *y) {
+    extern __shared__ float s_hot[];
+    if (HOT) {
+        for (int32_t i = threadIdx.x; i < hot; i += CTA) s_hot[i] = __ldg(contrib + i);
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * CTA + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * CTA) >> 5;
+    const int sh = (lane & 7) * 4;
+    const unsigned below = (1u << sh) - 1u;
+    // software pipeline: the next chunk's column ids and head words are
+    // loaded while this chunk's gathers are in flight
+    int4 nu4 = make_int4(0, 0, 0, 0);
+    uint4 nh = make_uint4(0, 0, 0, 0);
+    if (gw < nchunks) {
+        nu4 = reinterpret_cast<const int4 *>(pcol + gw * kSegArcs)[lane];
+        nh = reinterpret_cast<const uint4 *>(head)[gw];
+    }
+    for (int64_t c = gw; c < nchunks; c += nw) {
+        const int64_t b = c * kSegArcs;
+        const int4 u4 = nu4;
+        const uint32_t w0 = nh.x, w1 = nh.y, w2 = nh.z, w3 = nh.w;
+        if (c + nw < nchunks) {
+            nu4 = reinterpret_cast<const int4 *>(pcol + (c + nw) * kSegArcs)[lane];
+            nh = reinterpret_cast<const uint4 *>(head)[c + nw];
+        }
+        const int64_t a0 = b + 4 * lane;
+        float v0 = a0 + 0 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.x) : 0.f;
+        float v1 = a0 + 1 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.y) : 0.f;
+        float v2 = a0 + 2 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.z) : 0.f;
+        float v3 = a0 + 3 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.w) : 0.f;
+        const int wi = lane >> 3;
+        const uint32_t mine = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
+        const uint32_t hf = (mine >> sh) & 0xFu;
+        // heads before this lane in the chunk
+        int prefix = __popc(mine & below);
+        if (wi > 0) prefix += __popc(w0);
+        if (wi > 1) prefix += __popc(w1);
+        if (wi > 2) prefix += __popc(w2);
+        const int total_heads = __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3);
+        const int32_t base_rank = chunk_rank[c];
+        // lane-local pieces: A = arcs before the first head, inner complete
+        // segments, T = arcs from the last head on
+        float vals[4] = {v0, v1, v2, v3};
+        float A = 0.f, run = 0.f;
+        int seen = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if ((hf >> k) & 1u) {
+                if (seen == 0) {
+                    A = run;
+                } else if (run != 0.f) {
+                    // complete segment inside this lane: its head is the (seen-1)-th
+                    atomicAdd(y + nzrow[base_rank + prefix + seen - 1], run);
+                }
+                run = 0.f;
+                ++seen;
+            }
+            run += vals[k];
+        }
+        if (seen == 0) A = run;
+        const bool has_head = seen > 0;
+        const float T = has_head ? run : 0.f;
+        // segmented inclusive scan over lanes: q = T at a headed lane, else
+        // q(previous lane) + A
+        float q = has_head ? T : A;
+        bool f = has_head;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            float qo = __shfl_up_sync(G2_FULL, q, d);
+            bool fo = __shfl_up_sync(G2_FULL, f, d);
+            if (lane >= d && !f) {
+                q += qo;
+                f = fo;
+            }
+        }
+        float qprev = __shfl_up_sync(G2_FULL, q, 1);
+        if (lane == 0) qprev = 0.f;
+        if (has_head) {
+            // the segment that ends just before this lane's first head
+            float tot = qprev + A;
+            int32_t rk = base_rank + prefix - 1;
+            if (tot != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], tot);
+        }
+        if (lane == 31) {
+            // the segment that runs to the end of the chunk (may continue)
+            int32_t rk = base_rank + total_heads - 1;
+            if (q != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], q);
+        }
+    }
+}
+
+}  // namespace g2
