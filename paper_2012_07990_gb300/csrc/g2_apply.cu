@@ -300,9 +300,9 @@ extern "C" g2_status g2_edgeset_apply(g2_graph *g, g2_op op, g2_frontier *in, vo
         produced.size = size;
         if (outf->format == G2_FRONTIER_SPARSE) {
             if (size > outf->cap) {
-                cudaFree(outf->q);
+                dfree(outf->q, st);
                 outf->q = nullptr;
-                G2_CK(cudaMalloc(&outf->q, (size_t)size * 4));
+                G2_CK(dmalloc(&outf->q, (size_t)size * 4, st));
                 outf->cap = size;
             }
             if (produced.rep == OUT_SPARSE) {

@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -116,6 +118,74 @@ __global__ void k_validate_cols(const int32_t *col, const int32_t *w, int32_t n,
             if (!start && col[f] <= v) atomicExch(bad, 5);
         }
         if (w && w[e] < 0) atomicExch(bad, 6);
+    }
+}
+
+// Copy of the caller's column ids (and weights) into the graph's arrays with
+// the checks of k_validate_cols done on the way: the arcs are read once.
+// `src`/`wsrc` are device-readable addresses: device memory, pinned host
+// memory, or pageable host memory on a device that reads it through the host
+// page tables (a coherent CPU-GPU link); the caller checks 16-byte alignment.
+// Four arcs per thread with 16-byte accesses; a warp covers 128 consecutive
+// arcs, and the id after a thread's last arc comes from the next lane.
+__global__ void __launch_bounds__(256) k_load_cols(const int32_t *src, const int32_t *wsrc,
+                                                   int32_t *dst, int32_t *wdst, int32_t n,
+                                                   int32_t m, const uint32_t *rowstart,
+                                                   int32_t *bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nq = ((int64_t)m + 3) / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count (base is a multiple of 32): the shuffle below
+    // always has every lane present
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nq;
+         base += stride) {
+        const int64_t q = base + lane, e0 = q * 4;
+        const bool inq = q < nq, full = e0 + 4 <= m;
+        int32_t c[4] = {0, 0, 0, 0}, wv[4] = {0, 0, 0, 0};
+        if (inq) {
+            if (full) {
+                const int4 v = *reinterpret_cast<const int4 *>(src + e0);
+                c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+                if (wsrc) {
+                    const int4 x = *reinterpret_cast<const int4 *>(wsrc + e0);
+                    wv[0] = x.x; wv[1] = x.y; wv[2] = x.z; wv[3] = x.w;
+                }
+            } else {
+                for (int k = 0; k < 4; ++k)
+                    if (e0 + k < m) {
+                        c[k] = src[e0 + k];
+                        if (wsrc) wv[k] = wsrc[e0 + k];
+                    }
+            }
+        }
+        int32_t nxt = __shfl_down_sync(G2_FULL, c[0], 1);
+        if (lane == 31 && inq && e0 + 4 < m) nxt = src[e0 + 4];
+        if (!inq) continue;
+        int code = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t e = e0 + k;
+            if (e >= m) break;
+            if (c[k] < 0 || c[k] >= n) code = 4;
+            const int64_t f = e + 1;
+            if (f < m) {
+                const bool start = (rowstart[f >> 5] >> (f & 31)) & 1u;
+                const int32_t cn = k < 3 ? c[k + 1] : nxt;
+                if (!start && cn <= c[k]) code = code ? code : 5;
+            }
+            if (wsrc && wv[k] < 0) code = code ? code : 6;
+        }
+        if (full) {
+            *reinterpret_cast<int4 *>(dst + e0) = make_int4(c[0], c[1], c[2], c[3]);
+            if (wsrc) *reinterpret_cast<int4 *>(wdst + e0) = make_int4(wv[0], wv[1], wv[2], wv[3]);
+        } else {
+            for (int k = 0; k < 4; ++k)
+                if (e0 + k < m) {
+                    dst[e0 + k] = c[k];
+                    if (wsrc) wdst[e0 + k] = wv[k];
+                }
+        }
+        if (code) atomicExch(bad, code);
     }
 }
 
@@ -330,15 +400,71 @@ int grid_for(const g2_graph *g, int64_t items, int items_per_cta) {
     return (int)b;
 }
 
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices];
+int g_pool_state[kMaxDevices];  // 0 unknown, 1 pool, 2 no pool support
+
+// pool of the current device, or nullptr where pools are unsupported
+cudaMemPool_t current_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (g_pool_state[dev] == 0) {
+        int ok = 0;
+        cudaDeviceGetAttribute(&ok, cudaDevAttrMemoryPoolsSupported, dev);
+        cudaMemPool_t pool = nullptr;
+        if (ok) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) pool = nullptr;
+        }
+        if (pool) {
+            uint64_t keep = UINT64_MAX;  // never hand freed blocks back to the driver
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            g_pool[dev] = pool;
+            g_pool_state[dev] = 1;
+        } else {
+            cudaGetLastError();
+            g_pool_state[dev] = 2;
+        }
+    }
+    return g_pool_state[dev] == 1 ? g_pool[dev] : nullptr;
+}
+}  // namespace
+
+cudaError_t dmalloc_bytes(void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (bytes < 16) bytes = 16;
+    cudaMemPool_t pool = current_pool();
+    if (!pool) return cudaMalloc(p, bytes);
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+void dfree(void *p, cudaStream_t st) {
+    if (!p) return;
+    if (!current_pool()) {
+        cudaFree(p);
+        return;
+    }
+    cudaFreeAsync(p, st);
+}
+
 g2_status ws_get(g2_graph *g, Buf b, size_t bytes, void **out) {
     if (bytes == 0) bytes = 16;
     if (g->cap[b] < bytes) {
-        if (g->buf[b]) cudaFree(g->buf[b]);
+        // the old block may still be read by work queued on g->st: its
+        // release is ordered after that work
+        if (g->buf[b]) dfree(g->buf[b], g->st);
         g->buf[b] = nullptr;
         g->cap[b] = 0;
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "workspace cudaMalloc");
+        cudaError_t e = dmalloc_bytes(&p, bytes, g->st);
+        if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
         g->buf[b] = p;
         g->cap[b] = bytes;
     }
@@ -364,6 +490,7 @@ g2_status sync_and_check(g2_graph *g, cudaStream_t st, int32_t *d_err) {
 
 g2_status begin_call(g2_graph *g, cudaStream_t st, int32_t **d_err) {
     stats() = g2_stats{};
+    g->st = st;
     int32_t *ctrs;
     G2_TRY(ws(g, B_CTR, 64, &ctrs));
     G2_CK(cudaMemsetAsync(ctrs, 0, 64 * sizeof(int32_t), st));
@@ -411,7 +538,7 @@ g2_status exclusive_scan_i32(g2_graph *g, const int32_t *in, int32_t *out, int32
 g2_status ensure_coo(g2_graph *g, cudaStream_t st) {
     Topology *t = g->topo;
     if (t->coo_src || t->m == 0) return G2_OK;
-    G2_CK(cudaMalloc(&t->coo_src, (size_t)t->m * sizeof(int32_t)));
+    G2_CK(dmalloc(&t->coo_src, (size_t)t->m * sizeof(int32_t), st));
     k_coo_src<<<grid_for(g, (int64_t)t->n * 32, kCta), kCta, 0, st>>>(t->rowptr, t->n, t->coo_src);
     G2_CK(cudaGetLastError());
     return G2_OK;
@@ -434,19 +561,19 @@ g2_status ensure_edge_block(g2_graph *g, int32_t N, cudaStream_t st) {
     if (nseg * (int64_t)n >= 2147483647LL)
         return fail(G2_EUNSUPPORTED, "EdgeBlocking: segments x vertices must stay below 2^31");
     if (t->eb_src) {
-        cudaFree(t->eb_src); cudaFree(t->eb_dst); cudaFree(t->eb_seg);
+        dfree(t->eb_src, st); dfree(t->eb_dst, st); dfree(t->eb_seg, st);
         delete[] t->h_eb_seg;
         t->eb_src = t->eb_dst = nullptr; t->eb_seg = nullptr; t->h_eb_seg = nullptr;
     }
     G2_TRY(ensure_coo(g, st));
     int64_t runs = nseg * n;
     int32_t *cnt = nullptr, *off = nullptr, *beg = nullptr;
-    G2_CK(cudaMalloc(&t->eb_src, (size_t)std::max<int64_t>(m, 1) * 4));
-    G2_CK(cudaMalloc(&t->eb_dst, (size_t)std::max<int64_t>(m, 1) * 4));
-    G2_CK(cudaMalloc(&t->eb_seg, (size_t)(nseg + 1) * 8));
-    G2_CK(cudaMalloc(&cnt, (size_t)(runs + 1) * 4));
-    G2_CK(cudaMalloc(&off, (size_t)(runs + 1) * 4));
-    G2_CK(cudaMalloc(&beg, (size_t)(runs + 1) * 4));
+    G2_CK(dmalloc(&t->eb_src, (size_t)std::max<int64_t>(m, 1) * 4, st));
+    G2_CK(dmalloc(&t->eb_dst, (size_t)std::max<int64_t>(m, 1) * 4, st));
+    G2_CK(dmalloc(&t->eb_seg, (size_t)(nseg + 1) * 8, st));
+    G2_CK(dmalloc(&cnt, (size_t)(runs + 1) * 4, st));
+    G2_CK(dmalloc(&off, (size_t)(runs + 1) * 4, st));
+    G2_CK(dmalloc(&beg, (size_t)(runs + 1) * 4, st));
     if (runs > 0) {
         k_eb_runs<<<grid_for(g, runs, kCta), kCta, 0, st>>>(t->rowptr, t->col, n, N, (int32_t)nseg,
                                                             cnt, beg);
@@ -462,7 +589,7 @@ g2_status ensure_edge_block(g2_graph *g, int32_t N, cudaStream_t st) {
     G2_CK(cudaMemcpyAsync(t->h_eb_seg, t->eb_seg, (size_t)(nseg + 1) * 8, cudaMemcpyDeviceToHost,
                           st));
     G2_CK(cudaStreamSynchronize(st));
-    cudaFree(cnt); cudaFree(off); cudaFree(beg);
+    dfree(cnt, st); dfree(off, st); dfree(beg, st);
     t->eb_N = N;
     t->eb_nseg = (int32_t)nseg;
     return G2_OK;
@@ -537,21 +664,13 @@ g2_status vset_count(g2_graph *g, const VSet &v, int32_t *d_out, cudaStream_t st
 static void topo_release(Topology *t) {
     if (!t) return;
     if (--t->refs > 0) return;
-    cudaFree(t->rowptr);
-    cudaFree(t->col);
-    if (t->w) cudaFree(t->w);
-    if (!t->symmetric) {
-        cudaFree(t->crowptr);
-        cudaFree(t->ccol);
-        if (t->cw) cudaFree(t->cw);
-    }
-    if (t->coo_src) cudaFree(t->coo_src);
-    if (t->eb_src) { cudaFree(t->eb_src); cudaFree(t->eb_dst); cudaFree(t->eb_seg); }
-    if (t->pr_perm) cudaFree(t->pr_perm);
-    if (t->pr_ccol) cudaFree(t->pr_ccol);
-    if (t->seg_head) cudaFree(t->seg_head);
-    if (t->seg_nzrow) cudaFree(t->seg_nzrow);
-    if (t->seg_chunk_rank) cudaFree(t->seg_chunk_rank);
+    // every call on the topology has returned (calls synchronise their
+    // stream before returning), so the blocks are idle: release them to the pool
+    void *blocks[] = {t->rowptr, t->col, t->w, t->symmetric ? nullptr : t->crowptr,
+                      t->symmetric ? nullptr : t->ccol, t->symmetric ? nullptr : t->cw,
+                      t->coo_src, t->eb_src, t->eb_dst, t->eb_seg, t->pr_perm, t->pr_ccol,
+                      t->seg_head, t->seg_nzrow, t->seg_chunk_rank};
+    for (void *b : blocks) dfree(b, nullptr);
     delete[] t->h_eb_seg;
     delete t;
 }
@@ -563,12 +682,30 @@ static g2_graph *new_handle(Topology *t) {
     g->h_ctr = nullptr;
     g->round = 0;
     g->round2 = 0;
+    g->st = nullptr;
     return g;
 }
 
+// Pinned host counter blocks of freed handles are kept for the next handle
+// (pinning and unpinning host memory are slow driver calls).
+static std::mutex g_ctr_mu;
+static std::vector<int32_t *> g_ctr_free;
+
 static g2_status finish_handle(g2_graph *g) {
-    cudaError_t e = cudaMallocHost(&g->h_ctr, 64 * sizeof(int32_t));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost counters");
+    {
+        std::lock_guard<std::mutex> lk(g_ctr_mu);
+        if (!g_ctr_free.empty()) {
+            g->h_ctr = g_ctr_free.back();
+            g_ctr_free.pop_back();
+        }
+    }
+    if (!g->h_ctr) {
+        cudaError_t e = cudaMallocHost(&g->h_ctr, 64 * sizeof(int32_t));
+        if (e != cudaSuccess) {
+            g->h_ctr = nullptr;
+            return cuda_fail(e, "cudaMallocHost counters");
+        }
+    }
     memset(g->h_ctr, 0, 64 * sizeof(int32_t));
     return G2_OK;
 }
@@ -623,6 +760,29 @@ g2_status g2_kernel_time(const char *name, double *ms, int64_t *launches, int32_
     return G2_OK;
 }
 
+// Address at which kernels may read the caller's array p, or nullptr when
+// they cannot (then it is copied with cudaMemcpy): device memory (flag
+// G2_DEVICE_PTRS), pinned host memory, or pageable host memory on a device
+// that reads it through the host's page tables (the coherent link of a
+// Grace-Blackwell system; no page migration).  16-byte alignment required.
+static const int32_t *device_readable(const int32_t *p, bool dev, int device) {
+    if (!p || (reinterpret_cast<uintptr_t>(p) & 15u)) return nullptr;
+    if (dev) return p;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer &&
+        !(reinterpret_cast<uintptr_t>(a.devicePointer) & 15u))
+        return static_cast<const int32_t *>(a.devicePointer);
+    if (a.type != cudaMemoryTypeUnregistered) return nullptr;
+    int pageable = 0, host_tables = 0;
+    cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+    cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device);
+    return pageable && host_tables ? p : nullptr;
+}
+
 g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *col,
                       const int32_t *w, uint32_t flags, void *stream, g2_graph **out) {
     if (!out) return fail(G2_EINVAL, "null output handle");
@@ -661,10 +821,10 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     // rounded bulk copy of a slice ending at the last element stays in bounds
     size_t mb = ((size_t)std::max<int64_t>(m, 1) + kPad) * 4;
     size_t rb = ((size_t)n + 1 + kPad) * 4;
-    if ((e = cudaMalloc(&t->rowptr, rb)) != cudaSuccess)
-        return bail(cuda_fail(e, "cudaMalloc rowptr"));
-    if ((e = cudaMalloc(&t->col, mb)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc col"));
-    if (w && (e = cudaMalloc(&t->w, mb)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc w"));
+    if ((e = dmalloc(&t->rowptr, rb, st)) != cudaSuccess)
+        return bail(cuda_fail(e, "allocation of rowptr"));
+    if ((e = dmalloc(&t->col, mb, st)) != cudaSuccess) return bail(cuda_fail(e, "allocation of col"));
+    if (w && (e = dmalloc(&t->w, mb, st)) != cudaSuccess) return bail(cuda_fail(e, "allocation of w"));
     // zero the padding past the copied elements (the copies below fill the rest)
     const size_t mcopy = (size_t)m * 4, rcopy = ((size_t)n + 1) * 4;
     cudaMemsetAsync(reinterpret_cast<char *>(t->rowptr) + rcopy, 0, rb - rcopy, st);
@@ -672,33 +832,43 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     if (w) cudaMemsetAsync(reinterpret_cast<char *>(t->w) + mcopy, 0, mb - mcopy, st);
     if ((e = cudaMemcpyAsync(t->rowptr, rowptr, ((size_t)n + 1) * 4, kind, st)) != cudaSuccess)
         return bail(cuda_fail(e, "copy rowptr"));
-    if (m > 0 && (e = cudaMemcpyAsync(t->col, col, (size_t)m * 4, kind, st)) != cudaSuccess)
-        return bail(cuda_fail(e, "copy col"));
-    if (w && m > 0 && (e = cudaMemcpyAsync(t->w, w, (size_t)m * 4, kind, st)) != cudaSuccess)
-        return bail(cuda_fail(e, "copy w"));
+    // the arcs are read by the validating copy kernel itself where the device
+    // can address the caller's arrays; otherwise copied, then validated
+    const int32_t *col_rd = m > 0 ? device_readable(col, dev, t->device) : nullptr;
+    const int32_t *w_rd = (w && m > 0) ? device_readable(w, dev, t->device) : nullptr;
+    const bool fused_copy = col_rd && (!w || w_rd);
+    if (!fused_copy) {
+        if (m > 0 && (e = cudaMemcpyAsync(t->col, col, (size_t)m * 4, kind, st)) != cudaSuccess)
+            return bail(cuda_fail(e, "copy col"));
+        if (w && m > 0 && (e = cudaMemcpyAsync(t->w, w, (size_t)m * 4, kind, st)) != cudaSuccess)
+            return bail(cuda_fail(e, "copy w"));
+    }
     // validation on the device
     {
         uint32_t *rowstart = nullptr;
         int32_t *bad = nullptr;
         size_t words = ((size_t)std::max<int64_t>(m, 1) + 31) / 32;
-        if ((e = cudaMalloc(&rowstart, words * 4)) != cudaSuccess)
-            return bail(cuda_fail(e, "cudaMalloc validation"));
-        if ((e = cudaMalloc(&bad, 4)) != cudaSuccess) {
-            cudaFree(rowstart);
-            return bail(cuda_fail(e, "cudaMalloc validation"));
+        if ((e = dmalloc(&rowstart, words * 4, st)) != cudaSuccess)
+            return bail(cuda_fail(e, "allocation for validation"));
+        if ((e = dmalloc(&bad, 4, st)) != cudaSuccess) {
+            dfree(rowstart, st);
+            return bail(cuda_fail(e, "allocation for validation"));
         }
         cudaMemsetAsync(rowstart, 0, words * 4, st);
         cudaMemsetAsync(bad, 0, 4, st);
         k_validate_rows<<<(int)((n + 1 + 255) / 256), 256, 0, st>>>(t->rowptr, n, (int32_t)m,
                                                                    rowstart, bad);
-        if (m > 0)
+        if (m > 0 && fused_copy)
+            k_load_cols<<<t->sm_count * 8, 256, 0, st>>>(col_rd, w_rd, t->col, t->w, n, (int32_t)m,
+                                                         rowstart, bad);
+        else if (m > 0)
             k_validate_cols<<<grid_for(g, m, 256), 256, 0, st>>>(t->col, t->w, n, (int32_t)m,
                                                                  rowstart, bad);
         int32_t hbad = 0;
         cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, st);
         e = cudaStreamSynchronize(st);
-        cudaFree(rowstart);
-        cudaFree(bad);
+        dfree(rowstart, st);
+        dfree(bad, st);
         if (e != cudaSuccess) return bail(cuda_fail(e, "graph validation"));
         if (hbad) {
             static const char *why[] = {"", "rowptr[0] != 0", "rowptr[n] != m",
@@ -716,22 +886,24 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
         // transpose on the host (one-time load step)
         std::vector<int32_t> hrp((size_t)n + 1), hcl((size_t)std::max<int64_t>(m, 1)), hw;
         if (w) hw.resize((size_t)std::max<int64_t>(m, 1));
-        cudaMemcpy(hrp.data(), t->rowptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost);
-        if (m > 0) cudaMemcpy(hcl.data(), t->col, (size_t)m * 4, cudaMemcpyDeviceToHost);
-        if (w && m > 0) cudaMemcpy(hw.data(), t->w, (size_t)m * 4, cudaMemcpyDeviceToHost);
+        cudaMemcpyAsync(hrp.data(), t->rowptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, st);
+        if (m > 0) cudaMemcpyAsync(hcl.data(), t->col, (size_t)m * 4, cudaMemcpyDeviceToHost, st);
+        if (w && m > 0) cudaMemcpyAsync(hw.data(), t->w, (size_t)m * 4, cudaMemcpyDeviceToHost, st);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(e, "CSR download"));
         std::vector<int32_t> crp, ccl, cw;
         host_transpose(n, (int32_t)m, hrp.data(), hcl.data(), w ? hw.data() : nullptr, crp, ccl, cw);
-        if ((e = cudaMalloc(&t->crowptr, rb)) != cudaSuccess ||
-            (e = cudaMalloc(&t->ccol, mb)) != cudaSuccess ||
-            (w && (e = cudaMalloc(&t->cw, mb)) != cudaSuccess))
-            return bail(cuda_fail(e, "cudaMalloc CSC"));
-        cudaMemset(t->crowptr, 0, rb);
-        cudaMemset(t->ccol, 0, mb);
-        if (w) cudaMemset(t->cw, 0, mb);
-        cudaMemcpy(t->crowptr, crp.data(), ((size_t)n + 1) * 4, cudaMemcpyHostToDevice);
-        if (m > 0) cudaMemcpy(t->ccol, ccl.data(), (size_t)m * 4, cudaMemcpyHostToDevice);
-        if (w && m > 0) cudaMemcpy(t->cw, cw.data(), (size_t)m * 4, cudaMemcpyHostToDevice);
-        if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "CSC upload"));
+        if ((e = dmalloc(&t->crowptr, rb, st)) != cudaSuccess ||
+            (e = dmalloc(&t->ccol, mb, st)) != cudaSuccess ||
+            (w && (e = dmalloc(&t->cw, mb, st)) != cudaSuccess))
+            return bail(cuda_fail(e, "allocation of the CSC"));
+        cudaMemsetAsync(t->crowptr, 0, rb, st);
+        cudaMemsetAsync(t->ccol, 0, mb, st);
+        if (w) cudaMemsetAsync(t->cw, 0, mb, st);
+        cudaMemcpyAsync(t->crowptr, crp.data(), ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, st);
+        if (m > 0) cudaMemcpyAsync(t->ccol, ccl.data(), (size_t)m * 4, cudaMemcpyHostToDevice, st);
+        if (w && m > 0) cudaMemcpyAsync(t->cw, cw.data(), (size_t)m * 4, cudaMemcpyHostToDevice, st);
+        // the host vectors must outlive the copies
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(e, "CSC upload"));
     }
     *out = g;
     return G2_OK;
@@ -739,9 +911,12 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
 
 void g2_free_graph(g2_graph *g) {
     if (!g) return;
-    for (int i = 0; i < B_COUNT; ++i)
-        if (g->buf[i]) cudaFree(g->buf[i]);
-    if (g->h_ctr) cudaFreeHost(g->h_ctr);
+    // calls synchronise before returning, so the workspace is idle
+    for (int i = 0; i < B_COUNT; ++i) dfree(g->buf[i], nullptr);
+    if (g->h_ctr) {
+        std::lock_guard<std::mutex> lk(g_ctr_mu);
+        g_ctr_free.push_back(g->h_ctr);
+    }
     topo_release(g->topo);
     delete g;
 }
@@ -772,6 +947,7 @@ g2_status g2_graph_info(const g2_graph *g, int64_t *n, int64_t *m, int32_t *sm_c
 g2_status g2_edge_block(g2_graph *g, int32_t N, int32_t *num_segments, void *stream) {
     if (!g) return fail(G2_EINVAL, "null graph");
     cudaStream_t st = as_stream(stream);
+    g->st = st;
     G2_TRY(ensure_edge_block(g, N, st));
     G2_CK(cudaStreamSynchronize(st));
     if (num_segments) *num_segments = g->topo->eb_nseg;
@@ -784,6 +960,7 @@ g2_status g2_edge_block_export(g2_graph *g, int32_t *src, int32_t *dst, int64_t 
     Topology *t = g->topo;
     if (!t->eb_src) return fail(G2_EINVAL, "no EdgeBlocking layout built (call g2_edge_block)");
     cudaStream_t st = as_stream(stream);
+    g->st = st;
     if (t->m > 0) {
         G2_CK(cudaMemcpyAsync(src, t->eb_src, (size_t)t->m * 4, cudaMemcpyDeviceToDevice, st));
         G2_CK(cudaMemcpyAsync(dst, t->eb_dst, (size_t)t->m * 4, cudaMemcpyDeviceToDevice, st));
@@ -805,18 +982,22 @@ g2_status g2_frontier_create(g2_graph *g, int32_t format, g2_frontier **out) {
     f->format = format;
     f->q = nullptr; f->cnt = nullptr; f->bitmap = nullptr; f->boolmap = nullptr;
     f->cap = 0;
-    cudaError_t e = cudaMalloc(&f->cnt, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemset(f->cnt, 0, sizeof(int32_t));
+    // allocated and cleared on the legacy stream, then synchronised, so that
+    // the frontier is ready for a call on any stream
+    cudaError_t e = dmalloc(&f->cnt, sizeof(int32_t), nullptr);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->cnt, 0, sizeof(int32_t), nullptr);
     if (e == cudaSuccess && format == G2_FRONTIER_SPARSE) {
         f->cap = std::max(n, 1);
-        e = cudaMalloc(&f->q, (size_t)f->cap * 4);
+        e = dmalloc(&f->q, (size_t)f->cap * 4, nullptr);
     } else if (e == cudaSuccess && format == G2_FRONTIER_BITMAP) {
-        e = cudaMalloc(&f->bitmap, ((size_t)(n + 31) / 32 + 1) * 4);
-        if (e == cudaSuccess) e = cudaMemset(f->bitmap, 0, ((size_t)(n + 31) / 32 + 1) * 4);
+        e = dmalloc(&f->bitmap, ((size_t)(n + 31) / 32 + 1) * 4, nullptr);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(f->bitmap, 0, ((size_t)(n + 31) / 32 + 1) * 4, nullptr);
     } else if (e == cudaSuccess) {
-        e = cudaMalloc(&f->boolmap, (size_t)std::max(n, 1));
-        if (e == cudaSuccess) e = cudaMemset(f->boolmap, 0, (size_t)std::max(n, 1));
+        e = dmalloc(&f->boolmap, (size_t)std::max(n, 1), nullptr);
+        if (e == cudaSuccess) e = cudaMemsetAsync(f->boolmap, 0, (size_t)std::max(n, 1), nullptr);
     }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) {
         g2_frontier_free(f);
         return cuda_fail(e, "frontier allocation");
@@ -827,10 +1008,11 @@ g2_status g2_frontier_create(g2_graph *g, int32_t format, g2_frontier **out) {
 
 void g2_frontier_free(g2_frontier *f) {
     if (!f) return;
-    if (f->q) cudaFree(f->q);
-    if (f->cnt) cudaFree(f->cnt);
-    if (f->bitmap) cudaFree(f->bitmap);
-    if (f->boolmap) cudaFree(f->boolmap);
+    // calls synchronise before returning, so the frontier's blocks are idle
+    dfree(f->q, nullptr);
+    dfree(f->cnt, nullptr);
+    dfree(f->bitmap, nullptr);
+    dfree(f->boolmap, nullptr);
     delete f;
 }
 
@@ -841,15 +1023,16 @@ g2_status g2_frontier_set(g2_frontier *f, const int32_t *verts, int32_t k, void 
     for (int32_t i = 0; i < k; ++i)
         if (verts[i] < 0 || verts[i] >= n) return fail(G2_EINVAL, "vertex id out of range");
     cudaStream_t st = as_stream(stream);
+    g->st = st;
     int32_t *tmp;
     G2_TRY(ws(g, B_I1, (size_t)std::max(k, 1), &tmp));
     if (k > 0) G2_CK(cudaMemcpyAsync(tmp, verts, (size_t)k * 4, cudaMemcpyHostToDevice, st));
     VSet src{OUT_SPARSE, tmp, k, nullptr, nullptr, nullptr, k};
     if (f->format == G2_FRONTIER_SPARSE) {
         if (k > f->cap) {
-            cudaFree(f->q);
+            dfree(f->q, st);
             f->q = nullptr;
-            G2_CK(cudaMalloc(&f->q, (size_t)k * 4));
+            G2_CK(dmalloc(&f->q, (size_t)k * 4, st));
             f->cap = k;
         }
         if (k > 0) G2_CK(cudaMemcpyAsync(f->q, tmp, (size_t)k * 4, cudaMemcpyDeviceToDevice, st));
@@ -866,6 +1049,7 @@ g2_status g2_frontier_size(g2_frontier *f, int32_t *size, void *stream) {
     if (!f || !size) return fail(G2_EINVAL, "null argument");
     g2_graph *g = f->g;
     cudaStream_t st = as_stream(stream);
+    g->st = st;
     if (f->format == G2_FRONTIER_SPARSE) {
         G2_CK(cudaMemcpyAsync(g->h_ctr, f->cnt, 4, cudaMemcpyDeviceToHost, st));
     } else {
@@ -885,6 +1069,7 @@ g2_status g2_frontier_list(g2_frontier *f, int32_t *verts, int32_t cap, int32_t 
     if (!f || !verts || !k || cap < 0) return fail(G2_EINVAL, "null argument");
     g2_graph *g = f->g;
     cudaStream_t st = as_stream(stream);
+    g->st = st;
     int32_t size = 0;
     G2_TRY(g2_frontier_size(f, &size, stream));
     if (size > cap) return fail(G2_EOVERFLOW, "frontier larger than the output capacity");
@@ -908,16 +1093,20 @@ g2_status g2_selftest_wait_timeout(int64_t limit_ns, void *stream) {
     cudaStream_t st = as_stream(stream);
     unsigned *flag = nullptr;
     int32_t *err = nullptr;
-    G2_CK(cudaMalloc(&flag, 4));
-    G2_CK(cudaMalloc(&err, 4));
+    G2_CK(dmalloc(&flag, 4, st));
+    cudaError_t ea = dmalloc(&err, 4, st);
+    if (ea != cudaSuccess) {
+        dfree(flag, st);
+        return cuda_fail(ea, "selftest allocation");
+    }
     cudaMemsetAsync(flag, 0, 4, st);
     cudaMemsetAsync(err, 0, 4, st);
     k_wait_flag<<<1, 32, 0, st>>>(flag, (uint64_t)limit_ns, err);
     int32_t h = 0;
     cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(flag);
-    cudaFree(err);
+    dfree(flag, st);
+    dfree(err, st);
     if (e != cudaSuccess) return cuda_fail(e, "selftest");
     if (h == G2_ETIMEOUT) return fail(G2_ETIMEOUT, "bounded wait expired as expected");
     return G2_OK;

@@ -66,6 +66,7 @@ struct g2_graph {
     int32_t *h_ctr;   // pinned host mirror of B_CTR
     int32_t round;    // monotonic-counter stamp (advances every apply round)
     int32_t round2;
+    cudaStream_t st;  // stream of the call in progress (set at every entry)
 };
 
 struct g2_frontier {
@@ -116,8 +117,28 @@ struct Topology {
     }
 };
 
+// ------------------------------------------------------------ device memory
+// Every device allocation of the library comes from one stream-ordered pool
+// per device whose release threshold is unlimited: freed blocks stay with the
+// pool and later allocations reuse them without a driver round trip and
+// without the device-wide synchronisation a cudaFree implies.  A graph that
+// is loaded, queried and freed once per request pays for its memory once per
+// process, not once per request.  (Devices without memory-pool support fall
+// back to cudaMalloc/cudaFree.)
+//  dmalloc: the block is ordered on `st` (null = legacy stream); other
+//           streams may use it once the host has synchronised with `st`.
+//  dfree:   the release is ordered after the work already queued on `st`;
+//           the block must not be in use by work on any other stream.
+cudaError_t dmalloc_bytes(void **p, size_t bytes, cudaStream_t st);
+void dfree(void *p, cudaStream_t st);
+template <class T>
+inline cudaError_t dmalloc(T **p, size_t bytes, cudaStream_t st) {
+    return dmalloc_bytes(reinterpret_cast<void **>(p), bytes, st);
+}
+
 // Device buffer of at least `bytes` bytes for slot b (grown if needed; old
-// contents are NOT kept when it grows).
+// contents are NOT kept when it grows).  Allocation and release are ordered
+// on g->st, the stream of the call in progress on this handle.
 g2_status ws_get(g2_graph *g, Buf b, size_t bytes, void **out);
 template <class T>
 inline g2_status ws(g2_graph *g, Buf b, size_t count, T **out) {

@@ -685,12 +685,12 @@ static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, con
         return G2_OK;
     }
     const int32_t n = t->n, m = t->m;
-    if (t->pr_perm) cudaFree(t->pr_perm);
-    if (t->pr_ccol) cudaFree(t->pr_ccol);
+    dfree(t->pr_perm, st);
+    dfree(t->pr_ccol, st);
     t->pr_perm = t->pr_ccol = nullptr;
     t->pr_hot = -1;
-    G2_CK(cudaMalloc(&t->pr_perm, ((size_t)std::max(n, 1) + 1) * 4));
-    G2_CK(cudaMalloc(&t->pr_ccol, ((size_t)std::max(m, 1) + kPad) * 4));
+    G2_CK(dmalloc(&t->pr_perm, ((size_t)std::max(n, 1) + 1) * 4, st));
+    G2_CK(dmalloc(&t->pr_ccol, ((size_t)std::max(m, 1) + kPad) * 4, st));
     G2_TRY(select_hot(g, hot, t->pr_perm, st));
     // only the padding past the last arc needs zeroing; the arcs are all written
     G2_CK(cudaMemsetAsync(t->pr_ccol + m, 0, ((size_t)std::max(m, 1) - m + kPad) * 4, st));
@@ -714,16 +714,16 @@ static g2_status ensure_seg_layout(g2_graph *g, cudaStream_t st) {
     G2_TRY(ws(g, B_I0, (size_t)n + 1, &nz));
     G2_TRY(ws(g, B_I1, (size_t)n + 1, &pos));
     G2_TRY(ws(g, B_TWC_S, (size_t)nchunks + 1, &ccount));
-    G2_CK(cudaMalloc(&t->seg_head, words * 4));
+    G2_CK(dmalloc(&t->seg_head, words * 4, st));
     G2_CK(cudaMemsetAsync(t->seg_head, 0, words * 4, st));
     k_seg_heads<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->crowptr, n, t->seg_head, nz);
     G2_TRY(exclusive_scan_i32(g, nz, pos, n, st));
     int32_t nnz = 0;
     G2_CK(cudaMemcpyAsync(&nnz, pos + n, 4, cudaMemcpyDeviceToHost, st));
     G2_CK(cudaStreamSynchronize(st));
-    G2_CK(cudaMalloc(&t->seg_nzrow, ((size_t)nnz + 1) * 4));
+    G2_CK(dmalloc(&t->seg_nzrow, ((size_t)nnz + 1) * 4, st));
     k_seg_nzrow<<<grid_for(g, n, kCta), kCta, 0, st>>>(nz, pos, n, t->seg_nzrow);
-    G2_CK(cudaMalloc(&t->seg_chunk_rank, ((size_t)nchunks + 1) * 4));
+    G2_CK(dmalloc(&t->seg_chunk_rank, ((size_t)nchunks + 1) * 4, st));
     if (nchunks > 0) {
         k_seg_chunk_heads<<<grid_for(g, nchunks, kCta), kCta, 0, st>>>(t->seg_head, nchunks, ccount);
         G2_TRY(exclusive_scan_i32(g, ccount, t->seg_chunk_rank, (int32_t)nchunks, st));

@@ -509,3 +509,73 @@ def test_views_and_device_pointer_load(g2, rmat14):
         assert np.array_equal(host(d), od) and np.array_equal(host(p), op)
     info = dg.info()
     assert info["n"] == g.n and info["m"] == g.m and info["sm_count"] > 0
+
+
+def test_load_paths_and_memory_reuse(g2, rmat14):
+    """Every way of handing the CSR to g2_load_csr gives the same graph: pinned
+    host arrays and pageable ones (read by the validating copy kernel where the
+    device can address them), a misaligned host view (plain copy, then
+    validation), device arrays; invalid input is rejected on each path; and
+    graphs loaded and freed many times over reuse pooled memory correctly."""
+    g = rmat14
+    w = gg.pair_weights(g, 255, seed=3)
+    od, op = oracle.bfs_graph(g, 5)
+    osd = oracle.sssp_graph(g, w, 5)
+
+    def check(dg):
+        d, p, s = dev(g.n), dev(g.n), dev(g.n)
+        g2.g2_bfs(dg, 5, d, p, None)
+        g2.g2_sssp_delta(dg, 5, 64, s, None)
+        assert np.array_equal(host(d), od) and np.array_equal(host(p), op)
+        assert np.array_equal(host(s), osd)
+        dg.free()
+
+    # pageable numpy arrays
+    check(g2.load_graph(g, w))
+    # pinned host memory
+    prp = torch.from_numpy(g.rowptr).pin_memory()
+    pcl = torch.from_numpy(g.col).pin_memory()
+    pw = torch.from_numpy(w).pin_memory()
+    as_np = lambda t: np.frombuffer(t.numpy().data, dtype=np.int32)
+    check(g2.g2_load_csr(g.n, as_np(prp), as_np(pcl), as_np(pw), True))
+    # 4-byte misaligned host views of the same data
+    buf = np.empty(g.m + 1, np.int32)
+    col_mis = buf[1:]
+    col_mis[:] = g.col
+    wbuf = np.empty(g.m + 1, np.int32)
+    w_mis = wbuf[1:]
+    w_mis[:] = w
+    assert col_mis.ctypes.data % 16 != 0
+    check(g2.g2_load_csr(g.n, g.rowptr, col_mis, w_mis, True))
+    # device arrays
+    check(g2.g2_load_csr(g.n, torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.col).cuda(),
+                         torch.from_numpy(w).cuda(), True))
+    # invalid input on the pinned and misaligned paths
+    bad = g.col.copy()
+    bad[g.m // 2 + 3] = g.n  # id out of range
+    for c in (as_np(torch.from_numpy(bad).pin_memory()), np.concatenate([np.zeros(1, np.int32), bad])[1:]):
+        with pytest.raises(g2.G2Error) as e:
+            g2.g2_load_csr(g.n, g.rowptr, c, None, True)
+        assert e.value.status == g2.G2_EINVAL
+    wneg = w.copy()
+    wneg[g.m - 1] = -1  # negative weight in the ragged tail
+    with pytest.raises(g2.G2Error) as e:
+        g2.g2_load_csr(g.n, g.rowptr, g.col, wneg, True)
+    assert e.value.status == g2.G2_EINVAL
+    # swapped neighbours inside one adjacency list (the swap crosses a 4-arc quad)
+    uns = g.col.copy()
+    v = next(u for u in range(g.n) if g.rowptr[u + 1] - g.rowptr[u] >= 8 and g.rowptr[u] % 4 == 1)
+    b = int(g.rowptr[v]) + 2
+    uns[b], uns[b + 1] = uns[b + 1], uns[b]
+    with pytest.raises(g2.G2Error) as e:
+        g2.g2_load_csr(g.n, g.rowptr, uns, None, True)
+    assert e.value.status == g2.G2_EINVAL
+    # load / run / free repeatedly: pooled blocks are handed out again
+    for _ in range(12):
+        dg = g2.load_graph(g)
+        d = dev(g.n)
+        g2.g2_bfs(dg, 5, d, None, None)
+        assert np.array_equal(host(d), od)
+        r = torch.empty(g.n, dtype=torch.float32, device="cuda")
+        g2.g2_pagerank(dg, 0.85, 3, r)
+        dg.free()
