@@ -2,7 +2,7 @@
  * g2.h — C ABI of libg2.so: frontier-driven edge traversal on one GB300 GPU.
  *
  * The operator at the centre is edgeset.apply / applyModified of the paper's
- * algorithm language (Sec. IV, Fig. 1): for every arc u->v whose source u is
+ * algorithm language (Sec. IV, Fig. 2): for every arc u->v whose source u is
  * in the input vertexset (".from(frontier)") and whose destination passes the
  * destination filter (".to(filter)"), apply an update function to v; with
  * applyModified, return the vertexset of destinations whose tracked value
@@ -208,7 +208,7 @@ g2_status g2_edgeset_apply(g2_graph *g, g2_op op, g2_frontier *in, void *vdata, 
 /* Schedules: a non-NULL `sched` runs exactly that schedule (a simple one, or a
  * hybrid choosing s1/s2 each round by the input vertexset size).  NULL selects
  * the library's tuned schedule for the algorithm, stated with each call. */
-/* BFS (Fig. 1): depth int32[n] device (-1 unreachable), parent int32[n]
+/* BFS (Fig. 2): depth int32[n] device (-1 unreachable), parent int32[n]
  * device or NULL (parent[src] = src, else the smallest-id in-neighbour one
  * level up, -1 unreachable).  Loop until the frontier is empty.  With kernel
  * fusion the whole loop is one persistent cooperative kernel.  NULL schedule:

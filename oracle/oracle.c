@@ -12,7 +12,7 @@
  * col[rowptr[u] .. rowptr[u+1]-1].
  *
  * Functions and what they follow:
- *   oracle_bfs        BFS of the paper's Fig. 1 program (Sec. IV): hop depth,
+ *   oracle_bfs        BFS of the paper's Fig. 2 program (Sec. IV): hop depth,
  *                     and the parent array with the canonical reading
  *                     "minimum-id in-neighbour one level up" (the paper's
  *                     parent is any winner of the compare-and-swap race).

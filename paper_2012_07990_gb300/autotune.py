@@ -1,4 +1,4 @@
-"""Schedule autotuner (the role OpenTuner plays in Sec. VI-E of the paper).
+"""Schedule autotuner (the role OpenTuner plays in Sec. VI-F of the paper).
 
 The space is the scheduling language's (Table II fields and the Table III
 hybrid threshold) plus the integer parameters the paper names: the delta of

@@ -1,7 +1,7 @@
 // g2_algos.cu — BFS, connected components, delta-stepping SSSP and
 // betweenness centrality (Sec. VII) as host loops over edgeset.apply rounds
 // (the default, unfused schedules: the host reads the frontier size every
-// round, Fig. 3 left / right).  The fused variants live in g2_fused.cu.
+// round, Fig. 5 left / right).  The fused variants live in g2_fused.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,4 +1,4 @@
-// g2_fused.cu — kernel fusion (Sec. III and VI-C, Fig. 3 middle): the whole
+// g2_fused.cu — kernel fusion (Sec. III and VI-C, Fig. 5 middle): the whole
 // while loop of BFS or delta-stepping SSSP runs inside one persistent
 // cooperative kernel.  Loop state lives in device memory, every resident CTA
 // does the work of many virtual CTAs through the load-balancing library's

@@ -6,7 +6,7 @@ arcs), integer edge weights, and source-vertex choices.  It holds none of the
 traversal arithmetic.  Its C part (``graphgen.c``) is compiled on first use
 with gcc into ``libg2gen.so`` next to this file.
 
-Workload recipes (synthetic stand-ins for the paper's Table III graphs, which
+Workload recipes (synthetic stand-ins for the paper's Table IV graphs, which
 are real-world datasets not shipped here):
 
 * ``rmat(scale, ef=16, a=.57, b=.19, c=.19, seed=1)`` -- power-law, symmetrised.

@@ -355,7 +355,7 @@ def test_apply_pr_add_covers_each_arc_once(g2, rmat14):
 
 
 def test_apply_bfs_round_and_frontier_formats(g2, rmat14):
-    """One applyModified round of the Fig. 1 program from a frontier: the
+    """One applyModified round of the Fig. 2 program from a frontier: the
     output vertexset is exactly the unvisited out-neighbours."""
     g = rmat14
     rng = np.random.default_rng(1)
