@@ -214,6 +214,7 @@ def run_ours(args):
     g2.g2_set_kernel_timing(False)
     clk = clocks.stop()
     total_ms = e0.elapsed_time(e1)
+    pv_ms_total, pv_launches = g2.g2_kernel_time("pr_vertex", reset=False)
     pr_ms_total, pr_launches = g2.g2_kernel_time("pr_round", reset=True)
     if ws > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -234,7 +235,8 @@ def run_ours(args):
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_launch_ms * 1e3, 2),
-                "launches": pr_launches, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+                "launches": pr_launches, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "vertex_pass_us": round(pv_ms_total / max(pv_launches, 1) * 1e3, 2)}
 
     e2e = run_e2e(args, g2, G, src, sb, sc, edges_per_step) if not args.no_e2e else None
     cpu = None

@@ -307,7 +307,8 @@ void g2_set_count_arcs(int32_t enable);
 
 /* Kernel timing (diagnostic, off by default): when enabled, CUDA events are
  * recorded on the call's stream around every launch of the named hot kernels
- * ("pr_round" PageRank arc sweep, "bfs_push", "bfs_pull", "cc_hook", "sssp_relax")
+ * ("pr_round" PageRank arc sweep, "pr_vertex" its vertex pass, "bfs_push",
+ * "bfs_pull", "cc_hook", "sssp_relax")
  * and their durations accumulated per name on the calling thread.
  * g2_kernel_time returns the total milliseconds and launch count for `name`
  * since the last reset; reset != 0 clears every name afterwards. */

@@ -668,7 +668,7 @@ static void topo_release(Topology *t) {
     // stream before returning), so the blocks are idle: release them to the pool
     void *blocks[] = {t->rowptr, t->col, t->w, t->symmetric ? nullptr : t->crowptr,
                       t->symmetric ? nullptr : t->ccol, t->symmetric ? nullptr : t->cw,
-                      t->coo_src, t->eb_src, t->eb_dst, t->eb_seg, t->pr_perm, t->pr_ccol,
+                      t->coo_src, t->eb_src, t->eb_dst, t->eb_seg, t->pr_slot_of, t->pr_ccol,
                       t->seg_head, t->seg_nzrow, t->seg_chunk_rank};
     for (void *b : blocks) dfree(b, nullptr);
     delete[] t->h_eb_seg;
@@ -802,7 +802,7 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     t->rowptr = t->col = t->w = t->crowptr = t->ccol = t->cw = t->coo_src = nullptr;
     t->eb_N = 0; t->eb_nseg = 0; t->eb_src = t->eb_dst = nullptr; t->eb_seg = nullptr;
     t->h_eb_seg = nullptr;
-    t->pr_hot = -1; t->pr_perm = t->pr_ccol = nullptr;
+    t->pr_hot = -1; t->pr_hot_min_deg = 0; t->pr_slot_of = t->pr_ccol = nullptr;
     t->seg_head = nullptr; t->seg_nzrow = t->seg_chunk_rank = nullptr; t->seg_nnzrow = 0;
     g2_graph *g = new_handle(t);
     auto bail = [&](g2_status s) { g2_free_graph(g); return s; };

@@ -99,9 +99,11 @@ struct Topology {
     int32_t *eb_src, *eb_dst;
     int64_t *eb_seg;     // device [nseg+1]
     int64_t *h_eb_seg;   // host copy
-    // PageRank share-cache layout: vertex -> slot, CSC column ids as slots
+    // PageRank share-cache layout: the share slot of every vertex, the least
+    // out-degree of the cached vertices, the CSC column ids as share slots
     int32_t pr_hot;
-    int32_t *pr_perm, *pr_ccol;
+    int32_t pr_hot_min_deg;
+    int32_t *pr_slot_of, *pr_ccol;
     // segmented-sweep layout: row-head flags per arc, rows with in-arcs in
     // order, head count before every 128-arc chunk
     uint32_t *seg_head;

@@ -37,9 +37,10 @@ struct PrArgs {
     int32_t m;
     int32_t tile;            // merged items per tile
     const int32_t *crowptr;
-    const int32_t *ccol;     // column ids (renumbered when perm != null)
+    const int32_t *ccol;     // column ids as share slots (renumbered with a hot layout)
     const int32_t *rowptr;   // CSR offsets for out-degrees (null: symmetric, use CSC)
-    const int32_t *perm;     // vertex id -> share slot (null: identity)
+    const int32_t *slot_of;  // share slot of every vertex (hot > 0)
+    int32_t hot_min_deg;     // every cached vertex has at least this out-degree
     const int32_t *tile_r;   // merge-path row coordinate of every tile boundary
     int32_t ntiles;
     int32_t hot;             // shares [0, hot) are cached in shared memory
@@ -102,17 +103,35 @@ __global__ void k_pr_split_rows(const int32_t *crowptr, int32_t n, int32_t tile,
     }
 }
 
+// Share layout.  With H cached (hot) vertices, share slot H + v holds vertex
+// v's share x[v]/outdeg(v) for every v, and slots 0..H-1 repeat the shares of
+// the cached vertices, which the sweep keeps in shared memory; a CSC column id
+// is renumbered to the cached slot or H + u (slot_of[u]).  Shares are written
+// in vertex order; a vertex whose out-degree reaches min_deg (every cached
+// vertex does) reads slot_of[v] and, if below H, writes that slot too.
+// Without a hot layout H = 0 and slot v is vertex v.
+struct ShareMap {
+    int32_t hot;
+    int32_t min_deg;
+    const int32_t *slot_of;
+};
+
+__device__ __forceinline__ void store_cached_share(float *contrib, const ShareMap &sm, int32_t v,
+                                                   int32_t od, float share) {
+    if (sm.hot == 0 || od < sm.min_deg) return;
+    const int32_t slot = __ldg(sm.slot_of + v);
+    if (slot < sm.hot) contrib[slot] = share;
+}
+
 __device__ __forceinline__ void pr_finalize(const PrArgs &a, int32_t r, float y, int32_t in_beg,
                                             int32_t in_end, float dterm, double &dsum) {
     float xr = a.base + a.damp * (y + dterm);
     int32_t od = a.rowptr ? a.rowptr[r + 1] - a.rowptr[r] : in_end - in_beg;
-    int32_t slot = a.perm ? a.perm[r] : r;
-    if (od > 0) {
-        a.contrib_next[slot] = xr / (float)od;
-    } else {
-        a.contrib_next[slot] = 0.f;
-        dsum += xr;
-    }
+    float share = 0.f;
+    if (od > 0) share = xr / (float)od;
+    else dsum += xr;
+    a.contrib_next[a.hot + r] = share;
+    store_cached_share(a.contrib_next, ShareMap{a.hot, a.hot_min_deg, a.slot_of}, r, od, share);
     if (a.write_x) a.x[r] = xr;
 }
 
@@ -330,20 +349,14 @@ __global__ void __launch_bounds__(kCta) k_pr_fixup(PrArgs a, const int32_t *rows
     block_add_double(dsum, a.dnext);
 }
 
-// The dangling mass D is accumulated in kDSlots slots (one per 128-byte line)
-// instead of one word, so the per-CTA atomics of a pass spread over many L2
-// lines instead of serialising on one address; readers add the slots up.
-constexpr int kDSlots = 64;
-constexpr int kDStride = 16;  // doubles between slots
 
-// Out-degrees of the four vertices v0..v0+3 and their share slots (slot =
-// perm[v], or v without a hot layout); 16-byte loads for a full quad.
+// Out-degrees of the four vertices v0..v0+3; 16-byte loads for a full quad.
 struct PrQuad {
-    int32_t od[4], sl[4];
+    int32_t od[4];
 };
 
-__device__ __forceinline__ void pr_load_quad(const int32_t *rowptr, const int32_t *perm, int32_t n,
-                                             int64_t v0, PrQuad &q) {
+__device__ __forceinline__ void pr_load_quad(const int32_t *rowptr, int32_t n, int64_t v0,
+                                             PrQuad &q) {
     if (v0 + 4 <= n) {
         int4 r4 = __ldg(reinterpret_cast<const int4 *>(rowptr + v0));
         int32_t r5 = __ldg(rowptr + v0 + 4);
@@ -351,43 +364,82 @@ __device__ __forceinline__ void pr_load_quad(const int32_t *rowptr, const int32_
         q.od[1] = r4.z - r4.y;
         q.od[2] = r4.w - r4.z;
         q.od[3] = r5 - r4.w;
-        if (perm) {
-            int4 p4 = __ldg(reinterpret_cast<const int4 *>(perm + v0));
-            q.sl[0] = p4.x; q.sl[1] = p4.y; q.sl[2] = p4.z; q.sl[3] = p4.w;
-        } else {
-            for (int k = 0; k < 4; ++k) q.sl[k] = (int32_t)(v0 + k);
-        }
     } else {
-        for (int k = 0; k < 4; ++k) {
-            const bool in = v0 + k < n;
-            q.od[k] = in ? rowptr[v0 + k + 1] - rowptr[v0 + k] : 0;
-            q.sl[k] = in ? (perm ? perm[v0 + k] : (int32_t)(v0 + k)) : 0;
-        }
+        for (int k = 0; k < 4; ++k)
+            q.od[k] = v0 + k < n ? rowptr[v0 + k + 1] - rowptr[v0 + k] : 0;
     }
 }
 
-// x0 = 1/n: contrib0[slot(u)] = (1/n)/outdeg(u); D0 = (#vertices without
-// out-arcs)/n, added into slot (block & dmask) of d0 (dmask 0: one word).
-// Grid-stride over quads of four consecutive vertices.
-__global__ void __launch_bounds__(kCta) k_pr_init(const int32_t *rowptr, int32_t n,
-                                                    const int32_t *perm, float *contrib, double *d0,
-                                                    int dmask, float *x, double inv_n) {
-    double dsum = 0.0;
+// Shares of a quad into slots H + v0 .. H + v0 + 3 (one 16-byte store for a
+// full quad: H and v0 are multiples of 4), and the cached slots.
+__device__ __forceinline__ void store_quad_shares(float *contrib, const ShareMap &sm, int32_t n,
+                                                  int64_t v0, const PrQuad &q, const float sh[4]) {
+    if (v0 + 4 <= n)
+        *reinterpret_cast<float4 *>(contrib + sm.hot + v0) = make_float4(sh[0], sh[1], sh[2], sh[3]);
+    else
+        for (int k = 0; k < 4; ++k)
+            if (v0 + k < n) contrib[sm.hot + v0 + k] = sh[k];
+    for (int k = 0; k < 4; ++k)
+        if (v0 + k < n) store_cached_share(contrib, sm, (int32_t)(v0 + k), q.od[k], sh[k]);
+}
+
+// Offsets rowptr[v0 .. v0+4] of a quad of four consecutive vertices, one
+// quad per thread: a 16-byte load, the fifth offset from the next lane (the
+// last lane of a warp and the last full quad load it).  Every lane of the
+// warp must call it.
+__device__ __forceinline__ bool pr_quad_offsets(const int32_t *rowptr, int32_t n, int64_t v0,
+                                                int32_t r[5]) {
+    const bool full = v0 + 4 <= n;
+    for (int k = 0; k < 5; ++k) r[k] = 0;
+    if (full) {
+        const int4 r4 = *reinterpret_cast<const int4 *>(rowptr + v0);
+        r[0] = r4.x; r[1] = r4.y; r[2] = r4.z; r[3] = r4.w;
+    } else if (v0 < n) {
+        for (int k = 0; k < 4; ++k)
+            if (v0 + k <= n) r[k] = rowptr[v0 + k];
+    }
+    const int32_t r_next = __shfl_down_sync(G2_FULL, r[0], 1);
+    if (full) r[4] = ((threadIdx.x & 31) == 31 || v0 + 4 == n) ? rowptr[v0 + 4] : r_next;
+    return full;
+}
+
+// x0 = 1/n: shares (1/n)/outdeg(u) (fp32); D0 = (#vertices without out-arcs)/n
+// into the D slots.  One quad of four consecutive vertices per thread.
+__global__ void __launch_bounds__(kCta) k_pr_init(const int32_t *rowptr, int32_t n, ShareMap sm,
+                                                  float *contrib, double *dslots, float *x,
+                                                  double inv_n) {
+    const int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    int32_t r[5];
+    const bool full = pr_quad_offsets(rowptr, n, v0, r);
     const float x0 = (float)inv_n;
-    for (int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; v0 < n;
-         v0 += (int64_t)gridDim.x * blockDim.x * 4) {
+    float dangling = 0.f;
+    if (v0 < n) {
         PrQuad q;
-        pr_load_quad(rowptr, perm, n, v0, q);
+        float sh[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (v0 + k >= n) break;
-            contrib[q.sl[k]] = q.od[k] > 0 ? (float)(inv_n / q.od[k]) : 0.f;
-            if (q.od[k] == 0) dsum += inv_n;
-            if (x) x[v0 + k] = x0;
+            q.od[k] = v0 + k < n ? r[k + 1] - r[k] : 0;
+            sh[k] = q.od[k] > 0 ? x0 / (float)q.od[k] : 0.f;
+            if (v0 + k < n && q.od[k] == 0) dangling += 1.f;
+        }
+        store_quad_shares(contrib, sm, n, v0, q, sh);
+        if (x) {
+            if (full && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0))
+                *reinterpret_cast<float4 *>(x + v0) = make_float4(x0, x0, x0, x0);
+            else
+                for (int k = 0; k < 4 && v0 + k < n; ++k) x[v0 + k] = x0;
         }
     }
-    block_add_double(dsum, d0 + (blockIdx.x & dmask) * kDStride);
+    // at most 128 per warp: exact in fp32; scaled by 1/n in fp64
+    for (int o = 16; o > 0; o >>= 1) dangling += __shfl_xor_sync(G2_FULL, dangling, o);
+    if ((threadIdx.x & 31) == 0 && dangling != 0.f) {
+        const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        atomicAdd(dslots + (gw % kDSlots) * kDStride, (double)dangling * inv_n);
+    }
 }
+
+// Folds the D slots into *fin (one warp).
+__global__ void k_pr_fold(double *dslots, double *fin) { fold_dslots(dslots, fin); }
 
 // generic schedules: x from the accumulated sums, next shares, next D
 __global__ void __launch_bounds__(kCta) k_pr_vertex(const int32_t *rowptr, int32_t n,
@@ -438,69 +490,73 @@ __global__ void k_seg_chunk_heads(const uint32_t *head, int64_t nchunks, int32_t
                  __popc(head[4 * c + 3]);
 }
 
-// D/n for this round, added up from the kDSlots slots by every warp on its
-// own (no block barrier, so a warp's vertex loads are not held back by it).
-// Every lane of the warp must call it.
-__device__ __forceinline__ float pr_dterm(const double *d, double inv_n) {
-    const int lane = threadIdx.x & 31;
-    double v = d[lane * kDStride] + d[(lane + 32) * kDStride];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(G2_FULL, v, o);
-    return (float)(v * inv_n);
-}
-
 // vertex pass after a segmented sweep: x, next shares, next D; y back to zero.
 // Four consecutive vertices per thread with 16-byte loads, every vertex in
 // its own thread group, so the pass has the memory parallelism to stream; a
-// thread issues its loads before it reads D, and no block barrier comes
-// before the stores.
-__global__ void __launch_bounds__(kCta) k_pr_seg_vertex(const int32_t *rowptr, int32_t n,
-                                                        const int32_t *perm, float *y,
-                                                        float *contrib_next, float *x, int write_x,
-                                                        const double *dprev, double *dnext,
-                                                        float base, float damp, double inv_n) {
-    double dsum = 0.0;
+// thread issues its loads before it reads D (one word, folded by the sweep
+// that ran in between), and the pass has no block barrier.
+template <bool WRITE_X, int MIN_BLOCKS>
+__global__ void __launch_bounds__(kCta, MIN_BLOCKS) k_pr_seg_vertex(const int32_t *rowptr, int32_t n,
+                                                           ShareMap sm, float *y,
+                                                           float *contrib_next, float *x,
+                                                           const double *dprev, double *dslots,
+                                                           float base, float damp, double inv_n) {
+    const int lane = threadIdx.x & 31;
     const int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const bool full = v0 + 4 <= n;
+    int32_t r[5] = {0, 0, 0, 0, 0};
     float yv[4] = {0.f, 0.f, 0.f, 0.f};
-    PrQuad q;
-    if (v0 < n) {
-        pr_load_quad(rowptr, perm, n, v0, q);
-        if (v0 + 4 <= n) {
-            float4 y4 = *reinterpret_cast<const float4 *>(y + v0);
-            yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
-        } else {
-            for (int k = 0; k < 4; ++k)
-                if (v0 + k < n) yv[k] = y[v0 + k];
+    if (full) {
+        const int4 r4 = *reinterpret_cast<const int4 *>(rowptr + v0);
+        const float4 y4 = *reinterpret_cast<const float4 *>(y + v0);
+        r[0] = r4.x; r[1] = r4.y; r[2] = r4.z; r[3] = r4.w;
+        yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
+    } else if (v0 < n) {
+        for (int k = 0; k < 4; ++k) {
+            if (v0 + k <= n) r[k] = rowptr[v0 + k];
+            if (v0 + k < n) yv[k] = y[v0 + k];
         }
     }
-    const float dterm = pr_dterm(dprev, inv_n);
+    // rowptr[v0 + 4] is the next lane's first offset; the last lane of a warp
+    // and the last full quad load it
+    const int32_t r_next = __shfl_down_sync(G2_FULL, r[0], 1);
+    if (full) r[4] = (lane == 31 || v0 + 4 == n) ? rowptr[v0 + 4] : r_next;
+    const float dterm = (float)(*dprev * inv_n);
+    float dsum = 0.f;
     if (v0 < n) {
-        float xs[4];
+        PrQuad q;
+        float xs[4], sh[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (v0 + k >= n) break;
-            float xr = base + damp * (yv[k] + dterm);
-            if (q.od[k] > 0) contrib_next[q.sl[k]] = xr / (float)q.od[k];
-            else {
-                contrib_next[q.sl[k]] = 0.f;
-                dsum += xr;
-            }
-            xs[k] = xr;
+            q.od[k] = v0 + k < n ? r[k + 1] - r[k] : 0;
+            xs[k] = base + damp * (yv[k] + dterm);
+            sh[k] = 0.f;
+            if (v0 + k >= n) continue;
+            if (q.od[k] > 0) sh[k] = xs[k] / (float)q.od[k];
+            else dsum += xs[k];
         }
-        if (v0 + 4 <= n) {
+        store_quad_shares(contrib_next, sm, n, v0, q, sh);
+        if (full) {
             *reinterpret_cast<float4 *>(y + v0) = make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
             for (int k = 0; k < 4; ++k)
                 if (v0 + k < n) y[v0 + k] = 0.f;
         }
-        if (write_x) {
+        if (WRITE_X) {
             // x is the caller's array: vector stores only when 16-byte aligned
-            if (v0 + 4 <= n && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0))
+            if (full && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0))
                 *reinterpret_cast<float4 *>(x + v0) = make_float4(xs[0], xs[1], xs[2], xs[3]);
             else
                 for (int k = 0; k < 4 && v0 + k < n; ++k) x[v0 + k] = xs[k];
         }
     }
-    block_add_double(dsum, dnext + (blockIdx.x % kDSlots) * kDStride);
+    // D partial of the warp (a sum of at most 128 ranks, in fp32) into one of
+    // the fp64 slots, no block barrier; the next sweep folds the slots
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(G2_FULL, dsum, o);
+    if (lane == 0 && dsum != 0.f) {
+        const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        atomicAdd(dslots + (gw % kDSlots) * kDStride, (double)dsum);
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -510,6 +566,7 @@ struct PrCfg {
     int hot;        // cached shares (0 = none)
     int per_sm;     // merge kernel: resident CTAs per SM (0 = as many as fit)
     int cta;        // segmented sweep: 512 or 1024 threads per CTA
+    int vtx_full;   // vertex pass: 8 resident CTAs per SM (32 registers) or 6
 };
 
 // Defaults (measured on GB300 with RMAT-22): segmented sweep, 1024-thread
@@ -517,12 +574,13 @@ struct PrCfg {
 // (64 KB per CTA, two CTAs per SM).  The environment overrides them for
 // tuning sweeps.
 static PrCfg pr_config(const g2_graph *g) {
-    PrCfg c{0, 8, 16384, 0, 1024};
+    PrCfg c{0, 8, 16384, 0, 1024, 1};
     if (const char *e = getenv("G2_PR_KERNEL")) c.merge = strcmp(e, "merge") == 0;
     if (const char *e = getenv("G2_PR_IPT")) c.ipt = atoi(e) == 16 ? 16 : 8;
     if (const char *e = getenv("G2_PR_HOT")) c.hot = std::max(0, atoi(e));
     if (const char *e = getenv("G2_PR_CTAS_PER_SM")) c.per_sm = std::max(0, atoi(e));
     if (const char *e = getenv("G2_PR_SEG_CTA")) c.cta = atoi(e) == 512 ? 512 : 1024;
+    if (const char *e = getenv("G2_PR_VTX_BLOCKS")) c.vtx_full = atoi(e) != 6;
     c.hot = std::min<int64_t>(c.hot, g->topo->n);
     c.hot &= ~3;  // keeps the stage buffers 16-byte aligned
     return c;
@@ -612,18 +670,20 @@ __global__ void k_hot_flags(const int32_t *rowptr, int32_t n, int64_t tlo, int64
     }
 }
 
-// slot of v: its rank among the hot vertices, or hot + its rank among the rest
+// slot of v: its rank among the hot vertices, or hot + v
 __global__ void k_hot_perm(const int32_t *hotf, int32_t n, int32_t hot, int32_t *perm) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = perm[v];  // hot vertices before v
-        perm[v] = hotf[v] ? r : hot + (int32_t)v - r;
+        perm[v] = hotf[v] ? r : hot + (int32_t)v;
     }
 }
 
-// Slot map perm (n entries, plus one spare for the scan total) of the `hot`
-// highest-degree vertices; 0 < hot <= n.
-static g2_status select_hot(g2_graph *g, int32_t hot, int32_t *perm, cudaStream_t st) {
+// The `hot` highest-degree vertices (0 < hot <= n): the share slot of every
+// vertex, perm (n entries plus one spare for the scan total), and the least
+// degree among the hot vertices.
+static g2_status select_hot(g2_graph *g, int32_t hot, int32_t *perm, int32_t *min_deg,
+                            cudaStream_t st) {
     Topology *t = g->topo;
     const int32_t n = t->n;
     int32_t *hist, *a, *b;
@@ -671,35 +731,34 @@ static g2_status select_hot(g2_graph *g, int32_t hot, int32_t *perm, cudaStream_
     k_hot_flags<<<grid, kCta, 0, st>>>(t->rowptr, n, tlo, thi, b, need, a);
     G2_TRY(exclusive_scan_i32(g, a, perm, n, st));
     k_hot_perm<<<grid, kCta, 0, st>>>(a, n, hot, perm);
+    *min_deg = (int32_t)tlo;
     stats().launches += 6;
     G2_CK(cudaGetLastError());
     return G2_OK;
 }
 
-static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, const int32_t **perm,
+static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, ShareMap *sm,
                                       const int32_t **ccol) {
     Topology *t = g->topo;
-    if (t->pr_hot == hot && t->pr_perm) {
-        *perm = t->pr_perm;
-        *ccol = t->pr_ccol;
-        return G2_OK;
+    if (t->pr_hot != hot || !t->pr_slot_of) {
+        const int32_t n = t->n, m = t->m;
+        dfree(t->pr_slot_of, st);
+        dfree(t->pr_ccol, st);
+        t->pr_slot_of = t->pr_ccol = nullptr;
+        t->pr_hot = -1;
+        G2_CK(dmalloc(&t->pr_slot_of, ((size_t)std::max(n, 1) + 1) * 4, st));
+        G2_CK(dmalloc(&t->pr_ccol, ((size_t)std::max(m, 1) + kPad) * 4, st));
+        G2_TRY(select_hot(g, hot, t->pr_slot_of, &t->pr_hot_min_deg, st));
+        // only the padding past the last arc needs zeroing; the arcs are all written
+        G2_CK(cudaMemsetAsync(t->pr_ccol + m, 0, ((size_t)std::max(m, 1) - m + kPad) * 4, st));
+        if (m > 0)
+            k_remap_cols<<<grid_for(g, m, kCta), kCta, 0, st>>>(t->ccol, t->pr_slot_of, m,
+                                                                t->pr_ccol);
+        G2_CK(cudaGetLastError());
+        G2_CK(cudaStreamSynchronize(st));
+        t->pr_hot = hot;
     }
-    const int32_t n = t->n, m = t->m;
-    dfree(t->pr_perm, st);
-    dfree(t->pr_ccol, st);
-    t->pr_perm = t->pr_ccol = nullptr;
-    t->pr_hot = -1;
-    G2_CK(dmalloc(&t->pr_perm, ((size_t)std::max(n, 1) + 1) * 4, st));
-    G2_CK(dmalloc(&t->pr_ccol, ((size_t)std::max(m, 1) + kPad) * 4, st));
-    G2_TRY(select_hot(g, hot, t->pr_perm, st));
-    // only the padding past the last arc needs zeroing; the arcs are all written
-    G2_CK(cudaMemsetAsync(t->pr_ccol + m, 0, ((size_t)std::max(m, 1) - m + kPad) * 4, st));
-    if (m > 0)
-        k_remap_cols<<<grid_for(g, m, kCta), kCta, 0, st>>>(t->ccol, t->pr_perm, m, t->pr_ccol);
-    G2_CK(cudaGetLastError());
-    G2_CK(cudaStreamSynchronize(st));
-    t->pr_hot = hot;
-    *perm = t->pr_perm;
+    *sm = ShareMap{hot, t->pr_hot_min_deg, t->pr_slot_of};
     *ccol = t->pr_ccol;
     return G2_OK;
 }
@@ -736,10 +795,10 @@ static g2_status ensure_seg_layout(g2_graph *g, cudaStream_t st) {
 
 template <int CTA, bool HOT>
 static g2_status launch_pr_seg(g2_graph *g, const int32_t *pcol, int32_t hot, const float *contrib,
-                               float *y, cudaStream_t st) {
+                               float *y, double *dslots, double *dfin, cudaStream_t st) {
     Topology *t = g->topo;
+    // launched even without arcs: its first warp folds the dangling mass
     const int64_t nchunks = ((int64_t)t->m + kSegArcs - 1) / kSegArcs;
-    if (nchunks == 0) return G2_OK;
     const size_t smem = HOT ? (size_t)hot * 4 : 0;
     auto kern = k_pr_seg<CTA, HOT>;
     if (smem > 48 * 1024)
@@ -748,7 +807,7 @@ static g2_status launch_pr_seg(g2_graph *g, const int32_t *pcol, int32_t hot, co
     G2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, CTA, smem));
     if (b < 1) return fail(G2_EUNSUPPORTED, "PageRank sweep kernel does not fit on an SM");
     int64_t want = (nchunks * 32 + CTA - 1) / CTA;
-    int grid = (int)std::min<int64_t>(want, (int64_t)b * t->sm_count);
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b * t->sm_count));
     // slots [hot, warm) are loaded with L1 evict-last priority (off by
     // default: warm = hot; G2_PR_WARM sets it for sweeps)
     int32_t warm = hot;
@@ -756,7 +815,7 @@ static g2_status launch_pr_seg(g2_graph *g, const int32_t *pcol, int32_t hot, co
     KTime kt;
     ktime_begin(kt, "pr_round", st);
     kern<<<grid, CTA, smem, st>>>(pcol, t->seg_head, t->seg_chunk_rank, t->seg_nzrow, t->m, nchunks,
-                                  contrib, hot, warm, y);
+                                  contrib, hot, warm, y, dslots, dfin);
     ktime_end(kt, st);
     return G2_OK;
 }
@@ -786,16 +845,14 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
     if (n == 0) return G2_OK;
     const double inv_n = 1.0 / (double)n;
     float *cbuf[2], *acc;
-    G2_TRY(ws(g, B_F0, (size_t)n, &cbuf[0]));
-    G2_TRY(ws(g, B_F1, (size_t)n, &cbuf[1]));
     G2_TRY(ws(g, B_F2, (size_t)n + 1, &acc));
-    // D accumulators: dd[0], dd[1] for the merge and generic paths; two
-    // regions of kDSlots slots (dd[0..R), dd[R..2R)) for the segmented sweep,
-    // whose region A holds D0 in its slot 0 (= dd[0])
+    // D: dd[0], dd[1] for the merge and generic paths, dd[2], dd[3] for the
+    // segmented sweep's rounds; dd[8..8+R) the slots the x0 and vertex
+    // passes accumulate into (zero to start; every fold zeroes them again)
     constexpr size_t R = (size_t)kDSlots * kDStride;
     double *dd;
-    G2_TRY(ws(g, B_D1, 2 * R, &dd));
-    G2_CK(cudaMemsetAsync(dd, 0, 2 * R * sizeof(double), st));
+    G2_TRY(ws(g, B_D1, 8 + R, &dd));
+    G2_CK(cudaMemsetAsync(dd, 0, (8 + R) * sizeof(double), st));
     const g2_schedule &s = h.s1;  // one schedule for every round (the frontier is always all vertices)
     const float base = (float)((1.0 - damping) * inv_n);
     const bool merge = tuned_default || (s.direction == G2_PULL && s.load_balance == G2_LB_EDGE_ONLY);
@@ -804,40 +861,55 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
         if (s.kernel_fusion) return fail(G2_EUNSUPPORTED, "PageRank has no fused variant");
     }
     PrCfg cfg = pr_config(g);
-    const int32_t *perm = nullptr, *ccol = t->ccol;
-    if (merge && cfg.hot > 0) G2_TRY(ensure_pr_hot_layout(g, cfg.hot, st, &perm, &ccol));
+    ShareMap sm{0, 0, nullptr};
+    const int32_t *ccol = t->ccol;
+    if (merge && cfg.hot > 0) G2_TRY(ensure_pr_hot_layout(g, cfg.hot, st, &sm, &ccol));
+    // shares: slots 0..H-1 for the cached vertices, H + v for vertex v
+    G2_TRY(ws(g, B_F0, (size_t)n + sm.hot, &cbuf[0]));
+    G2_TRY(ws(g, B_F1, (size_t)n + sm.hot, &cbuf[1]));
     // vertex passes end with one fp64 atomic per CTA on a single address, and
     // same-address atomics serialise: few CTAs, each striding over many vertices
     const int vgrid = (int)std::min<int64_t>((n + kCta - 1) / kCta, (int64_t)t->sm_count * 2);
-    // the segmented sweep's rounds read D over kDSlots slots, so its x0 pass
-    // runs on a full grid of quads and spreads D0 over them; the other paths
-    // read dd[0] alone
+    // the x0 pass, one quad per thread; D0 goes into the slots, which the
+    // first sweep folds into dd[2] (segmented sweep) or k_pr_fold into dd[0]
     const bool seg = merge && !cfg.merge;
-    const int igrid = seg ? (int)((((int64_t)n + 3) / 4 + kCta - 1) / kCta) : vgrid;
-    k_pr_init<<<std::max(igrid, 1), kCta, 0, st>>>(t->rowptr, n, perm, cbuf[0], dd,
-                                                   seg ? kDSlots - 1 : 0, rank, inv_n);
+    const int igrid = (int)((((int64_t)n + 3) / 4 + kCta - 1) / kCta);
+    k_pr_init<<<std::max(igrid, 1), kCta, 0, st>>>(t->rowptr, n, sm, cbuf[0], dd + 8, rank, inv_n);
     stats().launches += 1;
+    if (!seg) {
+        k_pr_fold<<<1, 32, 0, st>>>(dd + 8, dd);
+        stats().launches += 1;
+    }
     if (iters <= 0) return G2_OK;
     if (merge && !cfg.merge) {
         G2_TRY(ensure_seg_layout(g, st));
-        const int32_t hot = perm ? cfg.hot : 0;
+        const int32_t hot = sm.hot;
         G2_CK(cudaMemsetAsync(acc, 0, (size_t)(n + 1) * 4, st));
         const int vblocks = (int)((((int64_t)n + 3) / 4 + kCta - 1) / kCta);
         for (int32_t it = 0; it < iters; ++it) {
             const float *c0 = cbuf[it & 1];
             float *c1 = cbuf[(it + 1) & 1];
-            double *dprev = dd + (it & 1) * R, *dnext = dd + ((it + 1) & 1) * R;
-            G2_CK(cudaMemsetAsync(dnext, 0, R * sizeof(double), st));
+            // D_{t-1}: the sweep folds the slots of the previous pass (the x0
+            // pass for round 0) into dd[2 + (t & 1)] for this round's vertex pass
+            double *dprev = dd + 2 + (it & 1);
+            double *fold = dd + 8;
             if (cfg.cta == 512) {
-                if (hot) G2_TRY((launch_pr_seg<512, true>(g, ccol, hot, c0, acc, st)));
-                else G2_TRY((launch_pr_seg<512, false>(g, ccol, hot, c0, acc, st)));
+                if (hot) G2_TRY((launch_pr_seg<512, true>(g, ccol, hot, c0, acc, fold, dprev, st)));
+                else G2_TRY((launch_pr_seg<512, false>(g, ccol, hot, c0, acc, fold, dprev, st)));
             } else {
-                if (hot) G2_TRY((launch_pr_seg<1024, true>(g, ccol, hot, c0, acc, st)));
-                else G2_TRY((launch_pr_seg<1024, false>(g, ccol, hot, c0, acc, st)));
+                if (hot) G2_TRY((launch_pr_seg<1024, true>(g, ccol, hot, c0, acc, fold, dprev, st)));
+                else G2_TRY((launch_pr_seg<1024, false>(g, ccol, hot, c0, acc, fold, dprev, st)));
             }
-            k_pr_seg_vertex<<<vblocks, kCta, 0, st>>>(t->rowptr, n, perm, acc, c1, rank,
-                                                      it == iters - 1, dprev, dnext, base, damping,
-                                                      inv_n);
+            KTime kv;
+            ktime_begin(kv, "pr_vertex", st);
+            // x itself is written by the last round only
+            auto vk = it == iters - 1 ? (cfg.vtx_full ? k_pr_seg_vertex<true, 8>
+                                                      : k_pr_seg_vertex<true, 6>)
+                                      : (cfg.vtx_full ? k_pr_seg_vertex<false, 8>
+                                                      : k_pr_seg_vertex<false, 6>);
+            vk<<<vblocks, kCta, 0, st>>>(t->rowptr, n, sm, acc, c1, rank, dprev, dd + 8, base,
+                                         damping, inv_n);
+            ktime_end(kv, st);
             stats().launches += 2;
             stats().iterations++;
             stats().pull_rounds++;
@@ -866,10 +938,11 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
         a.crowptr = t->crowptr;
         a.ccol = ccol;
         a.rowptr = t->symmetric ? nullptr : t->rowptr;
-        a.perm = perm;
+        a.slot_of = sm.slot_of;
+        a.hot_min_deg = sm.min_deg;
         a.tile_r = tile_r;
         a.ntiles = ntiles;
-        a.hot = perm ? cfg.hot : 0;
+        a.hot = sm.hot;
         a.acc = acc;
         a.base = base;
         a.damp = damping;

@@ -21,6 +21,22 @@ namespace g2 {
 // block barrier or search is needed anywhere.
 constexpr int kSegArcs = 128;  // arcs per warp chunk
 
+// The dangling mass D of a vertex pass is accumulated in kDSlots slots (one
+// per 128-byte line) instead of one word, so the warps' atomics spread over
+// many L2 lines instead of serialising on one address.
+constexpr int kDSlots = 64;
+constexpr int kDStride = 16;  // doubles between slots
+
+// One warp: *fin = the sum of the slots, which are zeroed for the next pass.
+__device__ __forceinline__ void fold_dslots(double *slots, double *fin) {
+    const int lane = threadIdx.x & 31;
+    double v = slots[lane * kDStride] + slots[(lane + 32) * kDStride];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(G2_FULL, v, o);
+    slots[lane * kDStride] = 0.0;
+    slots[(lane + 32) * kDStride] = 0.0;
+    if (lane == 0) *fin = v;
+}
+
 __device__ __forceinline__ float ld_evict_last(const float *p) {
     float v;
     asm volatile("ld.global.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
@@ -43,8 +59,13 @@ template <int CTA, bool HOT>
 __global__ void __launch_bounds__(CTA) k_pr_seg(const int32_t *pcol, const uint32_t *head,
                                                 const int32_t *chunk_rank, const int32_t *nzrow,
                                                 int32_t m, int64_t nchunks, const float *contrib,
-                                                int32_t hot, int32_t warm, float *y) {
+                                                int32_t hot, int32_t warm, float *y,
+                                                double *dslots, double *dfin) {
     extern __shared__ float s_hot[];
+    // The previous vertex pass left D in kDSlots slots: the first warp of
+    // block 0 adds them into *dfin (read by the next vertex pass) and zeroes
+    // them (dslots null: nothing to fold).
+    if (dslots && blockIdx.x == 0 && threadIdx.x < 32) fold_dslots(dslots, dfin);
     if (HOT) {
         for (int32_t i = threadIdx.x; i < hot; i += CTA) s_hot[i] = __ldg(contrib + i);
         __syncthreads();
