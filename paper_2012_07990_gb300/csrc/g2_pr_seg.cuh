@@ -71,31 +71,43 @@ __global__ void __launch_bounds__(CTA) k_pr_seg(const int32_t *pcol, const uint3
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * CTA + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * CTA) >> 5;
+    // chunk indices fit 32 bits: m < 2^31 arcs, 128 arcs per chunk
+    const int32_t nch = (int32_t)nchunks;
+    const int32_t gw = (int32_t)((blockIdx.x * CTA + threadIdx.x) >> 5);
+    const int32_t nw = (int32_t)((gridDim.x * CTA) >> 5);
     const int sh = (lane & 7) * 4;
     const unsigned below = (1u << sh) - 1u;
+    const int4 *pcol4 = reinterpret_cast<const int4 *>(pcol) + lane;
+    const uint4 *head4 = reinterpret_cast<const uint4 *>(head);
     // software pipeline: the next chunk's column ids and head words are
     // loaded while this chunk's gathers are in flight
     int4 nu4 = make_int4(0, 0, 0, 0);
     uint4 nh = make_uint4(0, 0, 0, 0);
-    if (gw < nchunks) {
-        nu4 = reinterpret_cast<const int4 *>(pcol + gw * kSegArcs)[lane];
-        nh = reinterpret_cast<const uint4 *>(head)[gw];
+    if (gw < nch) {
+        nu4 = pcol4[(int64_t)gw * (kSegArcs / 4)];
+        nh = head4[gw];
     }
-    for (int64_t c = gw; c < nchunks; c += nw) {
-        const int64_t b = c * kSegArcs;
+    for (int32_t c = gw; c < nch; c += nw) {
         const int4 u4 = nu4;
         const uint32_t w0 = nh.x, w1 = nh.y, w2 = nh.z, w3 = nh.w;
-        if (c + nw < nchunks) {
-            nu4 = reinterpret_cast<const int4 *>(pcol + (c + nw) * kSegArcs)[lane];
-            nh = reinterpret_cast<const uint4 *>(head)[c + nw];
+        if (c + nw < nch) {
+            nu4 = pcol4[(int64_t)(c + nw) * (kSegArcs / 4)];
+            nh = head4[c + nw];
         }
-        const int64_t a0 = b + 4 * lane;
-        float v0 = a0 + 0 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.x) : 0.f;
-        float v1 = a0 + 1 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.y) : 0.f;
-        float v2 = a0 + 2 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.z) : 0.f;
-        float v3 = a0 + 3 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.w) : 0.f;
+        float v0, v1, v2, v3;
+        if ((int64_t)(c + 1) * kSegArcs <= m) {
+            v0 = seg_gather<HOT>(contrib, s_hot, hot, warm, u4.x);
+            v1 = seg_gather<HOT>(contrib, s_hot, hot, warm, u4.y);
+            v2 = seg_gather<HOT>(contrib, s_hot, hot, warm, u4.z);
+            v3 = seg_gather<HOT>(contrib, s_hot, hot, warm, u4.w);
+        } else {
+            // the last, partial chunk
+            const int64_t a0 = (int64_t)c * kSegArcs + 4 * lane;
+            v0 = a0 + 0 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.x) : 0.f;
+            v1 = a0 + 1 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.y) : 0.f;
+            v2 = a0 + 2 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.z) : 0.f;
+            v3 = a0 + 3 < m ? seg_gather<HOT>(contrib, s_hot, hot, warm, u4.w) : 0.f;
+        }
         const int wi = lane >> 3;
         const uint32_t mine = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
         const uint32_t hf = (mine >> sh) & 0xFu;
@@ -129,16 +141,17 @@ __global__ void __launch_bounds__(CTA) k_pr_seg(const int32_t *pcol, const uint3
         const bool has_head = seen > 0;
         const float T = has_head ? run : 0.f;
         // segmented inclusive scan over lanes: q = T at a headed lane, else
-        // q(previous lane) + A
+        // q(previous lane) + A.  Shares are >= 0, so the partial sums are too
+        // and the head flag travels in the sign bit: one shuffle per step.
         float q = has_head ? T : A;
         bool f = has_head;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            float qo = __shfl_up_sync(G2_FULL, q, d);
-            bool fo = __shfl_up_sync(G2_FULL, f, d);
+            const uint32_t enc = __float_as_uint(q) | (f ? 0x80000000u : 0u);
+            const uint32_t o = __shfl_up_sync(G2_FULL, enc, d);
             if (lane >= d && !f) {
-                q += qo;
-                f = fo;
+                q += __uint_as_float(o & 0x7fffffffu);
+                f = (o >> 31) != 0u;
             }
         }
         float qprev = __shfl_up_sync(G2_FULL, q, 1);
