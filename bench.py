@@ -451,6 +451,99 @@ def run_grid_workload(args):
     print(json.dumps({"workload": f"grid{W}x{W}_sssp_bfs", "n": G.n, "m": G.m, **res}))
 
 
+def run_tune_workload(args):
+    """Autotuner: for a power-law graph (RMAT-18) and a road-like grid
+    (1024^2), BFS and delta-stepping SSSP (and PageRank on RMAT-18) are
+    tuned from cold (random sampling + successive halving); the tuned
+    schedule is compared with the library's default schedule and with the
+    paper's default schedule (all Table II fields at their defaults).  Then
+    a sibling graph of each family (RMAT-19 seed 2, grid 1200^2 seed 2) is
+    tuned once from cold and once warm-started from the first graph's cache
+    entry with a sixth of the random samples."""
+    import tempfile
+    import torch
+    from paper_2012_07990_gb300 import build_native
+    build_native.build()
+    from paper_2012_07990_gb300 import autotune as at
+    from paper_2012_07990_gb300 import g2
+    from paper_2012_07990_gb300 import graphgen as gg
+
+    fams = {"powerlaw": (lambda: gg.rmat(18, seed=1), lambda: gg.rmat(19, seed=2), 255),
+            "road": (lambda: gg.road_grid(1024, seed=1), lambda: gg.road_grid(1200, seed=2), 1000)}
+    algos = {"powerlaw": ("bfs", "sssp", "pr"), "road": ("bfs", "sssp")}
+    paper_default = {"criteria": 0, "threshold": 0.0, "s1": at._simple(), "s2": at._simple()}
+    cache = at.TuneCache(os.path.join(tempfile.mkdtemp(), "tune.json"))
+    out = {"workload": "autotune", "graphs": {}}
+
+    def evaluate(G, w, algo):
+        dg = g2.load_graph(G, w)
+        src = G.max_degree_vertex() if G.name.startswith("rmat") else 0
+        if algo == "sssp":
+            base = at.gpu_evaluator(g2, dg, "sssp", src=src)
+
+            def cost(d):
+                # the paper's default schedule leaves delta at its default, 1
+                if not d.get("tuned_default") and d["s1"]["delta"] == 0:
+                    d = json.loads(json.dumps(d))
+                    d["s1"]["delta"] = d["s2"]["delta"] = 1
+                return base(d)
+            return dg, cost
+        return dg, at.gpu_evaluator(g2, dg, algo, src=src)
+
+    for fam, (mk1, mk2, wmax) in fams.items():
+        G1, G2 = mk1(), mk2()
+        w1, w2 = gg.pair_weights(G1, wmax, seed=1), gg.pair_weights(G2, wmax, seed=2)
+        f1, f2 = at.graph_features(G1.n, G1.rowptr), at.graph_features(G2.n, G2.rowptr)
+        fp1 = at.graph_fingerprint(G1.n, G1.rowptr, G1.col)
+        rows = {}
+        for algo in algos[fam]:
+            dg, cost = evaluate(G1, w1, algo)
+            t0 = time.perf_counter()
+            res = at.tune(algo, cost, n_samples=24, seed=1)
+            tune_s = time.perf_counter() - t0
+            cache.put(fp1, algo, res, f1)
+            best = min(cost(res.best) for _ in range(3))
+            lib = min(cost({"tuned_default": True}) if algo in ("cc", "pr") else
+                      _lib_default_ms(g2, dg, G1, algo) for _ in range(3))
+            pdef = None
+            # delta = 1 on a road grid means ~10^6 buckets with a host round
+            # trip each: not timed
+            if not (algo == "sssp" and fam == "road"):
+                try:
+                    pdef = min(cost(paper_default) for _ in range(2))
+                except Exception:  # unsupported for this algorithm
+                    pdef = None
+            row = {"tuned_ms": round(best, 3), "library_default_ms": round(lib, 3),
+                   "paper_default_ms": None if pdef is None else round(pdef, 3),
+                   "evaluations": res.evaluated, "tune_s": round(tune_s, 2),
+                   "best": res.best}
+            dg.free()
+            # sibling graph: cold search vs warm start with 4 random samples
+            dg2, cost2 = evaluate(G2, w2, algo)
+            cold = at.tune(algo, cost2, n_samples=24, seed=5)
+            warm = at.tune(algo, cost2, n_samples=4, seed=5, warm=cache.warm_start(f2, algo))
+            row["sibling"] = {"cold_ms": round(min(cost2(cold.best) for _ in range(3)), 3),
+                              "cold_evaluations": cold.evaluated,
+                              "warm_ms": round(min(cost2(warm.best) for _ in range(3)), 3),
+                              "warm_evaluations": warm.evaluated}
+            dg2.free()
+            rows[algo] = row
+        out["graphs"][f"{fam}:{G1.name}"] = rows
+    print(json.dumps(out))
+
+
+def _lib_default_ms(g2, dg, G, algo):
+    """The library's tuned default schedule (NULL) for BFS / SSSP, timed."""
+    import torch
+    out = torch.empty(G.n, dtype=torch.int32, device="cuda")
+    src = G.max_degree_vertex() if G.name.startswith("rmat") else 0
+    if algo == "bfs":
+        fn = lambda: g2.g2_bfs(dg, src, out, None, None)
+    else:
+        fn = lambda: g2.g2_sssp_delta(dg, src, 64 if G.name.startswith("rmat") else 4096, out, None)
+    return _timed(fn, reps=1)
+
+
 def run_batched_workload(args):
     """RMAT scale 21 (ef 16, symmetric): 64-source BFS in one traversal vs 64
     single-source BFS calls (tuned and fixed TWC PUSH); 32-source SSSP (weights
@@ -557,7 +650,8 @@ def main():
     ap.add_argument("--serve-pool", choices=["full", "small"], default="full")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=1.0)
-    ap.add_argument("--workload", choices=["rmat22", "grid", "batched", "serve"], default="rmat22",
+    ap.add_argument("--workload", choices=["rmat22", "grid", "batched", "serve", "tune"],
+                    default="rmat22",
                     help="rmat22: the default step (the JSON line the driver reads); grid and "
                          "batched: the road-grid and multi-source configurations")
     ap.add_argument("--grid", type=int, default=4096)
@@ -579,6 +673,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched_workload(args)
+        return
+    if args.workload == "tune":
+        run_tune_workload(args)
         return
     if args.workload == "serve":
         run_serve_workload(args)

@@ -213,7 +213,8 @@ g2_status g2_edgeset_apply(g2_graph *g, g2_op op, g2_frontier *in, void *vdata, 
  * level up, -1 unreachable).  Loop until the frontier is empty.  With kernel
  * fusion the whole loop is one persistent cooperative kernel.  NULL schedule:
  * direction-optimising hybrid, STRICT PUSH below 2% of n, VERTEX_BASED PULL
- * over a bitmap otherwise. */
+ * over a bitmap otherwise; on a bounded-degree graph (largest out-degree
+ * <= 32: road networks, meshes) fused WM PUSH instead. */
 g2_status g2_bfs(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                  const g2_hybrid *sched, void *stream);
 
@@ -232,7 +233,8 @@ g2_status g2_cc(g2_graph *g, int32_t *label, const g2_hybrid *sched, void *strea
  * (Sec. III and V, configDelta): dist int32[n] device, INT32_MAX unreachable.
  * delta > 0 overrides the schedule's delta.  Needs weights >= 1.
  * G2_EOVERFLOW if a distance would reach INT32_MAX.  NULL schedule: STRICT
- * PUSH, unfused. */
+ * PUSH, unfused; fused WM PUSH on a bounded-degree graph (largest out-degree
+ * <= 32). */
 g2_status g2_sssp_delta(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
                         const g2_hybrid *sched, void *stream);
 
@@ -252,7 +254,8 @@ g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, float *rank,
  * they neither overflow nor underflow on high-diameter graphs.  Each level's
  * discovery follows the (hybrid) schedule; with kernel fusion each source
  * runs in one persistent cooperative kernel.  NULL schedule: the
- * direction-optimising hybrid of g2_bfs. */
+ * direction-optimising hybrid of g2_bfs; fused WM PUSH on a bounded-degree
+ * graph (largest out-degree <= 32). */
 g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc,
                 const g2_hybrid *sched, void *stream);
 

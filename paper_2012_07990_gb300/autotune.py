@@ -48,7 +48,9 @@ def sample_schedule(algo: str, rng: random.Random) -> dict:
         tau = rng.choice([0.0, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 1e9])
         return {"criteria": 1, "threshold": tau, "s1": push, "s2": pull}
     if algo == "sssp":
-        delta = 2 ** rng.randrange(0, 15)
+        # deltas below 8 turn delta-stepping into thousands of near-empty
+        # buckets on every input here (weights >= 1, means 128-500)
+        delta = 2 ** rng.randrange(3, 15)
         fused = rng.random() < 0.3
         lb = rng.choice(["VERTEX_BASED", "WM", "CM", "ETWC"] if fused else PUSH_FRONTIER_LBS)
         s = _simple(lb=lb, delta=delta, kernel_fusion=fused,
@@ -161,9 +163,11 @@ def successive_halving(cost, candidates: list[dict], reps0: int = 1, eta: int = 
 
 
 def tune(algo: str, cost, n_samples: int = 24, seed: int = 1, eta: int = 3,
-         max_evals: int | None = None) -> TuneResult:
+         max_evals: int | None = None, warm: list[dict] | None = None) -> TuneResult:
+    """Search `n_samples` random points plus the known-good seeds and any
+    warm-start schedules (tried first)."""
     rng = random.Random(seed)
-    cands = seeds(algo) + [sample_schedule(algo, rng) for _ in range(n_samples)]
+    cands = list(warm or []) + seeds(algo) + [sample_schedule(algo, rng) for _ in range(n_samples)]
     return successive_halving(cost, cands, eta=eta, max_evals=max_evals)
 
 
@@ -182,7 +186,26 @@ def graph_fingerprint(n: int, rowptr, col) -> str:
     return h.hexdigest()[:24]
 
 
+def graph_features(n: int, rowptr) -> list[float]:
+    """What the best schedule depends on, as a small vector: log2 of the
+    vertex and arc counts, log2 of the mean and maximum degree, the share of
+    vertices without arcs, and the coefficient of variation of the degrees
+    (power-law graphs: large; road-like grids: small)."""
+    import numpy as np
+    deg = np.diff(np.asarray(rowptr, dtype=np.int64))
+    m = int(deg.sum())
+    mean = m / max(n, 1)
+    cv = float(deg.std() / mean) if mean > 0 else 0.0
+    return [math.log2(max(n, 1)), math.log2(max(m, 1)), math.log2(max(mean, 1e-9) + 1.0),
+            math.log2(float(deg.max(initial=0)) + 1.0), float((deg == 0).mean()) * 10.0,
+            math.log2(cv + 1.0) * 4.0]
+
+
 class TuneCache:
+    """JSON cache: per graph fingerprint and algorithm, the best schedules
+    found (best first) and the graph's features, which warm-start the search
+    on graphs that were never tuned."""
+
     def __init__(self, path: str):
         self.path = path
         self.data = {}
@@ -193,21 +216,55 @@ class TuneCache:
     def get(self, fp: str, algo: str):
         return self.data.get(f"{fp}:{algo}")
 
-    def put(self, fp: str, algo: str, result: TuneResult):
+    def put(self, fp: str, algo: str, result: TuneResult, features: list[float] | None = None,
+            top: int = 3):
+        ranked = sorted((h for h in result.history if "ms" in h),
+                        key=lambda h: (-h["reps"], h["ms"]))
+        best, seen = [], set()
+        for h in [{"schedule": result.best}] + ranked:
+            k = key_of(h["schedule"])
+            if k not in seen:
+                seen.add(k)
+                best.append(h["schedule"])
+            if len(best) == top:
+                break
         self.data[f"{fp}:{algo}"] = {"schedule": result.best, "ms": result.best_ms,
-                                      "evaluated": result.evaluated}
+                                      "evaluated": result.evaluated, "top": best,
+                                      "features": features}
         tmp = self.path + ".tmp"
         with open(tmp, "w") as f:
             json.dump(self.data, f, indent=1, sort_keys=True)
         os.replace(tmp, self.path)
 
+    def warm_start(self, features: list[float], algo: str, k: int = 2) -> list[dict]:
+        """The best schedules of the k cached graphs nearest to `features`
+        (Euclidean distance), nearest first."""
+        near = []
+        for key, v in self.data.items():
+            if not key.endswith(f":{algo}") or not v.get("features"):
+                continue
+            d = math.dist(v["features"], features)
+            near.append((d, v.get("top") or [v["schedule"]]))
+        near.sort(key=lambda x: x[0])
+        out, seen = [], set()
+        for _, tops in near[:k]:
+            for sch in tops:
+                if key_of(sch) not in seen:
+                    seen.add(key_of(sch))
+                    out.append(sch)
+        return out
 
-def tune_cached(cache: TuneCache, fp: str, algo: str, cost, **kw) -> dict:
+
+def tune_cached(cache: TuneCache, fp: str, algo: str, cost, features: list[float] | None = None,
+                warm_k: int = 2, **kw) -> dict:
+    """The cached best schedule of this graph, else a search warm-started
+    from the nearest tuned graphs (when features are given), then cached."""
     hit = cache.get(fp, algo)
     if hit is not None:
         return hit["schedule"]
-    res = tune(algo, cost, **kw)
-    cache.put(fp, algo, res)
+    warm = cache.warm_start(features, algo, warm_k) if features is not None else None
+    res = tune(algo, cost, warm=warm, **kw)
+    cache.put(fp, algo, res, features)
     return res.best
 
 

@@ -513,11 +513,28 @@ g2_status sssp_plain(g2_graph *g, int32_t src, int32_t delta, int32_t *dist, con
 
 using namespace g2;
 
+// The fused WM PUSH loop that bounded-degree graphs run by default.
+static g2_hybrid fused_wm_hybrid() {
+    g2_hybrid h = default_hybrid();
+    h.s1.load_balance = G2_LB_WM;
+    h.s1.kernel_fusion = 1;
+    h.s2 = h.s1;
+    return h;
+}
+
+static bool bounded_degree(g2_graph *g, cudaStream_t st) {
+    int32_t d = 0;
+    return max_out_degree(g, st, &d) == G2_OK && d <= kBoundedDegree;
+}
+
 // Tuned schedule for BFS when the caller passes none (measured on GB300 with
 // RMAT-22): direction-optimising hybrid, STRICT PUSH on a sparse queue while
 // the frontier holds < 2% of the vertices, else VERTEX_BASED PULL over a
-// bitmap input with an unfused bitmap output and no deduplication.
-static g2_hybrid tuned_bfs_hybrid() {
+// bitmap input with an unfused bitmap output and no deduplication.  On a
+// bounded-degree graph: fused WM PUSH (measured on a 1024^2 road grid: 7.2 ms
+// against 35 ms for the hybrid).
+static g2_hybrid tuned_bfs_hybrid(g2_graph *g, cudaStream_t st) {
+    if (bounded_degree(g, st)) return fused_wm_hybrid();
     g2_hybrid h = default_hybrid();
     h.criteria = G2_INPUT_VERTEXSET_SIZE;
     h.threshold = 0.02f;
@@ -530,8 +547,10 @@ static g2_hybrid tuned_bfs_hybrid() {
     return h;
 }
 
-// Tuned schedule for delta-stepping when the caller passes none: STRICT PUSH.
-static g2_hybrid tuned_sssp_hybrid() {
+// Tuned schedule for delta-stepping when the caller passes none: STRICT PUSH;
+// fused WM PUSH on a bounded-degree graph.
+static g2_hybrid tuned_sssp_hybrid(g2_graph *g, cudaStream_t st) {
+    if (bounded_degree(g, st)) return fused_wm_hybrid();
     g2_hybrid h = default_hybrid();
     h.s1.load_balance = G2_LB_STRICT;
     return h;
@@ -545,7 +564,7 @@ g2_status g2_bfs(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent, cons
     if (!g || !depth) return fail(G2_EINVAL, "null graph or depth");
     G2_TRY(check_src(g, src));
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : tuned_bfs_hybrid();
+    g2_hybrid h = sched ? *sched : tuned_bfs_hybrid(g, st);
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));
     if (h.s1.kernel_fusion) {
@@ -577,7 +596,7 @@ g2_status g2_sssp_delta(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
     G2_TRY(check_src(g, src));
     if (!g->topo->w) return fail(G2_EINVAL, "SSSP needs arc weights");
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : tuned_sssp_hybrid();
+    g2_hybrid h = sched ? *sched : tuned_sssp_hybrid(g, st);
     if (delta <= 0) delta = h.s1.delta > 0 ? h.s1.delta : 1;
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));

@@ -376,8 +376,17 @@ g2_status bc_run(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const 
 using namespace g2;
 
 // Tuned schedule when the caller passes none: the direction-optimising
-// hybrid of BFS (STRICT PUSH below 2% of n, VERTEX_BASED PULL over a bitmap).
-static g2_hybrid tuned_bc_hybrid() {
+// hybrid of BFS (STRICT PUSH below 2% of n, VERTEX_BASED PULL over a bitmap);
+// on a bounded-degree graph each source runs fused (WM PUSH).
+static g2_hybrid tuned_bc_hybrid(g2_graph *g, cudaStream_t st) {
+    int32_t dmax = 0;
+    if (max_out_degree(g, st, &dmax) == G2_OK && dmax <= kBoundedDegree) {
+        g2_hybrid h = default_hybrid();
+        h.s1.load_balance = G2_LB_WM;
+        h.s1.kernel_fusion = 1;
+        h.s2 = h.s1;
+        return h;
+    }
     g2_hybrid h = default_hybrid();
     h.criteria = G2_INPUT_VERTEXSET_SIZE;
     h.threshold = 0.02f;
@@ -395,7 +404,7 @@ extern "C" g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *
     for (int32_t i = 0; i < k; ++i)
         if (srcs[i] < 0 || srcs[i] >= g->topo->n) return fail(G2_EINVAL, "source vertex out of range");
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : tuned_bc_hybrid();
+    g2_hybrid h = sched ? *sched : tuned_bc_hybrid(g, st);
     if (h.s1.kernel_fusion && h.criteria != G2_CRITERIA_NONE && !h.s2.kernel_fusion)
         return fail(G2_EUNSUPPORTED, "kernel fusion must be set on both hybrid schedules");
     int32_t *d_err;

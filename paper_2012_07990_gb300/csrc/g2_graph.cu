@@ -535,6 +535,30 @@ g2_status exclusive_scan_i32(g2_graph *g, const int32_t *in, int32_t *out, int32
     return G2_OK;
 }
 
+__global__ void k_max_degree(const int32_t *rowptr, int32_t n, int32_t *out) {
+    int32_t best = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        best = max(best, rowptr[v + 1] - rowptr[v]);
+    best = __reduce_max_sync(G2_FULL, best);
+    if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(out, best);
+}
+
+g2_status max_out_degree(g2_graph *g, cudaStream_t st, int32_t *out) {
+    Topology *t = g->topo;
+    if (t->max_out_deg < 0) {
+        int32_t *d;
+        G2_TRY(ws(g, B_CTR, 64, &d));
+        G2_CK(cudaMemsetAsync(d + 48, 0, 4, st));
+        if (t->n > 0) k_max_degree<<<grid_for(g, t->n, 256), 256, 0, st>>>(t->rowptr, t->n, d + 48);
+        G2_CK(cudaMemcpyAsync(g->h_ctr + 48, d + 48, 4, cudaMemcpyDeviceToHost, st));
+        G2_CK(cudaStreamSynchronize(st));
+        t->max_out_deg = g->h_ctr[48];
+    }
+    *out = t->max_out_deg;
+    return G2_OK;
+}
+
 g2_status ensure_coo(g2_graph *g, cudaStream_t st) {
     Topology *t = g->topo;
     if (t->coo_src || t->m == 0) return G2_OK;
@@ -802,6 +826,7 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     t->rowptr = t->col = t->w = t->crowptr = t->ccol = t->cw = t->coo_src = nullptr;
     t->eb_N = 0; t->eb_nseg = 0; t->eb_src = t->eb_dst = nullptr; t->eb_seg = nullptr;
     t->h_eb_seg = nullptr;
+    t->max_out_deg = -1;
     t->pr_hot = -1; t->pr_hot_min_deg = 0; t->pr_slot_of = t->pr_ccol = nullptr;
     t->seg_head = nullptr; t->seg_nzrow = t->seg_chunk_rank = nullptr; t->seg_nnzrow = 0;
     g2_graph *g = new_handle(t);

@@ -101,6 +101,7 @@ struct Topology {
     int64_t *h_eb_seg;   // host copy
     // PageRank share-cache layout: the share slot of every vertex, the least
     // out-degree of the cached vertices, the CSC column ids as share slots
+    int32_t max_out_deg;  // largest out-degree (-1: not computed yet)
     int32_t pr_hot;
     int32_t pr_hot_min_deg;
     int32_t *pr_slot_of, *pr_ccol;
@@ -176,6 +177,14 @@ g2_status ensure_coo(g2_graph *g, cudaStream_t st);
 // EdgeBlocking layout for segment size N (Algorithm 1), built on the device.
 g2_status ensure_edge_block(g2_graph *g, int32_t N, cudaStream_t st);
 int32_t default_block_size(const g2_graph *g, int bytes_per_vertex);
+
+// Largest out-degree of the graph (computed on the device once, then kept).
+g2_status max_out_degree(g2_graph *g, cudaStream_t st, int32_t *out);
+// Bounded-degree graphs (road networks, meshes: largest out-degree <= 32)
+// run BFS, SSSP and BC with kernel fusion when the caller gives no schedule:
+// their many small levels cost more in launches and host round trips than in
+// arcs.
+constexpr int32_t kBoundedDegree = 32;
 
 // Device-wide exclusive scan of int32 (out[0..count], out[count] = total).
 g2_status exclusive_scan_i32(g2_graph *g, const int32_t *in, int32_t *out, int32_t count,

@@ -77,6 +77,52 @@ def test_cache_roundtrip(tmp_path):
     assert len(calls) == n_calls  # served from the cache
 
 
+def test_graph_features_separate_graph_families():
+    from paper_2012_07990_gb300 import graphgen as gg
+    r10, r11 = gg.rmat(10, seed=1), gg.rmat(11, seed=1)
+    g64, g90 = gg.road_grid(64, seed=1), gg.road_grid(90, seed=1)
+    f = {k: at.graph_features(g.n, g.rowptr) for k, g in
+         (("r10", r10), ("r11", r11), ("g64", g64), ("g90", g90))}
+    import math
+    assert math.dist(f["r10"], f["r11"]) < math.dist(f["r10"], f["g90"])
+    assert math.dist(f["g64"], f["g90"]) < math.dist(f["g64"], f["r11"])
+    assert all(len(v) == 6 and all(math.isfinite(x) for x in v) for v in f.values())
+
+
+def test_warm_start_seeds_from_the_nearest_tuned_graph(tmp_path):
+    """A synthetic cost model in which the best schedule depends on the graph
+    family: tuning a power-law and a grid graph fills the cache; a new graph
+    of either family gets the matching family's best schedules as warm seeds
+    and, with a budget too small for random search alone, still finds its
+    optimum."""
+    from paper_2012_07990_gb300 import graphgen as gg
+    cache = at.TuneCache(str(tmp_path / "tune.json"))
+
+    def cost_for(family):
+        def cost(d):
+            s = d["s1"]
+            if family == "powerlaw":
+                return 1.0 if (s["lb"] == "STRICT" and d["threshold"] == 0.02) else 5.0
+            return 1.0 if (s["lb"] == "WM" and s["kernel_fusion"]) else 5.0
+        return cost
+
+    graphs = {"powerlaw": (gg.rmat(10, seed=1), gg.rmat(11, seed=2)),
+              "grid": (gg.road_grid(64, seed=1), gg.road_grid(80, seed=2))}
+    for fam, (g, _) in graphs.items():
+        fp = at.graph_fingerprint(g.n, g.rowptr, g.col)
+        at.tune_cached(cache, fp, "bfs", cost_for(fam), features=at.graph_features(g.n, g.rowptr),
+                       n_samples=12, seed=3)
+    for fam, (_, g) in graphs.items():
+        feats = at.graph_features(g.n, g.rowptr)
+        warm = cache.warm_start(feats, "bfs", k=1)
+        assert warm and cost_for(fam)(warm[0]) == 1.0
+        # a budget of one evaluation: only the first candidate (the warm seed) is timed
+        res = at.tune("bfs", cost_for(fam), n_samples=0, warm=warm, max_evals=1)
+        assert res.best_ms == 1.0
+    again = at.TuneCache(str(tmp_path / "tune.json"))
+    assert len(again.warm_start(feats, "bfs", k=2)) >= 2
+
+
 @pytest.mark.gpu
 def test_tuned_schedules_reproduce_the_oracle():
     torch = pytest.importorskip("torch")

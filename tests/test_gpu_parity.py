@@ -128,6 +128,31 @@ def test_bfs_fused(g2, rmat14, grid, lb):
         assert st["launches"] == 1 and st["iterations"] == od.max() + 1
 
 
+def test_null_schedule_follows_the_degree_bound(g2, rmat14, grid):
+    """With no schedule, a bounded-degree graph (road grid, largest degree
+    <= 32) runs BFS, SSSP and BC as one fused kernel; a power-law graph runs
+    the direction-optimising rounds.  Results are the oracle's either way."""
+    w = gg.pair_weights(grid, 1000, seed=2)
+    dg = g2.load_graph(grid, w)
+    od, op = oracle.bfs_graph(grid, 3)
+    d, p = dev(grid.n), dev(grid.n)
+    g2.g2_bfs(dg, 3, d, p, None)
+    assert np.array_equal(host(d), od) and np.array_equal(host(p), op)
+    assert g2.g2_last_stats()["launches"] == 1
+    dist = dev(grid.n)
+    g2.g2_sssp_delta(dg, 3, 512, dist, None)
+    assert np.array_equal(host(dist), oracle.sssp_graph(grid, w, 3))
+    assert g2.g2_last_stats()["launches"] == 1
+    bc = dev(grid.n, torch.float64)
+    g2.g2_bc(dg, [3, 77], bc, None)
+    assert bc_close(host(bc), oracle.bc_graph(grid, [3, 77]))
+    dr = g2.load_graph(rmat14)
+    d = dev(rmat14.n)
+    g2.g2_bfs(dr, 0, d, None, None)
+    assert np.array_equal(host(d), oracle.bfs_graph(rmat14, 0)[0])
+    assert g2.g2_last_stats()["launches"] > 1
+
+
 def test_bfs_edge_cases(g2):
     for g in edge_cases():
         for src in sorted({0, g.n - 1, g.n // 2}):
