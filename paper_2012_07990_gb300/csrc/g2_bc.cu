@@ -319,7 +319,7 @@ static g2_status bc_one_fused(g2_graph *g, const BcState &s, const g2_schedule &
     a.off = off;
     a.cnt3 = ctrs + 20;
     a.levels = ctrs + 24;
-    a.bar = GridBarrier{reinterpret_cast<unsigned *>(ctrs + 28), reinterpret_cast<unsigned *>(ctrs + 29)};
+    a.bar = GridBarrier{reinterpret_cast<unsigned long long *>(ctrs + 28)};
     a.err = d_err;
     a.limit_ns = 2000000000ULL;
     k_bc_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(s, n, ctrs + 20);

@@ -238,7 +238,7 @@ g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     G2_TRY(ws(g, B_Q1, (size_t)std::max(n, 1), &a.q[1]));
     a.cnt = ctrs + 20;
     a.result = ctrs + 24;
-    a.bar = GridBarrier{reinterpret_cast<unsigned *>(ctrs + 28), reinterpret_cast<unsigned *>(ctrs + 29)};
+    a.bar = GridBarrier{reinterpret_cast<unsigned long long *>(ctrs + 28)};
     a.err = d_err;
     a.limit_ns = barrier_limit_ns();
     a.ctr = nullptr;
@@ -297,7 +297,7 @@ g2_status sssp_fused(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
     a.fcnt = ctrs + 23;
     a.dmin = ctrs + 25;
     a.result = ctrs + 30;
-    a.bar = GridBarrier{reinterpret_cast<unsigned *>(ctrs + 28), reinterpret_cast<unsigned *>(ctrs + 29)};
+    a.bar = GridBarrier{reinterpret_cast<unsigned long long *>(ctrs + 28)};
     a.err = d_err;
     a.limit_ns = barrier_limit_ns();
     a.ctr = nullptr;

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kCta) k_static_bfs(StaticBfsArgs a) {
     int32_t *cnt = a.s;
     int32_t *err = a.s + 12;
     int32_t *q[2] = {a.s + kHdr, a.s + kHdr + kStaticMaxN};
-    GridBarrier bar{reinterpret_cast<unsigned *>(a.s + 8), reinterpret_cast<unsigned *>(a.s + 9)};
+    GridBarrier bar{reinterpret_cast<unsigned long long *>(a.s + 8)};
     OpBFS op{a.depth, a.parent};
     OutCtx out;
     memset(&out, 0, sizeof(out));
