@@ -261,7 +261,11 @@ g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc,
 
 /* Multi-source BFS: k <= 64 sources (host int32[k]) in one traversal, one bit
  * per source in per-vertex 64-bit visit/frontier masks.  depth int32[k][n]
- * device (row i = BFS from srcs[i]). */
+ * device (row i = BFS from srcs[i]).  Schedules: PUSH with any frontier load
+ * balancing but EDGE_ONLY, PULL with VERTEX_BASED or WM, or kernel fusion with
+ * WM PUSH (the whole loop in one cooperative kernel).  NULL schedule: the
+ * direction-optimising hybrid (STRICT PUSH below 2% of n, VERTEX_BASED PULL);
+ * fused WM PUSH on a bounded-degree graph (largest out-degree <= 32). */
 g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
                        const g2_hybrid *sched, void *stream);
 

@@ -120,6 +120,66 @@ __global__ void __launch_bounds__(kCta) k_ms_pull(DevGraph g, P op, OutCtx out,
     lb_pull<P, G>(g, nullptr, g.n, all, op, out, blockIdx.x, gridDim.x, ctr);
 }
 
+// ------------------------------------------- multi-source BFS, fused
+// The whole multi-source loop in one cooperative kernel (kernel fusion for
+// the batch): per level a WM PUSH over the list of vertices whose frontier
+// mask is non-zero, a grid barrier, the commit of the newly reached bits
+// (visit masks, depths) together with clearing the spent frontier masks, and
+// a second barrier.  Counters rotate over three words so that a level's
+// count is read after the barrier that completed it and reset two levels
+// ahead.
+struct MsBfsFusedArgs {
+    DevGraph g;
+    u64 *visit;
+    u64 *F[2];
+    int32_t *list[2];
+    int32_t *cnt;     // [3] rotating list lengths; cnt[0] = seeded sources
+    int32_t *depth;   // [k][n]
+    int32_t *levels;  // out
+    GridBarrier bar;
+    int32_t *err;
+    uint64_t limit_ns;
+};
+
+__global__ void __launch_bounds__(kCta) k_ms_bfs_fused(MsBfsFusedArgs a) {
+    const int32_t n = a.g.n;
+    OutCtx out;
+    memset(&out, 0, sizeof(out));
+    out.mode = OUT_SPARSE;
+    out.dedup = DD_NONE;  // the first arc that turns a mask non-zero lists the vertex
+    out.cap = n;
+    out.err = a.err;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    int level = 1;
+    for (;; ++level) {
+        const int p = (level - 1) & 1, q = level & 1;
+        const int32_t size = ld_relaxed_i32(a.cnt + (level - 1) % 3);
+        if (size == 0) break;
+        FrontierIn fin{a.list[p], size, nullptr};
+        out.q = a.list[q];
+        out.cnt = a.cnt + level % 3;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt[(level + 1) % 3] = 0;
+        lb_warp(a.g, fin, size, OpMsBfs{a.visit, a.F[p], a.F[q]}, out, blockIdx.x, gridDim.x,
+                nullptr);
+        if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+        const int32_t nt_new = ld_relaxed_i32(a.cnt + level % 3);
+        for (int64_t i = tid; i < nt_new; i += nt) {
+            const int32_t v = a.list[q][i];
+            u64 nm = a.F[q][v];
+            a.visit[v] |= nm;
+            while (nm) {
+                const int b = __ffsll((long long)nm) - 1;
+                nm &= nm - 1;
+                a.depth[(int64_t)b * n + v] = level;
+            }
+        }
+        for (int64_t i = tid; i < size; i += nt) a.F[p][a.list[p][i]] = 0ull;
+        if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+    }
+    if (tid == 0) *a.levels = level - 1;
+}
+
 static g2_status batch_lb(const g2_schedule &s) {
     if (s.load_balance < G2_LB_VERTEX_BASED || s.load_balance > G2_LB_TWC)
         return fail(G2_EINVAL, "bad load_balance");
@@ -131,8 +191,50 @@ static g2_status batch_lb(const g2_schedule &s) {
     return G2_OK;
 }
 
+static g2_status bfs_batch_fused(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
+                                 const g2_schedule &sc, cudaStream_t st, int32_t *d_err) {
+    if (sc.direction != G2_PUSH || sc.load_balance != G2_LB_WM)
+        return fail(G2_EUNSUPPORTED, "the fused multi-source BFS runs WM PUSH rounds");
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    int32_t *ctrs = d_err - 62;
+    MsBfsFusedArgs a;
+    a.g = t->view();
+    int32_t *dsrc;
+    G2_TRY(ws(g, B_MS0, (size_t)std::max(n, 1), &a.visit));
+    G2_TRY(ws(g, B_MS1, (size_t)std::max(n, 1), &a.F[0]));
+    G2_TRY(ws(g, B_MS2, (size_t)std::max(n, 1), &a.F[1]));
+    G2_TRY(ws(g, B_Q0, (size_t)std::max(n, 1), &a.list[0]));
+    G2_TRY(ws(g, B_Q1, (size_t)std::max(n, 1), &a.list[1]));
+    G2_TRY(ws(g, B_I1, 64, &dsrc));
+    G2_CK(cudaMemsetAsync(a.visit, 0, (size_t)n * 8, st));
+    G2_CK(cudaMemsetAsync(a.F[0], 0, (size_t)n * 8, st));
+    G2_CK(cudaMemsetAsync(a.F[1], 0, (size_t)n * 8, st));
+    G2_CK(cudaMemsetAsync(depth, 0xFF, (size_t)k * n * 4, st));
+    G2_CK(cudaMemcpyAsync(dsrc, srcs, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    a.cnt = ctrs + 20;  // [20..22]; zero from begin_call
+    a.levels = ctrs + 24;
+    k_ms_seed<<<1, 64, 0, st>>>(dsrc, k, a.visit, a.F[0], depth, n, a.list[0], a.cnt);
+    a.depth = depth;
+    a.bar = GridBarrier{reinterpret_cast<unsigned long long *>(ctrs + 28)};
+    a.err = d_err;
+    a.limit_ns = barrier_limit_ns();
+    stats().launches += 1;
+    G2_TRY(launch_coop(g, k_ms_bfs_fused, a, st));
+    G2_TRY(read_counters(g, ctrs + 24, 1, st, d_err));
+    stats().iterations = g->h_ctr[0];
+    stats().push_rounds = g->h_ctr[0];
+    stats().barriers = 2 * g->h_ctr[0];
+    return G2_OK;
+}
+
 g2_status bfs_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
                         const g2_hybrid &h, cudaStream_t st, int32_t *d_err) {
+    if (h.s1.kernel_fusion) {
+        if (h.criteria != G2_CRITERIA_NONE && !h.s2.kernel_fusion)
+            return fail(G2_EUNSUPPORTED, "kernel fusion must be set on both hybrid schedules");
+        return bfs_batch_fused(g, srcs, k, depth, h.s1, st, d_err);
+    }
     Topology *t = g->topo;
     const int32_t n = t->n;
     int32_t *ctrs = d_err - 62;
@@ -409,7 +511,18 @@ using namespace g2;
 // Tuned schedules when the caller passes none: multi-source BFS switches from
 // STRICT PUSH to VERTEX_BASED PULL once the union frontier holds 2% of the
 // vertices; multi-source SSSP relaxes with STRICT PUSH.
-static g2_hybrid tuned_batch_bfs() {
+// Tuned multi-source BFS: the direction-optimising hybrid (STRICT PUSH below
+// 2% of n, VERTEX_BASED PULL); on a bounded-degree graph the fused WM PUSH
+// loop (thousands of small levels: launches and host round trips dominate).
+static g2_hybrid tuned_batch_bfs(g2_graph *g, cudaStream_t st) {
+    int32_t dmax = 0;
+    if (max_out_degree(g, st, &dmax) == G2_OK && dmax <= kBoundedDegree) {
+        g2_hybrid h = default_hybrid();
+        h.s1.load_balance = G2_LB_WM;
+        h.s1.kernel_fusion = 1;
+        h.s2 = h.s1;
+        return h;
+    }
     g2_hybrid h = default_hybrid();
     h.criteria = G2_INPUT_VERTEXSET_SIZE;
     h.threshold = 0.02f;
@@ -434,8 +547,7 @@ g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *dep
         if (srcs[i] < 0 || srcs[i] >= g->topo->n) return fail(G2_EINVAL, "source out of range");
     if ((int64_t)k * g->topo->n >= (int64_t)1 << 40) return fail(G2_EINVAL, "output too large");
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : tuned_batch_bfs();
-    if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "batched BFS runs unfused rounds");
+    g2_hybrid h = sched ? *sched : tuned_batch_bfs(g, st);
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));
     G2_TRY(bfs_batch_run(g, srcs, k, depth, h, st, d_err));

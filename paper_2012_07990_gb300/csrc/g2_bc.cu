@@ -68,6 +68,11 @@ struct BcState {
     double *bc;
     int32_t *lvl;  // all levels, in order
     int32_t src;
+    // level-pass granularity: one thread per vertex on a symmetric
+    // bounded-degree graph (every list short), else one warp per vertex and,
+    // when some vertex may have kBigDeg or more arcs (`big`), one CTA for those
+    int32_t per_thread;
+    int32_t big;
 };
 
 // sigma of vertex w at level d+1: sum over in-neighbours u at level d
@@ -99,6 +104,22 @@ __device__ __forceinline__ double bc_delta_part(const BcState &s, int32_t v, int
 template <bool SIGMA>
 __device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt, int32_t d,
                               int bid, int nb) {
+    if (s.per_thread) {  // uniform over the grid
+        const int64_t nt = (int64_t)nb * blockDim.x;
+        for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < cnt; i += nt) {
+            const int32_t v = list[i];
+            if (SIGMA) {
+                const BigF a = bc_sigma_part(s, v, d, s.g.crowptr[v], s.g.crowptr[v + 1], 1, 0);
+                s.sm[v] = a.m;
+                s.se[v] = a.e;
+            } else {
+                const double a = bc_delta_part(s, v, d, s.g.rowptr[v], s.g.rowptr[v + 1], 1, 0);
+                s.delta[v] = a;
+                if (v != s.src) s.bc[v] += a;
+            }
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gw = bid * kWarps + wid, nw = nb * kWarps;
     // warps: vertices with fewer than kBigDeg arcs
@@ -128,6 +149,7 @@ __device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt
     // CTAs: vertices with at least kBigDeg arcs
     __shared__ double s_m[kWarps];
     __shared__ int s_e[kWarps];
+    if (!s.big) return;  // uniform: no vertex has that many arcs
     for (int32_t i = bid; i < cnt; i += nb) {
         int32_t v = list[i];
         int32_t b = SIGMA ? s.g.crowptr[v] : s.g.rowptr[v];
@@ -355,6 +377,10 @@ g2_status bc_run(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const 
     BcState s;
     s.g = t->view();
     s.bc = bc;
+    int32_t dmax = 0;
+    G2_TRY(max_out_degree(g, st, &dmax));
+    s.per_thread = t->symmetric && dmax <= kBoundedDegree;
+    s.big = !(t->symmetric && dmax < kBigDeg);
     G2_TRY(ws(g, B_I0, (size_t)std::max(n, 1), &s.depth));
     G2_TRY(ws(g, B_LVL, (size_t)std::max(n, 1), &s.lvl));
     G2_TRY(ws(g, B_D0, (size_t)std::max(n, 1), &s.sm));

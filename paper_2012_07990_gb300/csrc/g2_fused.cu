@@ -16,16 +16,6 @@
 
 namespace g2 {
 
-static uint64_t barrier_limit_ns() {
-    static uint64_t lim = 0;
-    if (lim == 0) {
-        const char *e = getenv("G2_BARRIER_TIMEOUT_NS");
-        long long v = e ? atoll(e) : 0;
-        lim = v > 0 ? (uint64_t)v : 2000000000ULL;  // 2 s per wait
-    }
-    return lim;
-}
-
 template <int LB, class Op>
 __device__ __forceinline__ void run_lb(const DevGraph &g, const FrontierIn &fin, int32_t size,
                                        const Op &op, const OutCtx &out,
@@ -190,27 +180,6 @@ __global__ void k_fill_dist(int32_t *a, int32_t n) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
         a[v] = G2_INF32;
-}
-
-template <class K, class A>
-static g2_status launch_coop(g2_graph *g, K kernel, A &args, cudaStream_t st) {
-    int per_sm = 0;
-    G2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCta, 0));
-    if (per_sm < 1) return fail(G2_EUNSUPPORTED, "fused kernel does not fit on an SM");
-    // fewer resident CTAs make every grid barrier cheaper; the round's work
-    // is spread over the virtual CTAs either way.  One CTA per SM measured
-    // best on road grids (G2_FUSED_CTAS_PER_SM overrides for sweeps).
-    static int cap = -1;
-    if (cap < 0) {
-        const char *e = getenv("G2_FUSED_CTAS_PER_SM");
-        cap = e ? atoi(e) : 1;
-    }
-    if (cap > 0 && cap < per_sm) per_sm = cap;
-    int grid = per_sm * g->topo->sm_count;
-    void *params[] = {&args};
-    G2_CK(cudaLaunchCooperativeKernel((const void *)kernel, dim3(grid), dim3(kCta), params, 0, st));
-    stats().launches += 1;
-    return G2_OK;
 }
 
 static g2_status check_fused_lb(const g2_schedule &s) {

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cstdlib>
 #include <string>
 
 #include "g2.h"
@@ -185,6 +186,41 @@ g2_status max_out_degree(g2_graph *g, cudaStream_t st, int32_t *out);
 // their many small levels cost more in launches and host round trips than in
 // arcs.
 constexpr int32_t kBoundedDegree = 32;
+
+// Time limit of one grid-barrier wait in the fused kernels (2 s;
+// G2_BARRIER_TIMEOUT_NS overrides).
+inline uint64_t barrier_limit_ns() {
+    static uint64_t lim = 0;
+    if (lim == 0) {
+        const char *e = getenv("G2_BARRIER_TIMEOUT_NS");
+        long long v = e ? atoll(e) : 0;
+        lim = v > 0 ? (uint64_t)v : 2000000000ULL;
+    }
+    return lim;
+}
+
+// Cooperative launch of a fused kernel taking one argument struct: resident
+// CTAs only (co-residency is what makes its grid barriers safe).
+template <class K, class A>
+inline g2_status launch_coop(g2_graph *g, K kernel, A &args, cudaStream_t st) {
+    int per_sm = 0;
+    G2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCta, 0));
+    if (per_sm < 1) return fail(G2_EUNSUPPORTED, "fused kernel does not fit on an SM");
+    // fewer resident CTAs make every grid barrier cheaper; the round's work
+    // is spread over the virtual CTAs either way.  One CTA per SM measured
+    // best on road grids (G2_FUSED_CTAS_PER_SM overrides for sweeps).
+    static int cap = -1;
+    if (cap < 0) {
+        const char *e = getenv("G2_FUSED_CTAS_PER_SM");
+        cap = e ? atoi(e) : 1;
+    }
+    if (cap > 0 && cap < per_sm) per_sm = cap;
+    int grid = per_sm * g->topo->sm_count;
+    void *params[] = {&args};
+    G2_CK(cudaLaunchCooperativeKernel((const void *)kernel, dim3(grid), dim3(kCta), params, 0, st));
+    stats().launches += 1;
+    return G2_OK;
+}
 
 // Device-wide exclusive scan of int32 (out[0..count], out[count] = total).
 g2_status exclusive_scan_i32(g2_graph *g, const int32_t *in, int32_t *out, int32_t count,

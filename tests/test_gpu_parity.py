@@ -469,11 +469,29 @@ def test_bfs_batch(g2):
     want = np.stack([oracle.bfs_graph(g, s, want_parent=False)[0] for s in srcs])
     for s in (None, g2.schedule("ETWC"), g2.schedule("WM"),
               g2.hybrid(g2.schedule("CM"), g2.schedule("WM", direction=g2.G2_PULL), 0.05),
-              g2.schedule("VERTEX_BASED", direction=g2.G2_PULL)):
+              g2.schedule("VERTEX_BASED", direction=g2.G2_PULL),
+              g2.schedule("WM", kernel_fusion=True)):
         for k in (1, 17, 64):
             depth = dev(k * g.n)
             g2.g2_bfs_batch(dg, srcs[:k], depth, s)
             assert np.array_equal(host(depth).reshape(k, g.n), want[:k]), k
+
+
+def test_bfs_batch_fused_on_a_road_grid(g2, grid):
+    """Bounded-degree graph: the NULL schedule runs the fused multi-source
+    loop (one launch), with repeated sources and a ragged k."""
+    srcs = np.concatenate([gg.random_sources(grid, 40, seed=3), [7, 7, 0]]).astype(np.int32)
+    want = np.stack([oracle.bfs_graph(grid, s, want_parent=False)[0] for s in srcs])
+    dg = g2.load_graph(grid)
+    for s in (None, g2.schedule("WM", kernel_fusion=True)):
+        depth = dev(len(srcs) * grid.n)
+        g2.g2_bfs_batch(dg, srcs, depth, s)
+        assert np.array_equal(host(depth).reshape(len(srcs), grid.n), want)
+        st = g2.g2_last_stats()
+        assert st["iterations"] == want.max() + 1 and st["launches"] == 2
+    with pytest.raises(g2.G2Error) as e:
+        g2.g2_bfs_batch(dg, srcs[:4], dev(4 * grid.n), g2.schedule("CM", kernel_fusion=True))
+    assert e.value.status == g2.G2_EUNSUPPORTED
 
 
 def test_sssp_batch(g2):
