@@ -231,7 +231,10 @@ __global__ void __launch_bounds__(kCta) k_bc_fused(BcFusedArgs a) {
     out.dedup = DD_NONE;
     out.err = a.err;
     int32_t b = 0, e = 1, d = 0;
-    // forward: discovery, barrier, sigma of the new level, barrier
+    // forward, one barrier per level: the discovery of level d+1 from level
+    // d and the sigma of level d (pulled from level d-1) share a phase.  The
+    // discovery reads no sigma, and the sigma pass only looks for depth d-1,
+    // which no vertex discovered in the same phase (depth -1 -> d+1) has.
     for (;; ++d) {
         FrontierIn fin{s.lvl + b, e - b, nullptr};
         out.q = s.lvl + e;
@@ -242,12 +245,11 @@ __global__ void __launch_bounds__(kCta) k_bc_fused(BcFusedArgs a) {
         else if (LB == G2_LB_CM) lb_cta(s.g, fin, e - b, op, out, blockIdx.x, gridDim.x, nullptr);
         else if (LB == G2_LB_ETWC) lb_etwc(s.g, fin, e - b, op, out, blockIdx.x, gridDim.x, nullptr);
         else lb_vertex(s.g, fin, e - b, op, out, blockIdx.x, gridDim.x, nullptr);
+        if (d > 0) bc_level_pass<true>(s, s.lvl + b, e - b, d - 1, blockIdx.x, gridDim.x);
         if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
         const int32_t nn = ld_relaxed_i32(a.cnt3 + d % 3);
         if (nn == 0) break;
-        bc_level_pass<true>(s, s.lvl + e, nn, d, blockIdx.x, gridDim.x);
         if (blockIdx.x == 0 && threadIdx.x == 0) a.off[d + 2] = e + nn;
-        if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
         b = e;
         e += nn;
     }
@@ -366,7 +368,7 @@ static g2_status bc_one_fused(g2_graph *g, const BcState &s, const g2_schedule &
     stats().launches += 2;
     G2_TRY(read_counters(g, ctrs + 24, 1, st, d_err));
     stats().iterations += g->h_ctr[0];
-    stats().barriers += 3 * g->h_ctr[0];
+    stats().barriers += 2 * g->h_ctr[0];
     return G2_OK;
 }
 
