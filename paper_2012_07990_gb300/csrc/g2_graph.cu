@@ -1,14 +1,16 @@
-// g2_graph.cu — runtime of libg2: graph load (Sec. VI-C host side), device
-// validation, transpose, the workspace that lets every round reuse its
-// frontier buffers (Sec. VI-A), vertexset conversions, the device-wide scan,
-// EdgeBlocking preprocessing (Algorithm 1) and the public frontier API.
+// g2_graph.cu — runtime of libg2: graph load (Sec. VI-C host side) with
+// device validation (inside the upload kernel where the device can read the
+// caller's arrays), transpose, the stream-ordered device memory pool, the
+// workspace that lets every round reuse its frontier buffers (Sec. VI-A),
+// vertexset conversions, the device-wide scan, EdgeBlocking preprocessing
+// (Algorithm 1) and the public frontier API.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
-#include <mutex>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 

@@ -350,25 +350,10 @@ __global__ void __launch_bounds__(kCta) k_pr_fixup(PrArgs a, const int32_t *rows
 }
 
 
-// Out-degrees of the four vertices v0..v0+3; 16-byte loads for a full quad.
+// Out-degrees of the four vertices v0..v0+3 of a quad.
 struct PrQuad {
     int32_t od[4];
 };
-
-__device__ __forceinline__ void pr_load_quad(const int32_t *rowptr, int32_t n, int64_t v0,
-                                             PrQuad &q) {
-    if (v0 + 4 <= n) {
-        int4 r4 = __ldg(reinterpret_cast<const int4 *>(rowptr + v0));
-        int32_t r5 = __ldg(rowptr + v0 + 4);
-        q.od[0] = r4.y - r4.x;
-        q.od[1] = r4.z - r4.y;
-        q.od[2] = r4.w - r4.z;
-        q.od[3] = r5 - r4.w;
-    } else {
-        for (int k = 0; k < 4; ++k)
-            q.od[k] = v0 + k < n ? rowptr[v0 + k + 1] - rowptr[v0 + k] : 0;
-    }
-}
 
 // Shares of a quad into slots H + v0 .. H + v0 + 3 (one 16-byte store for a
 // full quad: H and v0 are multiples of 4), and the cached slots.
