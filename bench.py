@@ -286,14 +286,19 @@ def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
     label = torch.empty(n, dtype=torch.int32, device="cuda")
     rank_t = torch.empty(n, dtype=torch.float32, device="cuda")
 
+    side = torch.cuda.Stream()
+
     def step():
         dg = g2.g2_load_csr(n, np.frombuffer(h_rp.numpy().data, dtype=np.int32),
                             np.frombuffer(h_col.numpy().data, dtype=np.int32), None, True)
         g2.g2_bfs(dg, src, depth, None, sb)
         g2.g2_cc(dg, label, sc)
+        # g2 calls return after their work completes: the BFS and CC results
+        # go back to the host on a side stream while PageRank runs
+        with torch.cuda.stream(side):
+            h_depth.copy_(depth, non_blocking=True)
+            h_label.copy_(label, non_blocking=True)
         g2.g2_pagerank(dg, DAMPING, PR_ITERS, rank_t)
-        h_depth.copy_(depth, non_blocking=True)
-        h_label.copy_(label, non_blocking=True)
         h_rank.copy_(rank_t, non_blocking=True)
         torch.cuda.synchronize()
         dg.free()

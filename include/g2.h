@@ -270,7 +270,12 @@ g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *dep
                        const g2_hybrid *sched, void *stream);
 
 /* Multi-source SSSP: k <= 32 sources, stacked distance arrays dist
- * int32[k][n] device, relaxed together in one frontier loop. */
+ * int32[k][n] device, relaxed together in one frontier loop with the
+ * near/far queue of g2_sssp_delta (one bit per source in per-vertex masks).
+ * Schedules: PUSH with any frontier load balancing but EDGE_ONLY, or kernel
+ * fusion with WM PUSH (the whole loop in one cooperative kernel).  NULL
+ * schedule: STRICT PUSH; fused WM PUSH on a bounded-degree graph (largest
+ * out-degree <= 32). */
 g2_status g2_sssp_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t delta,
                         int32_t *dist, const g2_hybrid *sched, void *stream);
 

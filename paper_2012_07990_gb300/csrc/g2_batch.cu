@@ -394,6 +394,130 @@ __global__ void k_msr_far_split(const int32_t *flist, int32_t cnt, unsigned *far
     }
 }
 
+// ------------------------------------------ multi-source SSSP, fused
+// The near/far loop of the multi-source relaxation in one cooperative kernel.
+// Near round r pushes from list NL[r % 3] with masks M[r % 3] into
+// NL[(r + 1) % 3] / M[(r + 1) % 3] (and the far pile), while the masks of
+// round r - 1's input (M[(r + 2) % 3], listed in NL[(r + 2) % 3]) are
+// cleared: three rotating buffers make one grid barrier per round enough.
+// When a round produces nothing, the smallest far distance at or above the
+// threshold picks the next bucket and the far pile is split as in the plain
+// loop (two barriers per bucket).
+struct MsSsspFusedArgs {
+    DevGraph g;
+    int32_t *dist;  // [k][n]
+    unsigned *M[3];
+    unsigned *far;
+    int32_t *NL[3];
+    int32_t *FL[2];
+    int32_t *ncnt;    // [3]; ncnt[0] = seeded sources
+    int32_t *fcnt;    // [2]
+    int32_t *dmin;    // [2]; dmin[0] = G2_INF32 at launch
+    int32_t *result;  // [0] near rounds, [1] buckets
+    int32_t delta;    // 0: one bucket
+    GridBarrier bar;
+    int32_t *err;
+    uint64_t limit_ns;
+};
+
+__global__ void __launch_bounds__(kCta) k_msr_fused(MsSsspFusedArgs a) {
+    const int32_t n = a.g.n;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    const bool bucketed = a.delta > 0;
+    int64_t T = bucketed ? a.delta : (int64_t)G2_INF32;
+    int r = 0, fp = 0, epoch = 0;
+    int32_t prev_size = 0;
+    OutCtx out;
+    memset(&out, 0, sizeof(out));
+    out.mode = OUT_SPARSE;
+    out.dedup = DD_NONE;  // a vertex is listed when its mask turns non-zero
+    out.cap = n;
+    out.cap2 = n;
+    out.err = a.err;
+    for (;;) {
+        for (;;) {
+            const int ia = r % 3, ib = (r + 1) % 3, ic = (r + 2) % 3;
+            const int32_t size = ld_relaxed_i32(a.ncnt + ia);
+            if (size == 0) break;
+            out.q = a.NL[ib];
+            out.cnt = a.ncnt + ib;
+            out.q2 = a.FL[fp];
+            out.cnt2 = a.fcnt + fp;
+            if (tid == 0) a.ncnt[ic] = 0;  // round r + 1's output count
+            for (int64_t i = tid; i < prev_size; i += nt) a.M[ic][a.NL[ic][i]] = 0u;
+            FrontierIn fin{a.NL[ia], size, nullptr};
+            OpMsRelax op{a.dist, a.g.w, a.M[ia], a.M[ib], a.far, n,
+                         (int32_t)(T < G2_INF32 ? T : G2_INF32), a.err};
+            lb_warp(a.g, fin, size, op, out, blockIdx.x, gridDim.x, nullptr);
+            if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+            prev_size = size;
+            ++r;
+        }
+        const int32_t nfar = ld_relaxed_i32(a.fcnt + fp);
+        if (!bucketed || nfar == 0) break;
+        const int32_t Told = (int32_t)(T < G2_INF32 ? T : G2_INF32);
+        // phase A: the smallest live far distance
+        {
+            int32_t best = G2_INF32;
+            for (int64_t i = tid; i < nfar; i += nt) {
+                const int32_t v = a.FL[fp][i];
+                unsigned m = a.far[v];
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int32_t d = a.dist[(int64_t)b * n + v];
+                    if (d >= Told && d < best) best = d;
+                }
+            }
+            best = (int32_t)__reduce_min_sync(G2_FULL, (unsigned)best);
+            if ((threadIdx.x & 31) == 0 && best != G2_INF32) atomicMin(a.dmin + (epoch & 1), best);
+            if (tid == 0) {
+                a.fcnt[1 - fp] = 0;                 // the far pile of the next epoch
+                a.dmin[(epoch + 1) & 1] = G2_INF32;  // its minimum
+            }
+        }
+        if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+        const int32_t dmin = ld_relaxed_i32(a.dmin + (epoch & 1));
+        if (dmin == G2_INF32) break;
+        const int64_t Tnew = ((int64_t)dmin / a.delta + 1) * (int64_t)a.delta;
+        const int32_t Tn = (int32_t)(Tnew < G2_INF32 ? Tnew : G2_INF32);
+        // phase B: split the far pile into round r's near list and the next pile
+        {
+            const int ia = r % 3;
+            for (int64_t base = tid & ~31LL; base < nfar; base += nt) {
+                const int64_t i = base + (threadIdx.x & 31);
+                int32_t v = 0;
+                unsigned nb = 0, fb = 0;
+                if (i < nfar) {
+                    v = a.FL[fp][i];
+                    unsigned m = a.far[v];
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int32_t d = a.dist[(int64_t)b * n + v];
+                        if (d < Told) continue;  // settled in an earlier bucket
+                        if (d < Tn) nb |= 1u << b;
+                        else fb |= 1u << b;
+                    }
+                    a.far[v] = fb;
+                    if (nb) a.M[ia][v] = nb;
+                }
+                warp_append(a.NL[ia], a.ncnt + ia, n, a.err, v, nb != 0);
+                warp_append(a.FL[1 - fp], a.fcnt + 1 - fp, n, a.err, v, fb != 0);
+            }
+        }
+        if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+        fp = 1 - fp;
+        T = Tnew;
+        ++epoch;
+    }
+    if (tid == 0) {
+        a.result[0] = r;
+        a.result[1] = epoch;
+    }
+}
+
 __global__ void k_msr_seed(const int32_t *srcs, int32_t k, int32_t *dist, int32_t n, unsigned *m,
                            int32_t *list, int32_t *cnt) {
     int i = threadIdx.x;
@@ -416,8 +540,61 @@ __global__ void k_fill_i32_b(int32_t *a, int64_t n, int32_t val) {
         a[v] = val;
 }
 
+static g2_status sssp_batch_fused(g2_graph *g, const int32_t *srcs, int32_t k, int32_t delta,
+                                  int32_t *dist, const g2_schedule &sc, cudaStream_t st,
+                                  int32_t *d_err) {
+    if (sc.direction != G2_PUSH || sc.load_balance != G2_LB_WM)
+        return fail(G2_EUNSUPPORTED, "the fused multi-source SSSP runs WM PUSH rounds");
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    int32_t *ctrs = d_err - 62;
+    MsSsspFusedArgs a;
+    a.g = t->view();
+    a.dist = dist;
+    int32_t *dsrc;
+    int32_t *m2;
+    G2_TRY(ws(g, B_F0, (size_t)std::max(n, 1), &a.M[0]));
+    G2_TRY(ws(g, B_F1, (size_t)std::max(n, 1), &a.M[1]));
+    G2_TRY(ws(g, B_STAMP, (size_t)std::max(n, 1), &m2));
+    a.M[2] = reinterpret_cast<unsigned *>(m2);
+    G2_TRY(ws(g, B_F2, (size_t)std::max(n, 1), &a.far));
+    G2_TRY(ws(g, B_Q0, (size_t)std::max(n, 1), &a.NL[0]));
+    G2_TRY(ws(g, B_Q1, (size_t)std::max(n, 1), &a.NL[1]));
+    G2_TRY(ws(g, B_Q2, (size_t)std::max(n, 1), &a.NL[2]));
+    G2_TRY(ws(g, B_Q3, (size_t)std::max(n, 1), &a.FL[0]));
+    G2_TRY(ws(g, B_STAMP2, (size_t)std::max(n, 1), &a.FL[1]));
+    G2_TRY(ws(g, B_I1, 64, &dsrc));
+    for (int i = 0; i < 3; ++i) G2_CK(cudaMemsetAsync(a.M[i], 0, (size_t)n * 4, st));
+    G2_CK(cudaMemsetAsync(a.far, 0, (size_t)n * 4, st));
+    k_fill_i32_b<<<grid_for(g, (int64_t)k * n, kCta), kCta, 0, st>>>(dist, (int64_t)k * n, G2_INF32);
+    G2_CK(cudaMemcpyAsync(dsrc, srcs, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    a.ncnt = ctrs + 36;   // [36..38], zero from begin_call
+    a.fcnt = ctrs + 39;   // [39..40]
+    a.dmin = ctrs + 41;   // [41..42]
+    a.result = ctrs + 43; // [43..44]
+    const int32_t inf = G2_INF32;
+    G2_CK(cudaMemcpyAsync(a.dmin, &inf, 4, cudaMemcpyHostToDevice, st));
+    k_msr_seed<<<1, 32, 0, st>>>(dsrc, k, dist, n, a.M[0], a.NL[0], a.ncnt);
+    a.delta = delta;
+    a.bar = GridBarrier{reinterpret_cast<unsigned long long *>(ctrs + 28)};
+    a.err = d_err;
+    a.limit_ns = barrier_limit_ns();
+    stats().launches += 2;
+    G2_TRY(launch_coop(g, k_msr_fused, a, st));
+    G2_TRY(read_counters(g, ctrs + 43, 2, st, d_err));
+    stats().iterations = g->h_ctr[0];
+    stats().push_rounds = g->h_ctr[0];
+    stats().barriers = g->h_ctr[0] + 2 * g->h_ctr[1];
+    return G2_OK;
+}
+
 g2_status sssp_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t delta, int32_t *dist,
                          const g2_hybrid &h, cudaStream_t st, int32_t *d_err) {
+    if (h.s1.kernel_fusion) {
+        if (h.criteria != G2_CRITERIA_NONE && !h.s2.kernel_fusion)
+            return fail(G2_EUNSUPPORTED, "kernel fusion must be set on both hybrid schedules");
+        return sssp_batch_fused(g, srcs, k, delta, dist, h.s1, st, d_err);
+    }
     Topology *t = g->topo;
     const int32_t n = t->n;
     int32_t *ctrs = d_err - 62;
@@ -532,7 +709,17 @@ static g2_hybrid tuned_batch_bfs(g2_graph *g, cudaStream_t st) {
     return h;
 }
 
-static g2_hybrid tuned_batch_sssp() {
+// Tuned multi-source SSSP: STRICT PUSH; the fused WM PUSH loop on a
+// bounded-degree graph.
+static g2_hybrid tuned_batch_sssp(g2_graph *g, cudaStream_t st) {
+    int32_t dmax = 0;
+    if (max_out_degree(g, st, &dmax) == G2_OK && dmax <= kBoundedDegree) {
+        g2_hybrid h = default_hybrid();
+        h.s1.load_balance = G2_LB_WM;
+        h.s1.kernel_fusion = 1;
+        h.s2 = h.s1;
+        return h;
+    }
     g2_hybrid h = default_hybrid();
     h.s1.load_balance = G2_LB_STRICT;
     return h;
@@ -561,8 +748,7 @@ g2_status g2_sssp_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t del
     for (int32_t i = 0; i < k; ++i)
         if (srcs[i] < 0 || srcs[i] >= g->topo->n) return fail(G2_EINVAL, "source out of range");
     cudaStream_t st = as_stream(stream);
-    g2_hybrid h = sched ? *sched : tuned_batch_sssp();
-    if (h.s1.kernel_fusion) return fail(G2_EUNSUPPORTED, "batched SSSP runs unfused rounds");
+    g2_hybrid h = sched ? *sched : tuned_batch_sssp(g, st);
     if (delta <= 0 && h.s1.delta > 0) delta = h.s1.delta;
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));

@@ -501,11 +501,30 @@ def test_sssp_batch(g2):
     want = np.stack([oracle.sssp_graph(g, w, s) for s in srcs])
     dg = g2.load_graph(g, w)
     for delta in (0, 1, 40, 1000):
-        for lb in ("VERTEX_BASED", "WM", "CM", "ETWC"):
+        for sch in [g2.schedule(lb) for lb in ("VERTEX_BASED", "WM", "CM", "ETWC")] + \
+                   [g2.schedule("WM", kernel_fusion=True)]:
             for k in (1, 32):
                 dist = dev(k * g.n)
-                g2.g2_sssp_batch(dg, srcs[:k], delta, dist, g2.schedule(lb))
-                assert np.array_equal(host(dist).reshape(k, g.n), want[:k]), (delta, lb, k)
+                g2.g2_sssp_batch(dg, srcs[:k], delta, dist, sch)
+                assert np.array_equal(host(dist).reshape(k, g.n), want[:k]), (delta, k)
+
+
+def test_sssp_batch_fused_on_a_road_grid(g2, grid):
+    """Bounded-degree graph: the NULL schedule runs the fused multi-source
+    near/far loop (one launch after seeding) for every delta, with repeated
+    sources and a ragged k."""
+    w = gg.pair_weights(grid, 1000, seed=4)
+    srcs = np.concatenate([gg.random_sources(grid, 27, seed=4), [9, 9]]).astype(np.int32)
+    want = np.stack([oracle.sssp_graph(grid, w, s) for s in srcs])
+    dg = g2.load_graph(grid, w)
+    for delta in (0, 1, 300, 5000, 1 << 30):
+        dist = dev(len(srcs) * grid.n)
+        g2.g2_sssp_batch(dg, srcs, delta, dist, None)
+        assert np.array_equal(host(dist).reshape(len(srcs), grid.n), want), delta
+        assert g2.g2_last_stats()["launches"] == 3
+    with pytest.raises(g2.G2Error) as e:
+        g2.g2_sssp_batch(dg, srcs[:3], 64, dev(3 * grid.n), g2.schedule("ETWC", kernel_fusion=True))
+    assert e.value.status == g2.G2_EUNSUPPORTED
 
 
 # ------------------------------------------------------------- errors, views
