@@ -548,6 +548,7 @@ __global__ void k_max_degree(const int32_t *rowptr, int32_t n, int32_t *out) {
 
 g2_status max_out_degree(g2_graph *g, cudaStream_t st, int32_t *out) {
     Topology *t = g->topo;
+    std::lock_guard<std::recursive_mutex> lk(t->layout_mu);
     if (t->max_out_deg < 0) {
         int32_t *d;
         G2_TRY(ws(g, B_CTR, 64, &d));
@@ -563,6 +564,7 @@ g2_status max_out_degree(g2_graph *g, cudaStream_t st, int32_t *out) {
 
 g2_status ensure_coo(g2_graph *g, cudaStream_t st) {
     Topology *t = g->topo;
+    std::lock_guard<std::recursive_mutex> lk(t->layout_mu);
     if (t->coo_src || t->m == 0) return G2_OK;
     G2_CK(dmalloc(&t->coo_src, (size_t)t->m * sizeof(int32_t), st));
     k_coo_src<<<grid_for(g, (int64_t)t->n * 32, kCta), kCta, 0, st>>>(t->rowptr, t->n, t->coo_src);
@@ -580,6 +582,7 @@ int32_t default_block_size(const g2_graph *g, int bytes_per_vertex) {
 
 g2_status ensure_edge_block(g2_graph *g, int32_t N, cudaStream_t st) {
     Topology *t = g->topo;
+    std::lock_guard<std::recursive_mutex> lk(t->layout_mu);
     if (N <= 0) N = default_block_size(g, 4);
     if (t->eb_src && t->eb_N == N) return G2_OK;
     int32_t n = t->n, m = t->m;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 #include <cstdlib>
 #include <string>
 
@@ -84,6 +85,9 @@ namespace g2 {
 
 struct Topology {
     std::atomic<int> refs;
+    // serialises the lazy layout builders (views on several threads share
+    // the topology); recursive because one builder may call another
+    std::recursive_mutex layout_mu;
     int32_t n;
     int32_t m;
     bool symmetric;

@@ -725,6 +725,7 @@ static g2_status select_hot(g2_graph *g, int32_t hot, int32_t *perm, int32_t *mi
 static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, ShareMap *sm,
                                       const int32_t **ccol) {
     Topology *t = g->topo;
+    std::lock_guard<std::recursive_mutex> lk(t->layout_mu);
     if (t->pr_hot != hot || !t->pr_slot_of) {
         const int32_t n = t->n, m = t->m;
         dfree(t->pr_slot_of, st);
@@ -750,6 +751,7 @@ static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, Sha
 
 static g2_status ensure_seg_layout(g2_graph *g, cudaStream_t st) {
     Topology *t = g->topo;
+    std::lock_guard<std::recursive_mutex> lk(t->layout_mu);
     if (t->seg_head) return G2_OK;
     const int32_t n = t->n, m = t->m;
     const size_t words = ((size_t)m + 31) / 32 + 8;

@@ -557,6 +557,42 @@ def test_bounded_wait_times_out(g2):
     assert x == 45
 
 
+def test_views_on_threads_build_shared_layouts_once(g2, rmat14):
+    """Views on four threads, each with its own stream, all ask at once for
+    the lazily built layouts of one fresh topology (PageRank's renumbering
+    and segment flags, the degree statistic)."""
+    import threading
+    g = rmat14
+    ref = oracle.pagerank_graph(g, 0.85, 20)
+    od = oracle.bfs_graph(g, 0)[0]
+    base = g2.load_graph(g)
+    views = [base.view() for _ in range(4)]
+    errors, outs = [], {}
+
+    def work(i):
+        try:
+            with torch.cuda.stream(torch.cuda.Stream()):
+                r = torch.empty(g.n, dtype=torch.float32, device="cuda")
+                d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+                s = torch.cuda.current_stream().cuda_stream
+                g2.g2_pagerank(views[i], 0.85, 20, r, None, s)
+                g2.g2_bfs(views[i], 0, d, None, None, s)
+                torch.cuda.current_stream().synchronize()
+                outs[i] = (r.cpu().numpy().astype(np.float64), d.cpu().numpy())
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
+    for i in range(4):
+        assert np.abs(outs[i][0] - ref).sum() <= PR_L1
+        assert np.array_equal(outs[i][1], od)
+
+
 def test_views_and_device_pointer_load(g2, rmat14):
     g = rmat14
     rp = torch.from_numpy(g.rowptr).cuda()
