@@ -121,11 +121,22 @@ typedef struct g2_graph g2_graph;
  *   out      receives the handle (library-owned; free with g2_free_graph)
  * The input arrays are copied; the caller may free them after return.  The
  * layout is validated on the device (G2_EINVAL if rowptr is not monotone,
- * an id is out of range or a list is unsorted / has duplicates).  For a
- * non-symmetric graph the transpose (CSC, lists sorted ascending) is built on
- * the device for the PULL direction. */
+ * an id is out of range, a list is unsorted / has duplicates or a weight is
+ * negative).  Where the device can read the caller's arrays directly (device
+ * memory, pinned host memory, or pageable host memory on a system whose GPU
+ * reads it through the host page tables, as over the Grace-Blackwell
+ * coherent link) and col / w are 16-byte aligned, one kernel reads, checks
+ * and stores the arcs; otherwise they are copied with cudaMemcpyAsync and
+ * checked after.  For a non-symmetric graph the transpose (CSC, lists sorted
+ * ascending) is built on the host for the PULL direction.  Device memory
+ * comes from the library's stream-ordered pool (see g2_free_graph). */
 g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *col,
                       const int32_t *w, uint32_t flags, void *stream, g2_graph **out);
+/* g2_free_graph — release a handle (a graph or a view); the topology goes
+ * when its last handle does.  No call on the handle may be in progress.  The
+ * device memory returns to the library's per-device stream-ordered pool,
+ * which keeps it for later loads instead of handing it back to the driver
+ * (no cudaFree, no device-wide synchronisation).  NULL is ignored. */
 void g2_free_graph(g2_graph *g);
 
 /* g2_graph_view — a second handle on g's device topology with a workspace of
