@@ -598,8 +598,9 @@ def run_batched_workload(args):
 def run_serve_workload(args):
     """Serving: Poisson stream (BFS 60% / SSSP 30% / single-source BC 10%) over
     a resident pool (full: RMAT 16/18/20/22 + grids 512^2..4096^2; small: RMAT
-    16/18/20 + grids 512^2, 1024^2), continuous batching on 4 slots vs the same
-    trace served serially with one plain launch per query."""
+    16/18/20 + grids 512^2, 1024^2), continuous batching on 4 slots (queue
+    choice by response ratio with learned batch costs, and oldest-first) vs
+    the same trace served serially with one launch per query."""
     from paper_2012_07990_gb300 import build_native
     build_native.build()
     from paper_2012_07990_gb300 import g2
@@ -613,15 +614,18 @@ def run_serve_workload(args):
     load_s = time.time() - t
     trace = serve.make_trace(pool, rate=args.serve_rate, duration=args.serve_duration, seed=1)
     ex = serve.GpuExecutor(g2, pool, slots=4)
-    srv = serve.Server(ex, pool)
-    srv.run(trace[: min(64, len(trace))])  # warm views and workspaces
-    batched = srv.run(trace)
+    res = {}
+    for policy in ("hrrn", "fifo"):
+        srv = serve.Server(ex, pool, policy=policy)
+        srv.run(trace[: min(256, len(trace))])  # warm views, workspaces and the cost model
+        res[policy] = srv.run(trace).summary()
     ex1 = serve.GpuExecutor(g2, pool, slots=1)
-    serial = serve.Server(ex1, pool, max_batch=dict(bfs=1, sssp=1, bc=1)).run(trace)
+    serial = serve.Server(ex1, pool, max_batch=dict(bfs=1, sssp=1, bc=1), policy="fifo").run(trace)
     print(json.dumps({"workload": f"serve_{args.serve_pool}", "graphs": [s.name for s in specs],
                       "pool_load_s": round(load_s, 2), "rate_per_s": args.serve_rate,
                       "duration_s": args.serve_duration, "requests": len(trace),
-                      "continuous_batching_4_slots": batched.summary(),
+                      "continuous_batching_4_slots": res["hrrn"],
+                      "continuous_batching_4_slots_fifo": res["fifo"],
                       "serial_plain": serial.summary()}))
 
 

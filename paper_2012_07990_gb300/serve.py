@@ -194,10 +194,54 @@ class GpuExecutor:
         return {}
 
 
-class Server:
-    """Continuous-batching dispatcher over `executor.nslots` slots."""
+class CostModel:
+    """Execution seconds of a batch per (graph, kind): an exponentially
+    weighted average of the batches seen so far (None before the first)."""
 
-    def __init__(self, executor, pool, max_batch=None, mem_budget: int | None = None):
+    def __init__(self, alpha: float = 0.3):
+        self.alpha = alpha
+        self.est: dict = {}
+
+    def get(self, key):
+        return self.est.get(key)
+
+    def update(self, key, seconds: float):
+        old = self.est.get(key)
+        self.est[key] = seconds if old is None else (1 - self.alpha) * old + self.alpha * seconds
+
+
+def _pick_queue(policy, cost, pending, now):
+    """The (graph, kind) queue to dispatch next under `policy`."""
+    if policy == "fifo":
+        return min(pending, key=lambda kk: pending[kk][0].t_arrival)
+    best, best_r = None, -1.0
+    for kk, q in pending.items():
+        c = cost.get(kk)
+        if c is None:
+            return kk  # never measured: run it to learn its cost
+        wait = max(0.0, now - q[0].t_arrival)
+        r = (wait + c) / max(c, 1e-6)
+        if r > best_r:
+            best, best_r = kk, r
+    return best
+
+
+class Server:
+    """Continuous-batching dispatcher over `executor.nslots` slots.
+
+    policy "hrrn" (default): highest response ratio next -- among the
+    non-empty queues take the one maximising (wait + cost) / cost, where wait
+    is the age of its oldest request and cost the learned execution time of
+    a batch of it (a queue never run yet goes first, to be measured); short
+    batches overtake long ones, and a long one's ratio grows with its wait.
+    policy "fifo": the queue whose oldest request has waited longest."""
+
+    def __init__(self, executor, pool, max_batch=None, mem_budget: int | None = None,
+                 policy: str = "hrrn"):
+        if policy not in ("hrrn", "fifo"):
+            raise ValueError(f"unknown policy {policy}")
+        self.policy = policy
+        self.cost = CostModel()
         self.ex = executor
         self.pool = pool
         self.max_batch = dict(bfs=64, sssp=32, bc=1)
@@ -208,6 +252,9 @@ class Server:
             free, _ = torch.cuda.mem_get_info()
             mem_budget = free // 2
         self.mem_budget = int(mem_budget)
+
+    def _pick(self, pending, now):
+        return _pick_queue(self.policy, self.cost, pending, now)
 
     def run(self, trace: list[Request], clock=time.perf_counter) -> ServeStats:
         pending = {}  # (graph, kind) -> deque of requests that have arrived
@@ -223,6 +270,7 @@ class Server:
         t0 = clock()
 
         def worker(slot, batch, nbytes):
+            ts = clock()
             try:
                 res = self.ex.execute(slot, batch)
             except Exception as e:  # re-raised by the dispatcher
@@ -230,6 +278,7 @@ class Server:
                 res = {}
             t = clock() - t0
             with lock:
+                self.cost.update((batch[0].graph, batch[0].kind), clock() - ts)
                 for r in batch:
                     done_t[r.rid] = t
                 results.update(res)
@@ -251,7 +300,7 @@ class Server:
                     i += 1
                 launched = False
                 while free_slots and pending:
-                    key = min(pending, key=lambda kk: pending[kk][0].t_arrival)
+                    key = self._pick(pending, clock() - t0)
                     q = pending[key]
                     kind = key[1]
                     n = self.pool.graphs[key[0]].host.n

@@ -84,6 +84,49 @@ def test_batches_shrink_to_fit_the_budget():
     assert max(len(b) for b in ex.batches) <= 16
 
 
+def test_queue_choice_fifo_and_response_ratio():
+    R = serve.Request
+    pending = {("g", "bfs"): [R(0, 0.00, "g", "bfs", 0)],
+               ("h", "bc"): [R(1, 0.05, "h", "bc", 0)],
+               ("k", "sssp"): [R(2, 0.09, "k", "sssp", 0)]}
+    cost = serve.CostModel()
+    # a queue never measured goes first
+    assert serve._pick_queue("hrrn", cost, pending, 0.1) == ("g", "bfs")
+    cost.update(("g", "bfs"), 1.0)     # slow
+    cost.update(("h", "bc"), 0.001)    # fast
+    cost.update(("k", "sssp"), 0.001)  # fast, but younger
+    assert serve._pick_queue("fifo", cost, pending, 0.1) == ("g", "bfs")
+    assert serve._pick_queue("hrrn", cost, pending, 0.1) == ("h", "bc")
+    # the slow queue's ratio grows with its wait until it beats fresh short
+    # requests: (wait + 1) / 1 against (wait' + 0.001) / 0.001 with wait' small
+    pending[("h", "bc")] = [R(3, 9.9995, "h", "bc", 0)]
+    pending[("k", "sssp")] = [R(4, 9.9995, "k", "sssp", 0)]
+    assert serve._pick_queue("hrrn", cost, pending, 10.0) == ("g", "bfs")
+    cost.update(("h", "bc"), 0.003)
+    assert abs(cost.get(("h", "bc")) - (0.7 * 0.001 + 0.3 * 0.003)) < 1e-12
+    with pytest.raises(ValueError):
+        serve.Server(FakeExecutor(1), fake_pool(), mem_budget=1, policy="lifo")
+
+
+class CostlyExecutor(FakeExecutor):
+    """Graph 'a' batches take 40 ms, the others 2 ms."""
+
+    def execute(self, slot, batch):
+        time.sleep(0.040 if batch[0].graph == "a" else 0.002)
+        return {r.rid: r.src for r in batch}
+
+
+def test_response_ratio_cuts_median_latency_under_overload():
+    pool = fake_pool(names=("a", "b", "c", "d"))
+    tr = serve.make_trace(pool, rate=3000, duration=0.25, seed=7)
+    p50 = {}
+    for policy in ("fifo", "hrrn"):
+        st = serve.Server(CostlyExecutor(nslots=2), pool, mem_budget=1 << 40, policy=policy).run(tr)
+        assert st.latencies_ms.size == len(tr)
+        p50[policy] = st.p50
+    assert p50["hrrn"] < 0.8 * p50["fifo"], p50
+
+
 @pytest.mark.gpu
 def test_results_alone_equal_results_in_the_mix():
     torch = pytest.importorskip("torch")
