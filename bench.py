@@ -116,6 +116,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, ws: int) -> float:
+    """The largest `value` over the ranks (the slowest replica's time); the
+    reduction runs on the device under NCCL and on the host under gloo."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gteps(ws: int, edges_per_step: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: every replica traverses edges_per_step per step;
+    the job takes the slowest replica's time."""
+    return ws * edges_per_step * steps / (total_ms * 1e-3) / 1e9
+
+
 def make_graph(scale: int):
     from paper_2012_07990_gb300 import graphgen as gg
     return gg.rmat(scale, 16, 0.57, 0.19, 0.19, seed=1)
@@ -216,12 +235,9 @@ def run_ours(args):
     total_ms = e0.elapsed_time(e1)
     pv_ms_total, pv_launches = g2.g2_kernel_time("pr_vertex", reset=False)
     pr_ms_total, pr_launches = g2.g2_kernel_time("pr_round", reset=True)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws)
     ms_per_step = total_ms / args.steps
-    value = ws * edges_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    value = job_gteps(ws, edges_per_step, args.steps, total_ms)
 
     # roofline of the dominant kernel: the PageRank arc sweep k_pr_seg (PULL +
     # EDGE_ONLY), algorithmic bytes per launch = 4 m (CSC column ids) + 4 n
