@@ -565,6 +565,66 @@ def _lib_default_ms(g2, dg, G, algo):
     return _timed(fn, reps=1)
 
 
+def run_gather_workload(args):
+    """The floor under the PageRank arc sweep: plain gather passes over
+    RMAT-22's column ids (g2_diag_gather) in CSC order, in the sweep's
+    renumbered order (only the arcs whose share is not in the shared-memory
+    cache), in uniformly random order, and the column stream alone, next to
+    the sweep's own time per round."""
+    import torch
+    from paper_2012_07990_gb300 import build_native
+    build_native.build()
+    from paper_2012_07990_gb300 import g2
+    G = make_graph(args.scale)
+    n, m = G.n, G.m
+    H = 16384
+    deg = G.degrees()
+    order = np.lexsort((np.arange(n), -deg))  # degree descending, ties to the lower id
+    hot = np.zeros(n, bool)
+    hot[order[:H]] = True
+    slot = (H + np.arange(n)).astype(np.int64)
+    slot[hot] = np.cumsum(hot)[hot] - 1
+    ren = slot[G.col]
+    cold = ren[ren >= H]
+    rng = np.random.default_rng(1)
+    variants = {"csc_order": G.col, "renumbered_cold_arcs": cold.astype(np.int32),
+                "uniform_random": rng.integers(0, n, m, dtype=np.int32)}
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    grid = sm * 8  # 2,048 threads per SM, as the sweep
+    x = torch.rand(n + H, device="cuda")
+    out = torch.empty(grid * 256, device="cuda")
+    res = {}
+
+    def best_pass(d, xx, mode, reps=5):
+        return min(g2.g2_diag_gather(d, xx, mode, out, grid) for _ in range(reps + 1))
+
+    for name, idx in variants.items():
+        d = torch.from_numpy(np.ascontiguousarray(idx)).cuda()
+        ms = best_pass(d, x, 0)
+        res[name] = {"loads": int(d.numel()), "us": round(ms * 1e3, 1),
+                     "gloads_per_s": round(d.numel() / ms / 1e6, 1)}
+    d = torch.from_numpy(G.col).cuda()
+    ms = best_pass(d, None, 1)
+    res["column_stream_only"] = {"bytes": 4 * m, "us": round(ms * 1e3, 1),
+                                 "gb_per_s": round(4 * m / ms / 1e6, 1)}
+    dg = g2.load_graph(G)
+    rank = torch.empty(n, dtype=torch.float32, device="cuda")
+    g2.g2_pagerank(dg, DAMPING, 2, rank)
+    g2.g2_set_kernel_timing(True)
+    g2.g2_kernel_time("pr_round", reset=True)
+    g2.g2_pagerank(dg, DAMPING, PR_ITERS, rank)
+    torch.cuda.synchronize()
+    kt, kl = g2.g2_kernel_time("pr_round", reset=True)
+    g2.g2_set_kernel_timing(False)
+    sweep_us = kt / kl * 1e3
+    print(json.dumps({"workload": f"gather_floor_rmat{args.scale}", "n": n, "m": m, "grid": grid,
+                      "hot_slots": H, **res, "pr_sweep_us": round(sweep_us, 1),
+                      "sweep_over_csc_order_gather": round(sweep_us / res["csc_order"]["us"], 3),
+                      "sweep_over_cold_gather_plus_stream": round(
+                          sweep_us / (res["renumbered_cold_arcs"]["us"] +
+                                      res["column_stream_only"]["us"]), 3)}))
+
+
 def run_batched_workload(args):
     """RMAT scale 21 (ef 16, symmetric): 64-source BFS in one traversal vs 64
     single-source BFS calls (tuned and fixed TWC PUSH); 32-source SSSP (weights
@@ -675,7 +735,7 @@ def main():
     ap.add_argument("--serve-pool", choices=["full", "small"], default="full")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=1.0)
-    ap.add_argument("--workload", choices=["rmat22", "grid", "batched", "serve", "tune"],
+    ap.add_argument("--workload", choices=["rmat22", "grid", "batched", "serve", "tune", "gather"],
                     default="rmat22",
                     help="rmat22: the default step (the JSON line the driver reads); grid and "
                          "batched: the road-grid and multi-source configurations")
@@ -701,6 +761,9 @@ def main():
         return
     if args.workload == "tune":
         run_tune_workload(args)
+        return
+    if args.workload == "gather":
+        run_gather_workload(args)
         return
     if args.workload == "serve":
         run_serve_workload(args)

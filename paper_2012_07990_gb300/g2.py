@@ -92,6 +92,7 @@ _SIGS = {
     "g2_set_count_arcs": [I32],
     "g2_last_error": [],
     "g2_selftest_wait_timeout": [I64, P],
+    "g2_diag_gather": [P, I64, P, I32, I32, P, I32, ctypes.POINTER(F32), P],
     "g2_bfs_csr_static": [I32, I64, P, P, I32, P, P, P],
     "g2_set_kernel_timing": [I32],
     "g2_kernel_time": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I32],
@@ -341,6 +342,16 @@ def g2_kernel_time(name: str, reset: bool = False):
 def g2_selftest_wait_timeout(limit_ns: int, stream=None) -> int:
     """Returns the status code (G2_ETIMEOUT expected)."""
     return _lib.g2_selftest_wait_timeout(int(limit_ns), _stream(stream))
+
+
+def g2_diag_gather(idx, x, mode, out, grid, stream=None) -> float:
+    """Diagnostic gather pass (see include/g2.h); idx/x/out torch CUDA tensors.
+    Returns the gather pass's device time in milliseconds."""
+    n = 0 if x is None else int(x.numel())
+    ms = F32()
+    _check(_lib.g2_diag_gather(_ptr(idx), int(idx.numel()), _ptr(x), n, int(mode), _ptr(out),
+                               int(grid), ctypes.byref(ms), _stream(stream)), "g2_diag_gather")
+    return ms.value
 
 
 # ------------------------------------------------------------- schedules

@@ -677,3 +677,25 @@ def test_load_paths_and_memory_reuse(g2, rmat14):
         r = torch.empty(g.n, dtype=torch.float32, device="cuda")
         g2.g2_pagerank(dg, 0.85, 3, r)
         dg.free()
+
+
+def test_diag_gather_sums_and_rejects_bad_indices(g2):
+    """The diagnostic gather pass adds up x[idx[e]] exactly once per element
+    (mode 0) or the indices themselves (mode 1); indices outside [0, n) are
+    refused without being loaded."""
+    rng = np.random.default_rng(3)
+    n, m, grid = 5000, 123457, 7
+    idx = rng.integers(0, n, m, dtype=np.int32)
+    x = rng.random(n).astype(np.float32)
+    out = torch.empty(grid * 256, device="cuda")
+    di, dx = torch.from_numpy(idx).cuda(), torch.from_numpy(x).cuda()
+    ms = g2.g2_diag_gather(di, dx, 0, out, grid)
+    assert ms > 0
+    assert abs(host(out).astype(np.float64).sum() - x[idx].astype(np.float64).sum()) < 1e-2
+    g2.g2_diag_gather(di, None, 1, out, grid)
+    assert abs(host(out).astype(np.float64).sum() - idx.astype(np.float64).sum()) < 1e-4 * idx.sum()
+    bad = idx.copy()
+    bad[777] = n
+    with pytest.raises(g2.G2Error) as e:
+        g2.g2_diag_gather(torch.from_numpy(bad).cuda(), dx, 0, out, grid)
+    assert e.value.status == g2.G2_EINVAL
