@@ -305,8 +305,10 @@ def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
     side = torch.cuda.Stream()
 
     def step():
+        # PageRank's layouts are built in the background while BFS and CC run
         dg = g2.g2_load_csr(n, np.frombuffer(h_rp.numpy().data, dtype=np.int32),
-                            np.frombuffer(h_col.numpy().data, dtype=np.int32), None, True)
+                            np.frombuffer(h_col.numpy().data, dtype=np.int32), None, True,
+                            prepare_pagerank=True)
         g2.g2_bfs(dg, src, depth, None, sb)
         g2.g2_cc(dg, label, sc)
         # g2 calls return after their work completes: the BFS and CC results

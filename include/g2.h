@@ -51,6 +51,7 @@ typedef enum {
 /* ---------------------------------------------------------- load flags */
 #define G2_SYMMETRIC   0x1u  /* every arc u->v has v->u (then CSC aliases CSR) */
 #define G2_DEVICE_PTRS 0x2u  /* rowptr/col/w are device pointers (else host) */
+#define G2_PREPARE_PAGERANK 0x4u /* build PageRank's layouts in the background */
 
 /* --------------------------------------------- schedule (Table II fields) */
 /* configLoadBalance load_balance_type */
@@ -116,7 +117,7 @@ typedef struct g2_graph g2_graph;
  *   rowptr   int32[n+1], rowptr[0] = 0, non-decreasing, rowptr[n] = m
  *   col      int32[m] arc heads; each list sorted ascending, no duplicates
  *   w        int32[m] arc weights (>= 1 for SSSP) or NULL
- *   flags    G2_SYMMETRIC | G2_DEVICE_PTRS
+ *   flags    G2_SYMMETRIC | G2_DEVICE_PTRS | G2_PREPARE_PAGERANK
  *   stream   stream for the copies and validation
  *   out      receives the handle (library-owned; free with g2_free_graph)
  * The input arrays are copied; the caller may free them after return.  The
@@ -129,7 +130,12 @@ typedef struct g2_graph g2_graph;
  * and stores the arcs; otherwise they are copied with cudaMemcpyAsync and
  * checked after.  For a non-symmetric graph the transpose (CSC, lists sorted
  * ascending) is built on the host for the PULL direction.  Device memory
- * comes from the library's stream-ordered pool (see g2_free_graph). */
+ * comes from the library's stream-ordered pool (see g2_free_graph).
+ * G2_PREPARE_PAGERANK: the layouts the tuned PageRank sweep needs (the
+ * hot-vertex renumbering of the column ids, the segment flags) are built
+ * after the load returns, by a host thread on a stream of its own, while the
+ * caller's next calls run; g2_pagerank (and g2_free_graph) wait for them.
+ * Without the flag the first g2_pagerank builds them. */
 g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *col,
                       const int32_t *w, uint32_t flags, void *stream, g2_graph **out);
 /* g2_free_graph — release a handle (a graph or a view); the topology goes

@@ -68,7 +68,10 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             and os.path.getmtime(OUT) >= max(os.path.getmtime(o) for o in objs)):
         return OUT
     tmp = OUT + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]
+    # every symbol must resolve at link time (a missing definition is an error
+    # here, not at load time on the GPU machine)
+    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-Xlinker", "--no-undefined", "-o", tmp,
+           *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -693,6 +693,7 @@ g2_status vset_count(g2_graph *g, const VSet &v, int32_t *d_out, cudaStream_t st
 static void topo_release(Topology *t) {
     if (!t) return;
     if (--t->refs > 0) return;
+    pr_prepare_wait(t);  // a background preparation still running finishes first
     // every call on the topology has returned (calls synchronise their
     // stream before returning), so the blocks are idle: release them to the pool
     void *blocks[] = {t->rowptr, t->col, t->w, t->symmetric ? nullptr : t->crowptr,
@@ -757,6 +758,60 @@ static void host_transpose(int32_t n, int32_t m, const int32_t *rp, const int32_
         }
 }
 
+// A handle's own resources (workspace, counter block), not its topology.
+static void handle_release(g2_graph *g) {
+    // calls synchronise before returning, so the workspace is idle
+    for (int i = 0; i < B_COUNT; ++i) dfree(g->buf[i], nullptr);
+    if (g->h_ctr) {
+        std::lock_guard<std::mutex> lk(g_ctr_mu);
+        g_ctr_free.push_back(g->h_ctr);
+    }
+    delete g;
+}
+
+g2_status pr_prepare_start(g2_graph *g) {
+    Topology *t = g->topo;
+    std::lock_guard<std::mutex> lk(t->prep_mu);
+    if (t->prep.joinable()) return G2_OK;
+    g2_graph *h = new_handle(t);  // holds no reference: the topology joins it before it goes
+    if (finish_handle(h) != G2_OK) {
+        handle_release(h);
+        return G2_ENOMEM;
+    }
+    cudaStream_t s2 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        handle_release(h);
+        return cuda_fail(e, "stream for the background preparation");
+    }
+    t->prep_handle = h;
+    t->prep_stream = s2;
+    t->prep_status = G2_OK;
+    const int dev = t->device;
+    t->prep = std::thread([t, h, s2, dev]() {
+        cudaSetDevice(dev);
+        g2_status s = pr_build_layouts(h, s2);
+        if (s == G2_OK && cudaStreamSynchronize(s2) != cudaSuccess) s = G2_ECUDA;
+        if (s != G2_OK) t->prep_error = g2_last_error();
+        t->prep_status = s;
+    });
+    return G2_OK;
+}
+
+g2_status pr_prepare_wait(Topology *t) {
+    std::lock_guard<std::mutex> lk(t->prep_mu);
+    if (!t->prep.joinable()) return G2_OK;
+    t->prep.join();
+    handle_release(t->prep_handle);
+    t->prep_handle = nullptr;
+    cudaStreamDestroy(t->prep_stream);
+    t->prep_stream = nullptr;
+    const g2_status s = t->prep_status;
+    t->prep_status = G2_OK;
+    if (s != G2_OK) return fail(s, "background PageRank preparation: " + t->prep_error);
+    return G2_OK;
+}
+
 }  // namespace g2
 
 using namespace g2;
@@ -819,7 +874,8 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     if (n < 0 || n >= 2147483647 || m < 0 || m >= 2147483647LL)
         return fail(G2_EINVAL, "n or m out of range (must be < 2^31 - 1)");
     if (!rowptr || (m > 0 && !col)) return fail(G2_EINVAL, "null rowptr/col");
-    if (flags & ~(G2_SYMMETRIC | G2_DEVICE_PTRS)) return fail(G2_EINVAL, "unknown flags");
+    if (flags & ~(G2_SYMMETRIC | G2_DEVICE_PTRS | G2_PREPARE_PAGERANK))
+        return fail(G2_EINVAL, "unknown flags");
     cudaStream_t st = as_stream(stream);
     const bool dev = flags & G2_DEVICE_PTRS;
     const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -935,21 +991,21 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
         // the host vectors must outlive the copies
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(e, "CSC upload"));
     }
+    if (flags & G2_PREPARE_PAGERANK) {
+        const g2_status ps = pr_prepare_start(g);
+        if (ps != G2_OK) return bail(ps);
+    }
     *out = g;
     return G2_OK;
 }
 
 void g2_free_graph(g2_graph *g) {
     if (!g) return;
-    // calls synchronise before returning, so the workspace is idle
-    for (int i = 0; i < B_COUNT; ++i) dfree(g->buf[i], nullptr);
-    if (g->h_ctr) {
-        std::lock_guard<std::mutex> lk(g_ctr_mu);
-        g_ctr_free.push_back(g->h_ctr);
-    }
-    topo_release(g->topo);
-    delete g;
+    Topology *t = g->topo;
+    handle_release(g);
+    topo_release(t);
 }
+
 
 g2_status g2_graph_view(g2_graph *g, g2_graph **out) {
     if (!g || !out) return fail(G2_EINVAL, "null graph or output");

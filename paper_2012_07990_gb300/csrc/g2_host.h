@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <thread>
 #include <cstdlib>
 #include <string>
 
@@ -85,9 +86,21 @@ namespace g2 {
 
 struct Topology {
     std::atomic<int> refs;
-    // serialises the lazy layout builders (views on several threads share
-    // the topology); recursive because one builder may call another
+    // serialise the lazy layout builders (views on several threads share
+    // the topology); recursive because one builder may call another.
+    // PageRank's layouts have a lock of their own, so that building them in
+    // the background does not hold up the other builders.
     std::recursive_mutex layout_mu;
+    std::recursive_mutex pr_mu;
+    // background preparation of PageRank's layouts (G2_PREPARE_PAGERANK):
+    // a host thread driving a handle of its own (own workspace, no reference
+    // on the topology) on a non-blocking stream
+    std::mutex prep_mu;
+    std::thread prep;
+    g2_graph *prep_handle = nullptr;
+    cudaStream_t prep_stream = nullptr;
+    g2_status prep_status = G2_OK;
+    std::string prep_error;
     int32_t n;
     int32_t m;
     bool symmetric;
@@ -182,6 +195,13 @@ g2_status ensure_coo(g2_graph *g, cudaStream_t st);
 // EdgeBlocking layout for segment size N (Algorithm 1), built on the device.
 g2_status ensure_edge_block(g2_graph *g, int32_t N, cudaStream_t st);
 int32_t default_block_size(const g2_graph *g, int bytes_per_vertex);
+
+// PageRank layouts for handle h, built on stream st (defined with PageRank).
+g2_status pr_build_layouts(g2_graph *h, cudaStream_t st);
+// Start the background preparation for g's topology / wait for it (joins the
+// thread, releases its handle and stream; returns its status).
+g2_status pr_prepare_start(g2_graph *g);
+g2_status pr_prepare_wait(Topology *t);
 
 // Largest out-degree of the graph (computed on the device once, then kept).
 g2_status max_out_degree(g2_graph *g, cudaStream_t st, int32_t *out);

@@ -725,7 +725,7 @@ static g2_status select_hot(g2_graph *g, int32_t hot, int32_t *perm, int32_t *mi
 static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, ShareMap *sm,
                                       const int32_t **ccol) {
     Topology *t = g->topo;
-    std::lock_guard<std::recursive_mutex> lk(t->layout_mu);
+    std::lock_guard<std::recursive_mutex> lk(t->pr_mu);
     if (t->pr_hot != hot || !t->pr_slot_of) {
         const int32_t n = t->n, m = t->m;
         dfree(t->pr_slot_of, st);
@@ -751,7 +751,7 @@ static g2_status ensure_pr_hot_layout(g2_graph *g, int hot, cudaStream_t st, Sha
 
 static g2_status ensure_seg_layout(g2_graph *g, cudaStream_t st) {
     Topology *t = g->topo;
-    std::lock_guard<std::recursive_mutex> lk(t->layout_mu);
+    std::lock_guard<std::recursive_mutex> lk(t->pr_mu);
     if (t->seg_head) return G2_OK;
     const int32_t n = t->n, m = t->m;
     const size_t words = ((size_t)m + 31) / 32 + 8;
@@ -986,6 +986,23 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
 
 using namespace g2;
 
+namespace g2 {
+
+// The layouts of the tuned sweep for handle g (its workspace, stream st).
+g2_status pr_build_layouts(g2_graph *g, cudaStream_t st) {
+    g->st = st;
+    const PrCfg cfg = pr_config(g);
+    if (cfg.hot > 0) {
+        ShareMap sm{0, 0, nullptr};
+        const int32_t *ccol = nullptr;
+        G2_TRY(ensure_pr_hot_layout(g, cfg.hot, st, &sm, &ccol));
+    }
+    if (!cfg.merge) G2_TRY(ensure_seg_layout(g, st));
+    return G2_OK;
+}
+
+}  // namespace g2
+
 extern "C" g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, float *rank,
                                  const g2_hybrid *sched, void *stream) {
     if (!g || !rank) return fail(G2_EINVAL, "null graph or rank");
@@ -993,6 +1010,7 @@ extern "C" g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, floa
         return fail(G2_EINVAL, "iters must be >= 0 and damping in [0, 1]");
     cudaStream_t st = as_stream(stream);
     g2_hybrid h = sched ? *sched : default_hybrid();
+    G2_TRY(pr_prepare_wait(g->topo));  // layouts a G2_PREPARE_PAGERANK load started
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));
     G2_TRY(pagerank_run(g, damping, iters, rank, h, sched == nullptr, st, d_err));

@@ -699,3 +699,38 @@ def test_diag_gather_sums_and_rejects_bad_indices(g2):
     with pytest.raises(g2.G2Error) as e:
         g2.g2_diag_gather(torch.from_numpy(bad).cuda(), dx, 0, out, grid)
     assert e.value.status == g2.G2_EINVAL
+
+
+def test_background_pagerank_preparation(g2, rmat14):
+    """G2_PREPARE_PAGERANK: PageRank's layouts are built by a background thread
+    on its own stream while BFS and CC run on the caller's; PageRank waits for
+    them; a graph freed while the preparation still runs waits for it too."""
+    g = rmat14
+    ref = oracle.pagerank_graph(g, 0.85, 20)
+    od = oracle.bfs_graph(g, 0)[0]
+    ol = oracle.cc_graph(g)
+    for _ in range(3):
+        dg = g2.g2_load_csr(g.n, g.rowptr, g.col, None, True, prepare_pagerank=True)
+        d, lab = dev(g.n), dev(g.n)
+        g2.g2_bfs(dg, 0, d, None, None)
+        g2.g2_cc(dg, lab, None)
+        r = dev(g.n, torch.float32)
+        g2.g2_pagerank(dg, 0.85, 20, r)
+        assert np.array_equal(host(d), od) and np.array_equal(host(lab), ol)
+        assert np.abs(host(r).astype(np.float64) - ref).sum() <= PR_L1
+        dg.free()
+    # freed at once: the free joins the preparation
+    for _ in range(3):
+        g2.g2_load_csr(g.n, g.rowptr, g.col, None, True, prepare_pagerank=True).free()
+    # a directed graph (CSC built at load) and an empty one
+    gd = gg.gnp(2000, 0.003, 5, symmetric=False)
+    dg = g2.g2_load_csr(gd.n, gd.rowptr, gd.col, None, False, prepare_pagerank=True)
+    r = dev(gd.n, torch.float32)
+    g2.g2_pagerank(dg, 0.85, 20, r)
+    assert np.abs(host(r).astype(np.float64) - oracle.pagerank_graph(gd, 0.85, 20)).sum() <= PR_L1
+    g0 = gg.from_arcs(5, [], [])
+    dg = g2.g2_load_csr(g0.n, g0.rowptr, g0.col, None, True, prepare_pagerank=True)
+    r = dev(5, torch.float32)
+    g2.g2_pagerank(dg, 0.85, 3, r)
+    assert np.allclose(host(r), 0.2)
+
