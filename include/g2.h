@@ -228,7 +228,11 @@ g2_status g2_edgeset_apply(g2_graph *g, g2_op op, g2_frontier *in, void *vdata, 
 /* BFS (Fig. 2): depth int32[n] device (-1 unreachable), parent int32[n]
  * device or NULL (parent[src] = src, else the smallest-id in-neighbour one
  * level up, -1 unreachable).  Loop until the frontier is empty.  With kernel
- * fusion the whole loop is one persistent cooperative kernel.  NULL schedule:
+ * fusion the whole loop is one persistent cooperative kernel; fused WM runs
+ * the levels of up to 1024 vertices per cluster CTA (16384 with 16-CTA
+ * clusters) inside one thread-block cluster and hands larger levels to the
+ * grid-wide kernel (back below half that size), one launch per hand-over.
+ * NULL schedule:
  * direction-optimising hybrid, STRICT PUSH below 2% of n, VERTEX_BASED PULL
  * over a bitmap otherwise; on a bounded-degree graph (largest out-degree
  * <= 32: road networks, meshes) fused WM PUSH instead. */
@@ -326,7 +330,7 @@ typedef struct {
     int32_t pull_rounds;    /* rounds run PULL */
     int32_t launches;       /* kernels launched */
     int64_t arcs_examined;  /* arcs read by the traversal (0 unless counted) */
-    int32_t barriers;       /* grid barriers passed in fused kernels */
+    int32_t barriers;       /* grid or cluster barriers passed in fused kernels */
     int32_t reserved;
 } g2_stats;
 g2_status g2_last_stats(g2_stats *out);

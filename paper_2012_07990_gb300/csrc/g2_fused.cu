@@ -31,17 +31,22 @@ struct FusedBfsArgs {
     int32_t *depth;
     int32_t *parent;
     int32_t *q[2];
-    int32_t *cnt;      // [3] rotating list lengths; cnt[0] = 1 at launch
-    int32_t *result;   // [0] rounds
+    int32_t *cnt;      // [3] rotating list lengths; cnt[d0 % 3] > 0 at launch
+    int32_t d0;        // first round (its frontier is list d0 & 1)
+    int32_t lo;        // after the first round, stop before a level with fewer vertices
+    int32_t *result;   // [0] level reached, [1] 1 if stopped for the cluster loop
     GridBarrier bar;
     int32_t *err;
     uint64_t limit_ns;
     unsigned long long *ctr;
 };
 
-// One launch for the whole BFS.  Round d reads list d&1 (length cnt[d%3]) and
-// appends to list (d+1)&1 (length cnt[(d+1)%3]); cnt[(d+2)%3], read in round
-// d-1 only, is cleared for round d+1.  One barrier per round.
+// One launch for the BFS rounds from d0 on.  Round d reads list d&1 (length
+// cnt[d%3]) and appends to list (d+1)&1 (length cnt[(d+1)%3]); cnt[(d+2)%3],
+// read in round d-1 only, is cleared for round d+1.  One barrier per round.
+// Every CTA reads the same length after the barrier, so all stop together:
+// at an empty level (the search is done) or, after the first round, at a
+// level smaller than `lo` (the one-cluster loop takes it over).
 template <int LB>
 __global__ void __launch_bounds__(kCta) k_bfs_fused(FusedBfsArgs a) {
     OpBFS op{a.depth, a.parent};
@@ -51,10 +56,15 @@ __global__ void __launch_bounds__(kCta) k_bfs_fused(FusedBfsArgs a) {
     out.dedup = DD_NONE;  // the compare-and-swap on depth admits each vertex once
     out.cap = a.g.n;
     out.err = a.err;
-    int d = 0;
+    int d = a.d0;
+    int handover = 0;
     for (;; ++d) {
         int32_t size = ld_relaxed_i32(a.cnt + d % 3);
         if (size == 0) break;
+        if (size < a.lo && d > a.d0) {
+            handover = 1;
+            break;
+        }
         FrontierIn fin{a.q[d & 1], size, nullptr};
         out.q = a.q[(d + 1) & 1];
         out.cnt = a.cnt + (d + 1) % 3;
@@ -62,7 +72,10 @@ __global__ void __launch_bounds__(kCta) k_bfs_fused(FusedBfsArgs a) {
         run_lb<LB>(a.g, fin, size, op, out, a.ctr);
         if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.result[0] = d;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.result[0] = d;
+        a.result[1] = handover;
+    }
 }
 
 struct FusedSsspArgs {
@@ -182,6 +195,289 @@ __global__ void k_fill_dist(int32_t *a, int32_t n) {
         a[v] = G2_INF32;
 }
 
+// ---------------------------------------------------- BFS in one cluster
+// Fused BFS rounds while the frontier is small (bounded degree, high
+// diameter): the loop runs inside one thread-block cluster of CL CTAs, so a
+// level boundary is the cluster's hardware barrier instead of a grid barrier
+// over global counters.  Each CTA appends the vertices it discovers to a
+// queue in its own shared memory; after the barrier every CTA reads the CL
+// queue lengths through distributed shared memory and takes an equal slice of
+// their concatenation, reading the vertices from the owners' shared memory.
+// Within a CTA a warp takes 32 frontier vertices and spreads their arcs over
+// its lanes (a warp-wide scan of the degrees and a shuffle search for each
+// arc's source), four arcs per lane in flight, so a level costs one chain of
+// dependent accesses: queue entry, row offsets, column ids, compare-and-swap.
+// Every CTA reads the same lengths and takes the same decisions, so all
+// threads pass the same sequence of cluster barriers.
+//
+// The loop and the grid-wide loop (k_bfs_fused) hand the search to each other
+// at a level boundary: the cluster stops when a level holds more than `hi`
+// vertices (its frontier is copied to the global list of that level), the
+// grid loop stops when a level holds fewer than `lo`.  Each launch runs at
+// least one level.  A level that outgrows a CTA's queue (appends past the
+// capacity are counted, not stored) also stops the cluster; its vertices are
+// all labelled, so the host rebuilds that frontier from the depths.
+constexpr int kClCta = 1024;      // threads per CTA
+constexpr int kClQcap = 28672;    // queue entries per CTA and buffer (2 buffers: 224 KiB)
+constexpr int kClArcs = 4;        // arcs per lane in flight
+
+enum { CL_DONE = 0, CL_TO_GRID = 1, CL_OVERFLOW = 2 };
+
+struct ClusterBfsArgs {
+    DevGraph g;
+    int32_t *depth;
+    int32_t *parent;  // may be null
+    int32_t *q[2];    // global lists: level d's frontier is q[d & 1] ...
+    int32_t *cnt;     // ... with length cnt[d % 3]
+    int32_t d0;       // first level (its frontier is in the global list)
+    int32_t hi;       // stop before a level with more vertices
+    int32_t *result;  // out: [0] level reached, [1] CL_DONE / CL_TO_GRID / CL_OVERFLOW
+    unsigned long long *ctr;  // arcs examined, or null
+};
+
+__device__ __forceinline__ void cl_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+                 ::: "memory");
+}
+
+// The value at `local` (a shared-memory address of this CTA) in the shared
+// memory of cluster CTA `rank`.
+__device__ __forceinline__ int32_t cl_read(const int32_t *local, uint32_t rank) {
+    uint32_t ra;
+    int32_t v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(ra)
+                 : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+template <int CL>
+__global__ void __launch_bounds__(kClCta, 1) k_bfs_cluster(ClusterBfsArgs a) {
+    extern __shared__ int32_t s_q[];    // [2][kClQcap]
+    __shared__ int32_t s_cnt[2];        // entries appended to queue buffer 0 / 1
+    __shared__ int32_t s_off[CL + 1];   // prefix of the cluster's queue lengths
+    __shared__ int32_t s_over;
+    uint32_t rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t *__restrict__ rowptr = a.g.rowptr;
+    const int32_t *__restrict__ col = a.g.col;
+    if (threadIdx.x == 0) {
+        s_cnt[0] = 0;
+        s_cnt[1] = 0;
+    }
+    const int32_t *qg = (a.d0 & 1) ? a.q[1] : a.q[0];
+    int32_t total = ld_relaxed_i32(a.cnt + a.d0 % 3);
+    int reason = CL_DONE;
+    unsigned long long arcs = 0;
+    cl_barrier();
+    int d = a.d0;
+    for (;; ++d) {
+        const int cb = d & 1, nb = cb ^ 1;
+        const bool first = d == a.d0;
+        if (!first) {
+            if (warp == 0) {
+                int32_t c = lane < CL ? cl_read(&s_cnt[cb], lane) : 0;
+                const bool over = __any_sync(G2_FULL, c > kClQcap);
+#pragma unroll
+                for (int o = 1; o < CL; o <<= 1) {
+                    const int32_t t = __shfl_up_sync(G2_FULL, c, o);
+                    if (lane >= o) c += t;
+                }
+                if (lane < CL) s_off[lane + 1] = c;
+                if (lane == 0) {
+                    s_off[0] = 0;
+                    s_over = over;
+                    s_cnt[nb] = 0;
+                }
+            }
+            __syncthreads();
+            total = s_off[CL];
+            if (total == 0) break;
+            if (s_over) {
+                reason = CL_OVERFLOW;
+                break;
+            }
+            if (total > a.hi) {
+                // hand the level to the grid loop: this CTA's part of the list
+                int32_t *dst = (cb ? a.q[1] : a.q[0]) + s_off[rank];
+                const int32_t mine = s_off[rank + 1] - s_off[rank];
+                for (int32_t j = threadIdx.x; j < mine; j += kClCta) dst[j] = s_q[cb * kClQcap + j];
+                reason = CL_TO_GRID;
+                break;
+            }
+        }
+        const int32_t *cur = s_q + cb * kClQcap;
+        int32_t *nxt = s_q + nb * kClQcap;
+        const int32_t lo = (int32_t)((int64_t)total * rank / CL);
+        const int32_t hi = (int32_t)((int64_t)total * (rank + 1) / CL);
+        for (int32_t base = lo + warp * 32; base < hi; base += kClCta) {
+            const int32_t i = base + lane;
+            int32_t u = 0, beg = 0, deg = 0;
+            if (i < hi) {
+                if (first) {
+                    u = qg[i];
+                } else {
+                    int r = 0;
+#pragma unroll
+                    for (int j = 1; j < CL; ++j) r += i >= s_off[j];
+                    u = cl_read(cur + (i - s_off[r]), (uint32_t)r);
+                }
+                beg = __ldg(rowptr + u);
+                deg = __ldg(rowptr + u + 1) - beg;
+            }
+            int32_t incl = deg;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t t = __shfl_up_sync(G2_FULL, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int32_t tot = __shfl_sync(G2_FULL, incl, 31);
+            const int32_t excl = incl - deg;
+            arcs += (unsigned)tot;
+            for (int32_t k0 = 0; k0 < tot; k0 += 32 * kClArcs) {
+                int32_t v[kClArcs], ou[kClArcs], dv[kClArcs];
+#pragma unroll
+                for (int j = 0; j < kClArcs; ++j) {
+                    const int32_t k = k0 + 32 * j + lane;
+                    // arc k belongs to the last lane whose first arc is <= k
+                    int own = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int32_t ex = __shfl_sync(G2_FULL, excl, own + step);
+                        if (ex <= k) own += step;
+                    }
+                    ou[j] = __shfl_sync(G2_FULL, u, own);
+                    const int32_t ob = __shfl_sync(G2_FULL, beg, own);
+                    const int32_t oe = __shfl_sync(G2_FULL, excl, own);
+                    v[j] = k < tot ? __ldg(col + ob + (k - oe)) : -1;
+                }
+#pragma unroll
+                for (int j = 0; j < kClArcs; ++j)
+                    dv[j] = v[j] >= 0 ? atomicCAS(a.depth + v[j], -1, d + 1) : 0;
+#pragma unroll
+                for (int j = 0; j < kClArcs; ++j) {
+                    const bool disc = v[j] >= 0 && dv[j] == -1;
+                    // the smallest source among this level's arcs into v
+                    if (a.parent && v[j] >= 0 && (disc || dv[j] == d + 1))
+                        atomicMin(reinterpret_cast<unsigned *>(a.parent + v[j]), (unsigned)ou[j]);
+                    const unsigned mask = __ballot_sync(G2_FULL, disc);
+                    if (mask) {
+                        const int leader = __ffs(mask) - 1;
+                        int32_t pos = 0;
+                        if (lane == leader) pos = atomicAdd(&s_cnt[nb], __popc(mask));
+                        pos = __shfl_sync(G2_FULL, pos, leader) + __popc(mask & lanemask_lt());
+                        if (disc && pos < kClQcap) nxt[pos] = v[j];
+                    }
+                }
+            }
+        }
+        cl_barrier();  // level d complete: queues nb filled, queues cb no longer read
+    }
+    cl_barrier();  // no CTA leaves while a peer may still read its queue lengths
+    if (a.ctr && lane == 0 && arcs) atomicAdd(a.ctr, arcs);
+    if (threadIdx.x == 0 && rank == 0) {
+        a.result[0] = d;
+        a.result[1] = reason;
+        if (reason == CL_TO_GRID) {
+            a.cnt[d % 3] = total;
+            a.cnt[(d + 1) % 3] = 0;
+        } else if (reason == CL_OVERFLOW) {
+            a.cnt[d % 3] = 0;  // rebuilt from the depths
+            a.cnt[(d + 1) % 3] = 0;
+        }
+    }
+}
+
+// The vertices at depth `lvl`, appended to q (the frontier of a level the
+// cluster loop could not hold).
+__global__ void k_level_list(const int32_t *depth, int32_t n, int32_t lvl, int32_t *q,
+                             int32_t *cnt, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + lane;
+        const bool p = v < n && depth[v] == lvl;
+        warp_append(q, cnt, n, err, (int32_t)v, p);
+    }
+}
+
+// Cluster size for the loop on the current device: 16 CTAs where a cluster
+// that large fits, else 8; 0 when none fits or G2_FUSED_CLUSTER=0 (read on
+// every call; G2_FUSED_CLUSTER=8 or 16 asks for that size).
+template <int CL>
+static bool cluster_fits() {
+    const size_t smem = 2 * (size_t)kClQcap * 4;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(kClCta);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    bool ok = cudaFuncSetAttribute(k_bfs_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem) == cudaSuccess;
+    if (ok && CL > 8)
+        ok = cudaFuncSetAttribute(k_bfs_cluster<CL>,
+                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    ok = ok && cudaOccupancyMaxActiveClusters(&clusters, k_bfs_cluster<CL>, &cfg) == cudaSuccess &&
+         clusters >= 1;
+    cudaGetLastError();
+    return ok;
+}
+
+static int cluster_size() {
+    const char *e = getenv("G2_FUSED_CLUSTER");
+    const int want = e ? atoi(e) : -1;
+    if (want == 0) return 0;
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static int fits[kMaxDev][2];  // per device: 16 / 8 CTAs; 0 unknown, 1 fits, 2 does not
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (fits[dev][0] == 0) fits[dev][0] = cluster_fits<16>() ? 1 : 2;
+    if (fits[dev][1] == 0) fits[dev][1] = cluster_fits<8>() ? 1 : 2;
+    if (want != 8 && fits[dev][0] == 1) return 16;
+    if (want != 16 && fits[dev][1] == 1) return 8;
+    return 0;
+}
+
+// Level-size thresholds of the hand-over (G2_CLUSTER_HI / G2_CLUSTER_LO
+// override them for sweeps).
+static int32_t env_i32(const char *name, int32_t dflt) {
+    const char *e = getenv(name);
+    return e ? (int32_t)atoi(e) : dflt;
+}
+
+template <int CL>
+static g2_status launch_cluster(const ClusterBfsArgs &a, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(kClCta);
+    cfg.dynamicSmemBytes = 2 * (size_t)kClQcap * 4;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    G2_CK(cudaLaunchKernelEx(&cfg, k_bfs_cluster<CL>, a));
+    stats().launches += 1;
+    return G2_OK;
+}
+
 static g2_status check_fused_lb(const g2_schedule &s) {
     if (s.direction != G2_PUSH)
         return fail(G2_EUNSUPPORTED, "fused loops run PUSH rounds");
@@ -206,6 +502,7 @@ g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     G2_TRY(ws(g, B_Q0, (size_t)std::max(n, 1), &a.q[0]));
     G2_TRY(ws(g, B_Q1, (size_t)std::max(n, 1), &a.q[1]));
     a.cnt = ctrs + 20;
+    a.d0 = 0;
     a.result = ctrs + 24;
     a.bar = GridBarrier{reinterpret_cast<unsigned long long *>(ctrs + 28)};
     a.err = d_err;
@@ -220,16 +517,60 @@ g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     if (parent) G2_CK(cudaMemcpyAsync(parent + src, &src, 4, cudaMemcpyHostToDevice, st));
     G2_CK(cudaMemcpyAsync(a.q[0], &src, 4, cudaMemcpyHostToDevice, st));
     G2_CK(cudaMemcpyAsync(a.cnt, &one, 4, cudaMemcpyHostToDevice, st));
-    switch (s.load_balance) {
-        case G2_LB_WM: G2_TRY(launch_coop(g, k_bfs_fused<G2_LB_WM>, a, st)); break;
-        case G2_LB_CM: G2_TRY(launch_coop(g, k_bfs_fused<G2_LB_CM>, a, st)); break;
-        case G2_LB_ETWC: G2_TRY(launch_coop(g, k_bfs_fused<G2_LB_ETWC>, a, st)); break;
-        default: G2_TRY(launch_coop(g, k_bfs_fused<G2_LB_VERTEX_BASED>, a, st)); break;
+    // WM rounds start in one cluster and move between it and the grid-wide
+    // loop as the levels grow and shrink; the other strategies (and a device
+    // without room for the cluster) run the grid-wide loop throughout.
+    const int cl = s.load_balance == G2_LB_WM ? cluster_size() : 0;
+    // measured on road grids 1024^2..4096^2 with 16-CTA clusters: hand a
+    // level to the grid above 16384 vertices, take it back below 8192
+    a.lo = cl ? env_i32("G2_CLUSTER_LO", 512 * cl) : 0;
+    ClusterBfsArgs c;
+    c.g = a.g;
+    c.depth = depth;
+    c.parent = parent;
+    c.q[0] = a.q[0];
+    c.q[1] = a.q[1];
+    c.cnt = a.cnt;
+    c.hi = env_i32("G2_CLUSTER_HI", 1024 * cl);
+    c.result = ctrs + 32;
+    c.ctr = a.ctr;
+    int32_t level = 0;
+    bool in_cluster = cl != 0;
+    for (;;) {
+        if (in_cluster) {
+            c.d0 = level;
+            if (cl == 16) G2_TRY(launch_cluster<16>(c, st));
+            else G2_TRY(launch_cluster<8>(c, st));
+            G2_TRY(read_counters(g, ctrs + 32, 2, st, d_err));
+            const int32_t reached = g->h_ctr[0], why = g->h_ctr[1];
+            if (reached <= level) return fail(G2_ECUDA, "cluster BFS made no progress");
+            level = reached;
+            if (why == CL_DONE) break;
+            if (why == CL_OVERFLOW) {
+                k_level_list<<<grid_for(g, n, kCta), kCta, 0, st>>>(depth, n, level, a.q[level & 1],
+                                                                    a.cnt + level % 3, d_err);
+                stats().launches += 1;
+                G2_CK(cudaGetLastError());
+            }
+        } else {
+            a.d0 = level;
+            switch (s.load_balance) {
+                case G2_LB_WM: G2_TRY(launch_coop(g, k_bfs_fused<G2_LB_WM>, a, st)); break;
+                case G2_LB_CM: G2_TRY(launch_coop(g, k_bfs_fused<G2_LB_CM>, a, st)); break;
+                case G2_LB_ETWC: G2_TRY(launch_coop(g, k_bfs_fused<G2_LB_ETWC>, a, st)); break;
+                default: G2_TRY(launch_coop(g, k_bfs_fused<G2_LB_VERTEX_BASED>, a, st)); break;
+            }
+            G2_TRY(read_counters(g, ctrs + 24, 2, st, d_err));
+            const int32_t reached = g->h_ctr[0], why = g->h_ctr[1];
+            if (reached <= level) return fail(G2_ECUDA, "fused BFS made no progress");
+            level = reached;
+            if (!why) break;
+        }
+        in_cluster = !in_cluster;
     }
-    G2_TRY(read_counters(g, ctrs + 24, 1, st, d_err));
-    stats().iterations = g->h_ctr[0];
-    stats().push_rounds = g->h_ctr[0];
-    stats().barriers = g->h_ctr[0];
+    stats().iterations = level;
+    stats().push_rounds = level;
+    stats().barriers = level;
     return G2_OK;
 }
 

@@ -118,7 +118,9 @@ def test_bfs_direction_optimising(g2, rmat14, lb, rep, fc):
 
 
 @pytest.mark.parametrize("lb", ["VERTEX_BASED", "WM", "CM", "ETWC"])
-def test_bfs_fused(g2, rmat14, grid, lb):
+def test_bfs_fused(g2, rmat14, grid, lb, monkeypatch):
+    """The grid-wide persistent loop (the one-cluster loop switched off)."""
+    monkeypatch.setenv("G2_FUSED_CLUSTER", "0")
     for g in (rmat14, grid):
         src = g.max_degree_vertex()
         od, op = oracle.bfs_graph(g, src)
@@ -126,6 +128,54 @@ def test_bfs_fused(g2, rmat14, grid, lb):
         assert np.array_equal(d, od) and np.array_equal(p, op), lb
         st = g2.g2_last_stats()
         assert st["launches"] == 1 and st["iterations"] == od.max() + 1
+
+
+def _handover_launches(levels, hi, lo):
+    """Launches of a fused WM BFS whose levels (vertex counts by depth) move
+    between the one-cluster loop (until a level holds more than `hi`) and the
+    grid-wide loop (until a level holds fewer than `lo`); each launch runs its
+    first level unconditionally."""
+    level, in_cluster, launches = 0, True, 0
+    while True:
+        launches += 1
+        d = level + 1
+        while d < len(levels) and levels[d] > 0:
+            if (levels[d] > hi) if in_cluster else (levels[d] < lo):
+                break
+            d += 1
+        if d >= len(levels) or levels[d] == 0:
+            return launches
+        level, in_cluster = d, not in_cluster
+
+
+@pytest.mark.parametrize("hi,lo", [(16384, 8192), (64, 16), (1, 1)])
+def test_bfs_in_one_cluster(g2, rmat14, grid, monkeypatch, hi, lo):
+    """A fused WM BFS runs its small levels inside one thread-block cluster
+    (frontier queues in shared memory, cluster barriers) and its large ones in
+    the grid-wide loop, handing the frontier over at level boundaries; the
+    launch count follows the level sizes.  A level that outgrows a CTA's queue
+    (a star's 30,000 leaves found by one CTA) is rebuilt from the depths and
+    the grid-wide loop finishes (three launches)."""
+    monkeypatch.delenv("G2_FUSED_CLUSTER", raising=False)
+    monkeypatch.setenv("G2_CLUSTER_HI", str(hi))
+    monkeypatch.setenv("G2_CLUSTER_LO", str(lo))
+    star = gg.star(30001)
+    for g in (grid, rmat14, gg.road_grid(300, seed=4), star, gg.path(5000)):
+        dg = g2.load_graph(g)
+        for src in (0, g.n - 1, g.n // 3):
+            od, op = oracle.bfs_graph(g, src)
+            d, p = dev(g.n), dev(g.n)
+            g2.g2_bfs(dg, src, d, p, g2.schedule("WM", kernel_fusion=True))
+            assert np.array_equal(host(d), od) and np.array_equal(host(p), op), (g.name, src)
+            st = g2.g2_last_stats()
+            assert st["iterations"] == od.max() + 1, (g.name, src)
+            levels = np.bincount(od[od >= 0])
+            want = 3 if g is star else _handover_launches(levels, hi, lo)
+            assert st["launches"] == want, (g.name, src, st["launches"], want)
+            # depths alone (no parent array)
+            d2 = dev(g.n)
+            g2.g2_bfs(dg, src, d2, None, g2.schedule("WM", kernel_fusion=True))
+            assert np.array_equal(host(d2), od), (g.name, src)
 
 
 def test_null_schedule_follows_the_degree_bound(g2, rmat14, grid):
