@@ -84,14 +84,18 @@ struct FusedSsspArgs {
     int32_t delta;
     int32_t *nq[2];
     int32_t *fq[2];
-    int32_t *ncnt;     // [3] rotating near-list lengths; ncnt[0] = 1 at launch
-    int32_t *fcnt;     // [2] far-pile lengths (zero at launch)
+    int32_t *ncnt;     // [3] rotating near-list lengths (list 0: ncnt[0] at launch)
+    int32_t *fcnt;     // [2] far-pile lengths (pile 0: fcnt[0] at launch, fcnt[1] = 0)
     int32_t *dmin;     // [2] far minimum per epoch parity (G2_INF32 at launch)
     int32_t *stamp;    // near dedup stamps
     int32_t round0;    // first near stamp
     int32_t *stamp2;   // far dedup stamps
-    int32_t epoch0;    // first far stamp
-    int32_t *result;   // [0] near rounds, [1] buckets
+    int32_t epoch0;    // far stamp of pile 0 at launch
+    int32_t T0;        // threshold of the bucket at launch (clamped to G2_INF32)
+    int32_t lo_far;    // after a near round, stop at a bucket boundary whose
+                       // pile holds at most this many entries (0: never)
+    int32_t *result;   // [0] near rounds, [1] buckets, [2] 1 if stopped for the
+                       // cluster loop, [3] threshold, [4] live pile, [5] epochs
     GridBarrier bar;
     int32_t *err;
     uint64_t limit_ns;
@@ -106,8 +110,8 @@ struct FusedSsspArgs {
 template <int LB>
 __global__ void __launch_bounds__(kCta) k_sssp_fused(FusedSsspArgs a) {
     const int32_t n = a.g.n;
-    int64_t T = a.delta;
-    int d = 0, fp = 0, epoch = 0, buckets = 0;
+    int64_t T = a.T0;
+    int d = 0, fp = 0, epoch = 0, buckets = 0, handover = 0;
     OutCtx out;
     memset(&out, 0, sizeof(out));
     out.mode = OUT_SPARSE;
@@ -138,6 +142,10 @@ __global__ void __launch_bounds__(kCta) k_sssp_fused(FusedSsspArgs a) {
         // near list empty: next bucket from the far pile
         const int32_t nfar = ld_relaxed_i32(a.fcnt + fp);
         if (nfar == 0) break;
+        if (nfar <= a.lo_far && d > 0) {  // no CTA appends now: the same length everywhere
+            handover = 1;
+            break;
+        }
         const int32_t Told = (int32_t)(T < G2_INF32 ? T : G2_INF32);
         int32_t *dm = a.dmin + (epoch & 1);
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -186,6 +194,10 @@ __global__ void __launch_bounds__(kCta) k_sssp_fused(FusedSsspArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.result[0] = d;
         a.result[1] = buckets;
+        a.result[2] = handover;
+        a.result[3] = (int32_t)(T < G2_INF32 ? T : G2_INF32);
+        a.result[4] = fp;
+        a.result[5] = epoch;
     }
 }
 
@@ -250,6 +262,20 @@ __device__ __forceinline__ int32_t cl_read(const int32_t *local, uint32_t rank) 
                  : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
     asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
     return v;
+}
+
+// Warp-aggregated append of the lanes with `pred` to a shared-memory list:
+// one shared atomic per warp; entries past `cap` are counted, not stored.
+// Called by all 32 lanes.
+__device__ __forceinline__ void cta_append(int32_t *q, int32_t *cnt, int32_t cap, int32_t v,
+                                           bool pred, int lane) {
+    const unsigned mask = __ballot_sync(G2_FULL, pred);
+    if (mask == 0) return;
+    const int leader = __ffs(mask) - 1;
+    int32_t pos = 0;
+    if (lane == leader) pos = atomicAdd(cnt, __popc(mask));
+    pos = __shfl_sync(G2_FULL, pos, leader) + __popc(mask & lanemask_lt());
+    if (pred && pos < cap) q[pos] = v;
 }
 
 template <int CL>
@@ -362,14 +388,7 @@ __global__ void __launch_bounds__(kClCta, 1) k_bfs_cluster(ClusterBfsArgs a) {
                     // the smallest source among this level's arcs into v
                     if (a.parent && v[j] >= 0 && (disc || dv[j] == d + 1))
                         atomicMin(reinterpret_cast<unsigned *>(a.parent + v[j]), (unsigned)ou[j]);
-                    const unsigned mask = __ballot_sync(G2_FULL, disc);
-                    if (mask) {
-                        const int leader = __ffs(mask) - 1;
-                        int32_t pos = 0;
-                        if (lane == leader) pos = atomicAdd(&s_cnt[nb], __popc(mask));
-                        pos = __shfl_sync(G2_FULL, pos, leader) + __popc(mask & lanemask_lt());
-                        if (disc && pos < kClQcap) nxt[pos] = v[j];
-                    }
+                    cta_append(nxt, &s_cnt[nb], kClQcap, v[j], disc, lane);
                 }
             }
         }
@@ -403,12 +422,316 @@ __global__ void k_level_list(const int32_t *depth, int32_t n, int32_t lvl, int32
     }
 }
 
-// Cluster size for the loop on the current device: 16 CTAs where a cluster
-// that large fits, else 8; 0 when none fits or G2_FUSED_CLUSTER=0 (read on
-// every call; G2_FUSED_CLUSTER=8 or 16 asks for that size).
+// ------------------------------------------------- delta-stepping in one cluster
+// The near/far loop of k_sssp_fused inside one thread-block cluster while the
+// near lists are small.  Each CTA keeps, in its own shared memory, the near
+// list entries it appended (two buffers, as the BFS above) and its part of
+// the far pile (two piles, old and new epoch).  A near round relaxes an equal
+// slice of the cluster's near list (read through distributed shared memory),
+// four arcs per lane in flight; an improvement below the bucket threshold
+// joins the CTA's next near list, one at or above it joins the CTA's far pile
+// (deduplicated per round / epoch by the same stamps as the grid loop).  When
+// the near list empties, every CTA takes the smallest live distance of its
+// own pile, the cluster minimum (read through distributed shared memory)
+// fixes the next bucket, and each CTA splits its own pile into its near list
+// and its new pile.
+//
+// Hand-over: the cluster stops before a near round of more than `hi`
+// vertices and writes its near list and far pile to the global lists the grid
+// loop starts from; the grid loop stops at a bucket boundary whose far pile
+// holds at most `lo_far` entries and the cluster starts from that pile.  A
+// near list or pile that outgrows its shared buffer (appends past the
+// capacity are counted, not stored) stops the cluster too; the bucket's state
+// is then rebuilt from the distances (k_sssp_rebuild) and the grid loop goes
+// on.  Decisions use only counts that no CTA changes while they are read, so
+// every CTA takes the same ones and passes the same cluster barriers.
+constexpr int kCsQn = 12288;  // near entries per CTA and buffer
+constexpr int kCsQf = 14336;  // far entries per CTA and pile
+constexpr size_t kCsSmem = (2 * (size_t)kCsQn + 2 * (size_t)kCsQf) * 4;  // 208 KiB
+
+struct ClusterSsspArgs {
+    DevGraph g;
+    int32_t *dist;
+    int32_t delta;
+    const int32_t *nq_in;    // first near list (global) ...
+    const int32_t *ncnt_in;  // ... and its length (null: empty)
+    const int32_t *fq_in;    // far pile at launch (global) ...
+    const int32_t *fcnt_in;  // ... and its length; at most kCsQf * CL / 2 entries
+    int32_t T0;              // threshold of the current bucket (clamped to G2_INF32)
+    int32_t *stamp;          // near dedup: round r's appends carry round0 + r
+    int32_t round0;
+    int32_t *stamp2;         // far dedup: the pile of epoch e carries epoch0 + e
+    int32_t epoch0;
+    int32_t hi;              // stop before a near round with more vertices
+    int32_t *nq_out;         // hand-over: near list ...
+    int32_t *fq_out;         // ... and far pile for the grid loop
+    int32_t *ncnt;           // the grid loop's near lengths [3], far lengths [2],
+    int32_t *fcnt;           // far minima [2], set on hand-over
+    int32_t *dmin;
+    int32_t *result;         // out: [0] near rounds, [1] epochs advanced, [2] CL_*, [3] T
+    int32_t *err;
+    unsigned long long *ctr;
+};
+
 template <int CL>
-static bool cluster_fits() {
-    const size_t smem = 2 * (size_t)kClQcap * 4;
+__global__ void __launch_bounds__(kClCta, 1) k_sssp_cluster(ClusterSsspArgs a) {
+    extern __shared__ int32_t s_mem[];
+    int32_t *s_nq = s_mem;              // [2][kCsQn]
+    int32_t *s_fq = s_mem + 2 * kCsQn;  // [2][kCsQf]
+    __shared__ int32_t s_ncnt[2], s_fcnt[2];
+    __shared__ int32_t s_off[CL + 1], s_foff[CL + 1];
+    __shared__ int32_t s_nover, s_fover, s_min;
+    uint32_t rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t *__restrict__ rowptr = a.g.rowptr;
+    const int32_t *__restrict__ col = a.g.col;
+    const int32_t *__restrict__ wt = a.g.w;
+    // this CTA's slice of the far pile
+    {
+        const int32_t ftot = ld_relaxed_i32(a.fcnt_in);
+        const int32_t flo = (int32_t)((int64_t)ftot * rank / CL);
+        const int32_t fhi = (int32_t)((int64_t)ftot * (rank + 1) / CL);
+        for (int32_t j = threadIdx.x; j < fhi - flo; j += kClCta) s_fq[j] = a.fq_in[flo + j];
+        if (threadIdx.x == 0) {
+            s_fcnt[0] = fhi - flo;
+            s_fcnt[1] = 0;
+            s_ncnt[0] = 0;
+            s_ncnt[1] = 0;
+        }
+    }
+    int32_t total = a.ncnt_in ? ld_relaxed_i32(a.ncnt_in) : 0;
+    int32_t T = a.T0;
+    int fp = 0, e = 0, r = 0, reason = CL_DONE;
+    unsigned long long arcs = 0;
+    cl_barrier();
+    int d = 0;  // near buffer parity: level d reads buffer d & 1
+    bool first = true;
+    for (;;) {
+        const int cb = d & 1, nb = cb ^ 1;
+        if (!first) {
+            if (warp == 0) {
+                int32_t c = lane < CL ? cl_read(&s_ncnt[cb], lane) : 0;
+                int32_t f = lane < CL ? cl_read(&s_fcnt[fp], lane) : 0;
+                const bool nover = __any_sync(G2_FULL, c > kCsQn);
+                const bool fover = __any_sync(G2_FULL, f > kCsQf);
+#pragma unroll
+                for (int o = 1; o < CL; o <<= 1) {
+                    const int32_t t1 = __shfl_up_sync(G2_FULL, c, o);
+                    const int32_t t2 = __shfl_up_sync(G2_FULL, f, o);
+                    if (lane >= o) {
+                        c += t1;
+                        f += t2;
+                    }
+                }
+                if (lane < CL) {
+                    s_off[lane + 1] = c;
+                    s_foff[lane + 1] = f;
+                }
+                if (lane == 0) {
+                    s_off[0] = 0;
+                    s_foff[0] = 0;
+                    s_nover = nover;
+                    s_fover = fover;  // meaningful only when no CTA appends this level
+                    s_ncnt[nb] = 0;
+                }
+            }
+            __syncthreads();
+            total = s_off[CL];
+            if (s_nover || ((total == 0 || total > a.hi) && s_fover)) {
+                reason = CL_OVERFLOW;
+                break;
+            }
+            if (total > a.hi) {
+                // hand the bucket to the grid loop: this CTA's near list and pile
+                const int32_t nmine = s_off[rank + 1] - s_off[rank];
+                const int32_t fmine = s_foff[rank + 1] - s_foff[rank];
+                for (int32_t j = threadIdx.x; j < nmine; j += kClCta)
+                    a.nq_out[s_off[rank] + j] = s_nq[cb * kCsQn + j];
+                for (int32_t j = threadIdx.x; j < fmine; j += kClCta)
+                    a.fq_out[s_foff[rank] + j] = s_fq[fp * kCsQf + j];
+                reason = CL_TO_GRID;
+                break;
+            }
+        }
+        if (total > 0) {
+            // near round r: relax the arcs of this CTA's slice of the near list
+            const int32_t rid = a.round0 + r, eid = a.epoch0 + e;
+            const int32_t *cur = s_nq + cb * kCsQn;
+            int32_t *nxt = s_nq + nb * kCsQn;
+            int32_t *far = s_fq + fp * kCsQf;
+            const int32_t lo = (int32_t)((int64_t)total * rank / CL);
+            const int32_t hi = (int32_t)((int64_t)total * (rank + 1) / CL);
+            for (int32_t base = lo + warp * 32; base < hi; base += kClCta) {
+                const int32_t i = base + lane;
+                int32_t u = 0, beg = 0, deg = 0, du = 0;
+                if (i < hi) {
+                    if (first) {
+                        u = a.nq_in[i];
+                    } else {
+                        int q = 0;
+#pragma unroll
+                        for (int j = 1; j < CL; ++j) q += i >= s_off[j];
+                        u = cl_read(cur + (i - s_off[q]), (uint32_t)q);
+                    }
+                    beg = __ldg(rowptr + u);
+                    deg = __ldg(rowptr + u + 1) - beg;
+                    du = a.dist[u];
+                }
+                int32_t incl = deg;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t t = __shfl_up_sync(G2_FULL, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int32_t tot = __shfl_sync(G2_FULL, incl, 31);
+                const int32_t excl = incl - deg;
+                arcs += (unsigned)tot;
+                for (int32_t k0 = 0; k0 < tot; k0 += 32 * kClArcs) {
+                    int32_t v[kClArcs], nv[kClArcs], old[kClArcs];
+#pragma unroll
+                    for (int j = 0; j < kClArcs; ++j) {
+                        const int32_t k = k0 + 32 * j + lane;
+                        int own = 0;
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1) {
+                            const int32_t ex = __shfl_sync(G2_FULL, excl, own + step);
+                            if (ex <= k) own += step;
+                        }
+                        const int32_t ob = __shfl_sync(G2_FULL, beg, own);
+                        const int32_t oe = __shfl_sync(G2_FULL, excl, own);
+                        const int32_t od = __shfl_sync(G2_FULL, du, own);
+                        v[j] = -1;
+                        nv[j] = 0;
+                        if (k < tot) {
+                            const int32_t arc = ob + (k - oe);
+                            const int64_t nd = (int64_t)od + __ldg(wt + arc);
+                            if (nd >= G2_INF32) {
+                                set_error(a.err, G2_EOVERFLOW);
+                            } else {
+                                v[j] = __ldg(col + arc);
+                                nv[j] = (int32_t)nd;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < kClArcs; ++j)
+                        old[j] = v[j] >= 0 ? atomicMin(a.dist + v[j], nv[j]) : 0;
+#pragma unroll
+                    for (int j = 0; j < kClArcs; ++j) {
+                        const bool better = v[j] >= 0 && nv[j] < old[j];
+                        bool to_near = better && nv[j] < T;
+                        bool to_far = better && nv[j] >= T;
+                        if (to_near) to_near = atomicExch(a.stamp + v[j], rid) != rid;
+                        if (to_far) to_far = atomicExch(a.stamp2 + v[j], eid) != eid;
+                        cta_append(nxt, &s_ncnt[nb], kCsQn, v[j], to_near, lane);
+                        cta_append(far, &s_fcnt[fp], kCsQf, v[j], to_far, lane);
+                    }
+                }
+            }
+            first = false;
+            cl_barrier();  // round complete: lists nb and piles filled
+            ++d;
+            ++r;
+            continue;
+        }
+        if (first) {  // launched at a bucket boundary: read the counts first
+            first = false;
+            continue;
+        }
+        // bucket boundary: the smallest live far distance over the cluster
+        if (s_foff[CL] == 0) break;  // nothing left: done
+        const int32_t Told = T;
+        {
+            if (threadIdx.x == 0) s_min = G2_INF32;
+            __syncthreads();
+            int32_t best = G2_INF32;
+            const int32_t mine = s_fcnt[fp];
+            for (int32_t j = threadIdx.x; j < mine; j += kClCta) {
+                const int32_t dv = a.dist[s_fq[fp * kCsQf + j]];
+                if (dv >= Told && dv < best) best = dv;
+            }
+            best = (int32_t)__reduce_min_sync(G2_FULL, (unsigned)best);
+            if (lane == 0 && best != G2_INF32) atomicMin(&s_min, best);
+        }
+        cl_barrier();
+        int32_t dm = lane < CL ? cl_read(&s_min, lane) : G2_INF32;
+        dm = (int32_t)__reduce_min_sync(G2_FULL, (unsigned)dm);
+        if (dm == G2_INF32) break;  // only stale entries left: done
+        const int64_t Tnew = ((int64_t)dm / a.delta + 1) * (int64_t)a.delta;
+        const int32_t Tn = (int32_t)(Tnew < G2_INF32 ? Tnew : G2_INF32);
+        const int32_t neid = a.epoch0 + e + 1;
+        if (threadIdx.x == 0) s_fcnt[fp ^ 1] = 0;
+        __syncthreads();
+        // split this CTA's pile: the next bucket to near list cb, the rest to
+        // the new pile (stale entries, already settled, are dropped)
+        {
+            const int32_t mine = s_fcnt[fp];
+            const int32_t *pile = s_fq + fp * kCsQf;
+            int32_t *npile = s_fq + (fp ^ 1) * kCsQf;
+            int32_t *nl = s_nq + cb * kCsQn;
+            for (int32_t base = warp * 32; base < mine; base += kClCta) {
+                const int32_t j = base + lane;
+                int32_t v = 0, dv = G2_INF32;
+                if (j < mine) {
+                    v = pile[j];
+                    dv = a.dist[v];
+                }
+                const bool to_near = j < mine && dv >= Told && dv < Tn;
+                const bool to_far = j < mine && dv >= Tn;
+                if (to_far) a.stamp2[v] = neid;
+                cta_append(nl, &s_ncnt[cb], kCsQn, v, to_near, lane);
+                cta_append(npile, &s_fcnt[fp ^ 1], kCsQf, v, to_far, lane);
+            }
+        }
+        cl_barrier();  // split complete everywhere; the near counts of cb are final
+        fp ^= 1;
+        ++e;
+        T = Tn;
+    }
+    cl_barrier();  // no CTA leaves while a peer may still read its counts
+    if (a.ctr && lane == 0 && arcs) atomicAdd(a.ctr, arcs);
+    if (threadIdx.x == 0 && rank == 0) {
+        a.result[0] = r;
+        a.result[1] = e;
+        a.result[2] = reason;
+        a.result[3] = T;
+        if (reason == CL_TO_GRID) {
+            a.ncnt[0] = total;
+            a.ncnt[1] = 0;
+            a.ncnt[2] = 0;
+            a.fcnt[0] = s_foff[CL];
+            a.fcnt[1] = 0;
+            a.dmin[0] = G2_INF32;
+            a.dmin[1] = G2_INF32;
+        }
+    }
+}
+
+// The state of the bucket below T rebuilt from the distances: every vertex in
+// [T - delta, T) to near list 0 (settled ones among them relax nothing new),
+// every finite distance >= T to far pile 0 with the epoch stamp `eid`.
+__global__ void k_sssp_rebuild(const int32_t *dist, int32_t n, int32_t T, int32_t delta,
+                               int32_t *nq, int32_t *ncnt, int32_t *fq, int32_t *fcnt,
+                               int32_t *stamp2, int32_t eid, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t Tb = (int64_t)T - delta;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + lane;
+        const int32_t dv = v < n ? dist[v] : G2_INF32;
+        const bool to_near = v < n && dv >= Tb && dv < T;
+        const bool to_far = v < n && dv >= T && dv != G2_INF32;
+        if (to_far) stamp2[v] = eid;
+        warp_append(nq, ncnt, n, err, (int32_t)v, to_near);
+        warp_append(fq, fcnt, n, err, (int32_t)v, to_far);
+    }
+}
+
+// Whether one cluster of CL CTAs of `kernel` (kClCta threads, `smem` bytes
+// of dynamic shared memory) fits on the current device.
+template <class K>
+static bool cluster_fits(K kernel, int CL, size_t smem) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -421,34 +744,44 @@ static bool cluster_fits() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    bool ok = cudaFuncSetAttribute(k_bfs_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    bool ok = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem) == cudaSuccess;
     if (ok && CL > 8)
-        ok = cudaFuncSetAttribute(k_bfs_cluster<CL>,
-                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
-    ok = ok && cudaOccupancyMaxActiveClusters(&clusters, k_bfs_cluster<CL>, &cfg) == cudaSuccess &&
+        ok = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+             cudaSuccess;
+    ok = ok && cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) == cudaSuccess &&
          clusters >= 1;
     cudaGetLastError();
     return ok;
 }
 
-static int cluster_size() {
+// Cluster size for the one-cluster loops (which = 0 BFS, 1 SSSP) on the
+// current device: 16 CTAs where a cluster that large fits, else 8; 0 when
+// none fits or G2_FUSED_CLUSTER=0 (read on every call; G2_FUSED_CLUSTER=8 or
+// 16 asks for that size).
+static int cluster_size(int which) {
     const char *e = getenv("G2_FUSED_CLUSTER");
     const int want = e ? atoi(e) : -1;
     if (want == 0) return 0;
     constexpr int kMaxDev = 64;
     static std::mutex mu;
-    static int fits[kMaxDev][2];  // per device: 16 / 8 CTAs; 0 unknown, 1 fits, 2 does not
+    static int fits[kMaxDev][2][2];  // device, loop, 16 / 8 CTAs: 0 unknown, 1 fits, 2 not
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
         cudaGetLastError();
         return 0;
     }
     std::lock_guard<std::mutex> lock(mu);
-    if (fits[dev][0] == 0) fits[dev][0] = cluster_fits<16>() ? 1 : 2;
-    if (fits[dev][1] == 0) fits[dev][1] = cluster_fits<8>() ? 1 : 2;
-    if (want != 8 && fits[dev][0] == 1) return 16;
-    if (want != 16 && fits[dev][1] == 1) return 8;
+    int *f = fits[dev][which];
+    const size_t bfs_smem = 2 * (size_t)kClQcap * 4;
+    if (f[0] == 0)
+        f[0] = (which ? cluster_fits(k_sssp_cluster<16>, 16, kCsSmem)
+                      : cluster_fits(k_bfs_cluster<16>, 16, bfs_smem)) ? 1 : 2;
+    if (f[1] == 0)
+        f[1] = (which ? cluster_fits(k_sssp_cluster<8>, 8, kCsSmem)
+                      : cluster_fits(k_bfs_cluster<8>, 8, bfs_smem)) ? 1 : 2;
+    if (want != 8 && f[0] == 1) return 16;
+    if (want != 16 && f[1] == 1) return 8;
     return 0;
 }
 
@@ -459,8 +792,8 @@ static int32_t env_i32(const char *name, int32_t dflt) {
     return e ? (int32_t)atoi(e) : dflt;
 }
 
-template <int CL>
-static g2_status launch_cluster(const ClusterBfsArgs &a, cudaStream_t st) {
+template <class K, class A>
+static g2_status launch_cluster(K kernel, int CL, size_t smem, const A &a, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -469,11 +802,11 @@ static g2_status launch_cluster(const ClusterBfsArgs &a, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(kClCta);
-    cfg.dynamicSmemBytes = 2 * (size_t)kClQcap * 4;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    G2_CK(cudaLaunchKernelEx(&cfg, k_bfs_cluster<CL>, a));
+    G2_CK(cudaLaunchKernelEx(&cfg, kernel, a));
     stats().launches += 1;
     return G2_OK;
 }
@@ -520,7 +853,7 @@ g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     // WM rounds start in one cluster and move between it and the grid-wide
     // loop as the levels grow and shrink; the other strategies (and a device
     // without room for the cluster) run the grid-wide loop throughout.
-    const int cl = s.load_balance == G2_LB_WM ? cluster_size() : 0;
+    const int cl = s.load_balance == G2_LB_WM ? cluster_size(0) : 0;
     // measured on road grids 1024^2..4096^2 with 16-CTA clusters: hand a
     // level to the grid above 16384 vertices, take it back below 8192
     a.lo = cl ? env_i32("G2_CLUSTER_LO", 512 * cl) : 0;
@@ -539,8 +872,8 @@ g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     for (;;) {
         if (in_cluster) {
             c.d0 = level;
-            if (cl == 16) G2_TRY(launch_cluster<16>(c, st));
-            else G2_TRY(launch_cluster<8>(c, st));
+            if (cl == 16) G2_TRY(launch_cluster(k_bfs_cluster<16>, 16, 2 * (size_t)kClQcap * 4, c, st));
+            else G2_TRY(launch_cluster(k_bfs_cluster<8>, 8, 2 * (size_t)kClQcap * 4, c, st));
             G2_TRY(read_counters(g, ctrs + 32, 2, st, d_err));
             const int32_t reached = g->h_ctr[0], why = g->h_ctr[1];
             if (reached <= level) return fail(G2_ECUDA, "cluster BFS made no progress");
@@ -618,18 +951,95 @@ g2_status sssp_fused(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
     int32_t zero = 0;
     G2_CK(cudaMemcpyAsync(dist + src, &zero, 4, cudaMemcpyHostToDevice, st));
     G2_CK(cudaMemcpyAsync(a.nq[0], &src, 4, cudaMemcpyHostToDevice, st));
-    switch (s.load_balance) {
-        case G2_LB_WM: G2_TRY(launch_coop(g, k_sssp_fused<G2_LB_WM>, a, st)); break;
-        case G2_LB_CM: G2_TRY(launch_coop(g, k_sssp_fused<G2_LB_CM>, a, st)); break;
-        case G2_LB_ETWC: G2_TRY(launch_coop(g, k_sssp_fused<G2_LB_ETWC>, a, st)); break;
-        default: G2_TRY(launch_coop(g, k_sssp_fused<G2_LB_VERTEX_BASED>, a, st)); break;
+    // WM buckets start in one cluster; near rounds above `hi` vertices move to
+    // the grid-wide loop, which hands back at a bucket boundary with at most
+    // `lo_far` pile entries (never more than the next near list can start
+    // with in the cluster, nor than the cluster's piles hold).
+    const int cl = s.load_balance == G2_LB_WM ? cluster_size(1) : 0;
+    ClusterSsspArgs c;
+    c.g = a.g;
+    c.dist = dist;
+    c.delta = delta;
+    c.stamp = a.stamp;
+    c.stamp2 = a.stamp2;
+    c.hi = env_i32("G2_CLUSTER_HI", 1024 * cl);
+    c.nq_out = a.nq[0];
+    c.fq_out = a.fq[0];
+    c.ncnt = a.ncnt;
+    c.fcnt = a.fcnt;
+    c.dmin = a.dmin;
+    c.result = ctrs + 36;
+    c.err = d_err;
+    c.ctr = a.ctr;
+    a.lo_far = cl ? std::min(std::min(env_i32("G2_CLUSTER_FAR_LO", 1024 * cl), c.hi),
+                             (int32_t)(kCsQf / 2 * cl))
+                  : 0;
+    int32_t T = (int32_t)std::min<int64_t>(delta, G2_INF32);
+    int32_t round0 = g->round + 1, epoch0 = g->round2 + 1;
+    int32_t rounds = 0, buckets = 0;
+    const int32_t *near_in = a.nq[0], *ncnt_in = a.ncnt, *far_in = a.fq[0], *fcnt_in = a.fcnt;
+    bool in_cluster = cl != 0;
+    for (;;) {
+        if (in_cluster) {
+            c.nq_in = near_in;
+            c.ncnt_in = ncnt_in;
+            c.fq_in = far_in;
+            c.fcnt_in = fcnt_in;
+            c.T0 = T;
+            c.round0 = round0;
+            c.epoch0 = epoch0;
+            if (cl == 16) G2_TRY(launch_cluster(k_sssp_cluster<16>, 16, kCsSmem, c, st));
+            else G2_TRY(launch_cluster(k_sssp_cluster<8>, 8, kCsSmem, c, st));
+            G2_TRY(read_counters(g, ctrs + 36, 4, st, d_err));
+            const int32_t r = g->h_ctr[0], e = g->h_ctr[1], why = g->h_ctr[2];
+            rounds += r;
+            buckets += e;
+            round0 += r + 1;
+            epoch0 += e;
+            T = g->h_ctr[3];
+            if (why == CL_DONE) break;
+            if (r + e == 0) return fail(G2_ECUDA, "cluster SSSP made no progress");
+            if (why == CL_OVERFLOW) {
+                // near list and pile of the bucket below T from the distances
+                const int32_t reset[7] = {0, 0, 0, 0, 0, G2_INF32, G2_INF32};
+                G2_CK(cudaMemcpyAsync(ctrs + 20, reset, 7 * 4, cudaMemcpyHostToDevice, st));
+                ++epoch0;
+                k_sssp_rebuild<<<grid_for(g, n, kCta), kCta, 0, st>>>(
+                    dist, n, T, delta, a.nq[0], a.ncnt, a.fq[0], a.fcnt, a.stamp2, epoch0, d_err);
+                stats().launches += 1;
+                G2_CK(cudaGetLastError());
+            }
+        } else {
+            a.T0 = T;
+            a.round0 = round0;
+            a.epoch0 = epoch0;
+            switch (s.load_balance) {
+                case G2_LB_WM: G2_TRY(launch_coop(g, k_sssp_fused<G2_LB_WM>, a, st)); break;
+                case G2_LB_CM: G2_TRY(launch_coop(g, k_sssp_fused<G2_LB_CM>, a, st)); break;
+                case G2_LB_ETWC: G2_TRY(launch_coop(g, k_sssp_fused<G2_LB_ETWC>, a, st)); break;
+                default: G2_TRY(launch_coop(g, k_sssp_fused<G2_LB_VERTEX_BASED>, a, st)); break;
+            }
+            G2_TRY(read_counters(g, ctrs + 30, 6, st, d_err));
+            const int32_t r = g->h_ctr[0], why = g->h_ctr[2], fp = g->h_ctr[4];
+            rounds += r;
+            buckets += g->h_ctr[1];
+            round0 += r + 1;
+            epoch0 += g->h_ctr[5];
+            T = g->h_ctr[3];
+            if (!why) break;
+            if (r == 0) return fail(G2_ECUDA, "fused SSSP made no progress");
+            near_in = nullptr;  // handed back at a bucket boundary: no near list
+            ncnt_in = nullptr;
+            far_in = a.fq[fp];
+            fcnt_in = a.fcnt + fp;
+        }
+        in_cluster = !in_cluster;
     }
-    G2_TRY(read_counters(g, ctrs + 30, 2, st, d_err));
-    stats().iterations = g->h_ctr[0];
-    stats().push_rounds = g->h_ctr[0];
-    stats().barriers = g->h_ctr[0] + 2 * g->h_ctr[1];
-    g->round += g->h_ctr[0] + 1;
-    g->round2 += g->h_ctr[1] + 1;
+    stats().iterations = rounds;
+    stats().push_rounds = rounds;
+    stats().barriers = rounds + 2 * buckets;
+    g->round = round0;
+    g->round2 = epoch0 + 1;
     return G2_OK;
 }
 

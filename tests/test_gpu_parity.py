@@ -256,7 +256,9 @@ def test_sssp_delta_sweep(g2, rmat14, grid):
 
 
 @pytest.mark.parametrize("lb", ["VERTEX_BASED", "WM", "CM", "ETWC"])
-def test_sssp_fused(g2, rmat14, grid, lb):
+def test_sssp_fused(g2, rmat14, grid, lb, monkeypatch):
+    """The grid-wide persistent near/far loop (the one-cluster loop off)."""
+    monkeypatch.setenv("G2_FUSED_CLUSTER", "0")
     for g, wmax in ((rmat14, 255), (grid, 1000)):
         w = gg.pair_weights(g, wmax, seed=2)
         src = 5
@@ -267,6 +269,40 @@ def test_sssp_fused(g2, rmat14, grid, lb):
             g2.g2_sssp_delta(dg, src, delta, dist, g2.schedule(lb, kernel_fusion=True))
             assert np.array_equal(host(dist), want), (g.name, lb, delta)
             assert g2.g2_last_stats()["launches"] == 1
+
+
+@pytest.mark.parametrize("hi,far_lo", [(None, None), (64, 64), (64, 1), (1, 1)])
+def test_sssp_in_one_cluster(g2, rmat14, grid, monkeypatch, hi, far_lo):
+    """Fused WM delta-stepping starts in one thread-block cluster (near lists
+    and far piles in shared memory) and moves to the grid-wide loop before a
+    near round of more than `hi` vertices, back at a bucket boundary whose
+    pile holds at most `far_lo` entries.  A near list that outgrows a CTA's
+    buffer (a star's 30,000 leaves) is rebuilt from the distances.  Every
+    combination gives the oracle's distances."""
+    monkeypatch.delenv("G2_FUSED_CLUSTER", raising=False)
+    if hi is None:
+        monkeypatch.delenv("G2_CLUSTER_HI", raising=False)
+        monkeypatch.delenv("G2_CLUSTER_FAR_LO", raising=False)
+    else:
+        monkeypatch.setenv("G2_CLUSTER_HI", str(hi))
+        monkeypatch.setenv("G2_CLUSTER_FAR_LO", str(far_lo))
+    star = gg.star(30001)
+    graphs = [(grid, 1000), (rmat14, 255), (gg.road_grid(300, seed=4), 1000), (star, 50),
+              (gg.path(3000), 20)]
+    for g, wmax in graphs:
+        w = gg.pair_weights(g, wmax, seed=3)
+        dg = g2.load_graph(g, w)
+        for src in (0, g.n - 1):
+            want = oracle.sssp_graph(g, w, src)
+            for delta in (1, 100, 4096, 1 << 30):
+                dist = dev(g.n)
+                g2.g2_sssp_delta(dg, src, delta, dist, g2.schedule("WM", kernel_fusion=True))
+                assert np.array_equal(host(dist), want), (g.name, src, delta)
+                st = g2.g2_last_stats()
+                if g is star:
+                    assert st["launches"] >= 3, (src, delta, st)  # cluster, rebuild, grid
+                elif hi is None and g.n <= 16384:
+                    assert st["launches"] == 1, (g.name, src, delta, st)  # all in the cluster
 
 
 def test_sssp_dedup_variants_and_edge_cases(g2, rmat14):
