@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "g2_cluster.cuh"
 #include "g2_host.h"
 #include "g2_lb.cuh"
 
@@ -229,11 +230,8 @@ __global__ void k_fill_dist(int32_t *a, int32_t n) {
 // least one level.  A level that outgrows a CTA's queue (appends past the
 // capacity are counted, not stored) also stops the cluster; its vertices are
 // all labelled, so the host rebuilds that frontier from the depths.
-constexpr int kClCta = 1024;      // threads per CTA
 constexpr int kClQcap = 28672;    // queue entries per CTA and buffer (2 buffers: 224 KiB)
 constexpr int kClArcs = 4;        // arcs per lane in flight
-
-enum { CL_DONE = 0, CL_TO_GRID = 1, CL_OVERFLOW = 2 };
 
 struct ClusterBfsArgs {
     DevGraph g;
@@ -247,45 +245,13 @@ struct ClusterBfsArgs {
     unsigned long long *ctr;  // arcs examined, or null
 };
 
-__device__ __forceinline__ void cl_barrier() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
-                 ::: "memory");
-}
-
-// The value at `local` (a shared-memory address of this CTA) in the shared
-// memory of cluster CTA `rank`.
-__device__ __forceinline__ int32_t cl_read(const int32_t *local, uint32_t rank) {
-    uint32_t ra;
-    int32_t v;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
-                 : "=r"(ra)
-                 : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
-    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
-    return v;
-}
-
-// Warp-aggregated append of the lanes with `pred` to a shared-memory list:
-// one shared atomic per warp; entries past `cap` are counted, not stored.
-// Called by all 32 lanes.
-__device__ __forceinline__ void cta_append(int32_t *q, int32_t *cnt, int32_t cap, int32_t v,
-                                           bool pred, int lane) {
-    const unsigned mask = __ballot_sync(G2_FULL, pred);
-    if (mask == 0) return;
-    const int leader = __ffs(mask) - 1;
-    int32_t pos = 0;
-    if (lane == leader) pos = atomicAdd(cnt, __popc(mask));
-    pos = __shfl_sync(G2_FULL, pos, leader) + __popc(mask & lanemask_lt());
-    if (pred && pos < cap) q[pos] = v;
-}
-
 template <int CL>
 __global__ void __launch_bounds__(kClCta, 1) k_bfs_cluster(ClusterBfsArgs a) {
     extern __shared__ int32_t s_q[];    // [2][kClQcap]
     __shared__ int32_t s_cnt[2];        // entries appended to queue buffer 0 / 1
     __shared__ int32_t s_off[CL + 1];   // prefix of the cluster's queue lengths
     __shared__ int32_t s_over;
-    uint32_t rank;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const uint32_t rank = cl_rank();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t *__restrict__ rowptr = a.g.rowptr;
     const int32_t *__restrict__ col = a.g.col;
@@ -345,9 +311,7 @@ __global__ void __launch_bounds__(kClCta, 1) k_bfs_cluster(ClusterBfsArgs a) {
                 if (first) {
                     u = qg[i];
                 } else {
-                    int r = 0;
-#pragma unroll
-                    for (int j = 1; j < CL; ++j) r += i >= s_off[j];
+                    const int r = cl_owner<CL>(s_off, i);
                     u = cl_read(cur + (i - s_off[r]), (uint32_t)r);
                 }
                 beg = __ldg(rowptr + u);
@@ -406,19 +370,6 @@ __global__ void __launch_bounds__(kClCta, 1) k_bfs_cluster(ClusterBfsArgs a) {
             a.cnt[d % 3] = 0;  // rebuilt from the depths
             a.cnt[(d + 1) % 3] = 0;
         }
-    }
-}
-
-// The vertices at depth `lvl`, appended to q (the frontier of a level the
-// cluster loop could not hold).
-__global__ void k_level_list(const int32_t *depth, int32_t n, int32_t lvl, int32_t *q,
-                             int32_t *cnt, int32_t *err) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < n;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = base + lane;
-        const bool p = v < n && depth[v] == lvl;
-        warp_append(q, cnt, n, err, (int32_t)v, p);
     }
 }
 
@@ -481,8 +432,7 @@ __global__ void __launch_bounds__(kClCta, 1) k_sssp_cluster(ClusterSsspArgs a) {
     __shared__ int32_t s_ncnt[2], s_fcnt[2];
     __shared__ int32_t s_off[CL + 1], s_foff[CL + 1];
     __shared__ int32_t s_nover, s_fover, s_min;
-    uint32_t rank;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const uint32_t rank = cl_rank();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t *__restrict__ rowptr = a.g.rowptr;
     const int32_t *__restrict__ col = a.g.col;
@@ -569,9 +519,7 @@ __global__ void __launch_bounds__(kClCta, 1) k_sssp_cluster(ClusterSsspArgs a) {
                     if (first) {
                         u = a.nq_in[i];
                     } else {
-                        int q = 0;
-#pragma unroll
-                        for (int j = 1; j < CL; ++j) q += i >= s_off[j];
+                        const int q = cl_owner<CL>(s_off, i);
                         u = cl_read(cur + (i - s_off[q]), (uint32_t)q);
                     }
                     beg = __ldg(rowptr + u);
@@ -728,89 +676,6 @@ __global__ void k_sssp_rebuild(const int32_t *dist, int32_t n, int32_t T, int32_
     }
 }
 
-// Whether one cluster of CL CTAs of `kernel` (kClCta threads, `smem` bytes
-// of dynamic shared memory) fits on the current device.
-template <class K>
-static bool cluster_fits(K kernel, int CL, size_t smem) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(CL);
-    cfg.blockDim = dim3(kClCta);
-    cfg.dynamicSmemBytes = smem;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int clusters = 0;
-    bool ok = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem) == cudaSuccess;
-    if (ok && CL > 8)
-        ok = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-             cudaSuccess;
-    ok = ok && cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) == cudaSuccess &&
-         clusters >= 1;
-    cudaGetLastError();
-    return ok;
-}
-
-// Cluster size for the one-cluster loops (which = 0 BFS, 1 SSSP) on the
-// current device: 16 CTAs where a cluster that large fits, else 8; 0 when
-// none fits or G2_FUSED_CLUSTER=0 (read on every call; G2_FUSED_CLUSTER=8 or
-// 16 asks for that size).
-static int cluster_size(int which) {
-    const char *e = getenv("G2_FUSED_CLUSTER");
-    const int want = e ? atoi(e) : -1;
-    if (want == 0) return 0;
-    constexpr int kMaxDev = 64;
-    static std::mutex mu;
-    static int fits[kMaxDev][2][2];  // device, loop, 16 / 8 CTAs: 0 unknown, 1 fits, 2 not
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
-        cudaGetLastError();
-        return 0;
-    }
-    std::lock_guard<std::mutex> lock(mu);
-    int *f = fits[dev][which];
-    const size_t bfs_smem = 2 * (size_t)kClQcap * 4;
-    if (f[0] == 0)
-        f[0] = (which ? cluster_fits(k_sssp_cluster<16>, 16, kCsSmem)
-                      : cluster_fits(k_bfs_cluster<16>, 16, bfs_smem)) ? 1 : 2;
-    if (f[1] == 0)
-        f[1] = (which ? cluster_fits(k_sssp_cluster<8>, 8, kCsSmem)
-                      : cluster_fits(k_bfs_cluster<8>, 8, bfs_smem)) ? 1 : 2;
-    if (want != 8 && f[0] == 1) return 16;
-    if (want != 16 && f[1] == 1) return 8;
-    return 0;
-}
-
-// Level-size thresholds of the hand-over (G2_CLUSTER_HI / G2_CLUSTER_LO
-// override them for sweeps).
-static int32_t env_i32(const char *name, int32_t dflt) {
-    const char *e = getenv(name);
-    return e ? (int32_t)atoi(e) : dflt;
-}
-
-template <class K, class A>
-static g2_status launch_cluster(K kernel, int CL, size_t smem, const A &a, cudaStream_t st) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(CL);
-    cfg.blockDim = dim3(kClCta);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    G2_CK(cudaLaunchKernelEx(&cfg, kernel, a));
-    stats().launches += 1;
-    return G2_OK;
-}
-
 static g2_status check_fused_lb(const g2_schedule &s) {
     if (s.direction != G2_PUSH)
         return fail(G2_EUNSUPPORTED, "fused loops run PUSH rounds");
@@ -853,7 +718,9 @@ g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     // WM rounds start in one cluster and move between it and the grid-wide
     // loop as the levels grow and shrink; the other strategies (and a device
     // without room for the cluster) run the grid-wide loop throughout.
-    const int cl = s.load_balance == G2_LB_WM ? cluster_size(0) : 0;
+    const int cl = s.load_balance == G2_LB_WM
+                       ? cluster_size(0, k_bfs_cluster<16>, k_bfs_cluster<8>, 2 * (size_t)kClQcap * 4)
+                       : 0;
     // measured on road grids 1024^2..4096^2 with 16-CTA clusters: hand a
     // level to the grid above 16384 vertices, take it back below 8192
     a.lo = cl ? env_i32("G2_CLUSTER_LO", 512 * cl) : 0;
@@ -955,7 +822,9 @@ g2_status sssp_fused(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
     // the grid-wide loop, which hands back at a bucket boundary with at most
     // `lo_far` pile entries (never more than the next near list can start
     // with in the cluster, nor than the cluster's piles hold).
-    const int cl = s.load_balance == G2_LB_WM ? cluster_size(1) : 0;
+    const int cl = s.load_balance == G2_LB_WM
+                       ? cluster_size(1, k_sssp_cluster<16>, k_sssp_cluster<8>, kCsSmem)
+                       : 0;
     ClusterSsspArgs c;
     c.g = a.g;
     c.dist = dist;

@@ -419,6 +419,49 @@ def test_bc_level_spread_beyond_fp64(g2):
         assert bc_close(got, want)
 
 
+@pytest.mark.parametrize("cluster", ["default", "0", "64,32", "1,1"])
+def test_bc_fused_in_one_cluster(g2, grid, monkeypatch, cluster):
+    """Fused WM BC on symmetric bounded-degree graphs: the forward pass runs
+    small levels inside one thread-block cluster and large ones in the
+    grid-wide kernel, handing over at level boundaries (thresholds hi,lo
+    forced low to make many hand-overs); the backward pass runs ranges of
+    small / large levels on one or the other.  With the cluster switched off,
+    the grid-wide kernel alone (init + one launch per source).  A 31-ary tree,
+    whose last level (923,521 leaves) outgrows a CTA's buffer, rebuilds that
+    level's list from the depths.  Sums over several sources against the long
+    double oracle."""
+    if cluster == "0":
+        monkeypatch.setenv("G2_FUSED_CLUSTER", "0")
+    else:
+        monkeypatch.delenv("G2_FUSED_CLUSTER", raising=False)
+    if "," in cluster:
+        hi, lo = cluster.split(",")
+        monkeypatch.setenv("G2_CLUSTER_BC_HI", hi)
+        monkeypatch.setenv("G2_CLUSTER_BC_LO", lo)
+    else:
+        monkeypatch.delenv("G2_CLUSTER_BC_HI", raising=False)
+        monkeypatch.delenv("G2_CLUSTER_BC_LO", raising=False)
+    kids = np.arange(1, 1 + 31 + 961 + 29791 + 923521)
+    tree = gg.from_arcs(len(kids) + 1, (kids - 1) // 31, kids, name="tree31")
+    cases = [(grid, gg.random_sources(grid, 6, seed=7)), (gg.road_grid(300, seed=4), [0, 89999, 45150]),
+             (gg.path(4000), [0, 3999, 1234]), (gg.full_grid(200, 200), [0, 20100]), (tree, [0, 5])]
+    for g, srcs in cases:
+        srcs = np.asarray(srcs, dtype=np.int32)
+        want = oracle.bc_graph(g, srcs)
+        dg = g2.load_graph(g)
+        bc = dev(g.n, torch.float64)
+        g2.g2_bc(dg, srcs, bc, g2.schedule("WM", kernel_fusion=True))
+        assert bc_close(host(bc), want), g.name
+        st = g2.g2_last_stats()
+        if cluster == "0":
+            assert st["launches"] == 2 * len(srcs), (g.name, st)
+        elif cluster == "default" and g is not tree:
+            # every level fits: init, forward and (with two or more levels)
+            # backward in the cluster
+            want_l = sum(3 if oracle.bfs_graph(g, int(x))[0].max() >= 1 else 2 for x in srcs)
+            assert st["launches"] == want_l, (g.name, st)
+
+
 def test_bc_path_counts_beyond_fp64(g2):
     """Full 600x600 grid from a corner: path counts reach C(1198, 599) ~ 1e359,
     past fp64; per-level power-of-two rescaling keeps the result exact to
