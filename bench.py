@@ -437,7 +437,10 @@ def _timed(fn, reps=3):
 def run_grid_workload(args):
     """Road-like 4096 x 4096 grid (10% of lattice edges deleted, 1% local
     shortcuts, weights U[1, 1000], seed 1): delta-stepping SSSP plain vs fused
-    across deltas, BFS plain vs fused, from vertex 0 (a corner)."""
+    across deltas, BFS plain vs fused, single-source BC fused, from vertex 0
+    (a corner).  The fused WM loops run small levels in one thread-block
+    cluster; `*_grid_only` is the same schedule with the one-cluster loops
+    switched off (G2_FUSED_CLUSTER=0), the grid-wide kernel throughout."""
     import torch
     from paper_2012_07990_gb300 import build_native
     build_native.build()
@@ -451,26 +454,46 @@ def run_grid_workload(args):
     depth = torch.empty(G.n, dtype=torch.int32, device="cuda")
     res = {"sssp": [], "bfs": []}
     deg = G.degrees()
+    wm = g2.schedule("WM", kernel_fusion=True)
+
+    def grid_only(fn):
+        os.environ["G2_FUSED_CLUSTER"] = "0"
+        try:
+            return fn()
+        finally:
+            os.environ.pop("G2_FUSED_CLUSTER", None)
+
     for delta in (16, 64, 256, 1024, 4096, 16384):
         row = {"delta": delta}
         for name, s in (("plain_strict", g2.schedule("STRICT")),
                         ("fused_vertex", g2.schedule("VERTEX_BASED", kernel_fusion=True)),
-                        ("fused_wm", g2.schedule("WM", kernel_fusion=True))):
-            ms = _timed(lambda: g2.g2_sssp_delta(dg, 0, delta, dist, s), reps=2)
+                        ("fused_wm", wm), ("fused_wm_grid_only", wm)):
+            run = lambda: _timed(lambda: g2.g2_sssp_delta(dg, 0, delta, dist, s), reps=2)
+            ms = grid_only(run) if name.endswith("grid_only") else run()
             st = g2.g2_last_stats()
             row[name + "_ms"] = round(ms, 3)
             row[name + "_rounds"] = st["iterations"]
         reached = int(deg[dist.cpu().numpy() < 2**31 - 1].sum())
         row["gteps_best"] = round(reached / min(v for k, v in row.items() if k.endswith("_ms")) / 1e6, 3)
         res["sssp"].append(row)
-    for name, s in (("plain_tuned", None), ("plain_strict", g2.schedule("STRICT")),
+    for name, s in (("null_schedule", None), ("plain_strict", g2.schedule("STRICT")),
                     ("fused_vertex", g2.schedule("VERTEX_BASED", kernel_fusion=True)),
-                    ("fused_wm", g2.schedule("WM", kernel_fusion=True))):
-        ms = _timed(lambda: g2.g2_bfs(dg, 0, depth, None, s))
+                    ("fused_wm", wm), ("fused_wm_grid_only", wm)):
+        run = lambda: _timed(lambda: g2.g2_bfs(dg, 0, depth, None, s))
+        ms = grid_only(run) if name.endswith("grid_only") else run()
         st = g2.g2_last_stats()
         reached = int(deg[depth.cpu().numpy() >= 0].sum())
         res["bfs"].append({"schedule": name, "ms": round(ms, 3), "levels": st["iterations"],
                            "launches": st["launches"], "gteps": round(reached / ms / 1e6, 3)})
+    res["bc"] = []
+    bc = torch.empty(G.n, dtype=torch.float64, device="cuda")
+    reached = int(deg[depth.cpu().numpy() >= 0].sum())  # BFS from vertex 0 above
+    for name in ("fused_wm", "fused_wm_grid_only"):
+        run = lambda: _timed(lambda: g2.g2_bc(dg, [0], bc, wm), reps=2)
+        ms = grid_only(run) if name.endswith("grid_only") else run()
+        st = g2.g2_last_stats()
+        res["bc"].append({"schedule": name, "ms": round(ms, 3), "levels": st["iterations"],
+                          "launches": st["launches"], "gteps": round(2 * reached / ms / 1e6, 3)})
     print(json.dumps({"workload": f"grid{W}x{W}_sssp_bfs", "n": G.n, "m": G.m, **res}))
 
 
