@@ -288,27 +288,37 @@ def run_ours(args):
 
 
 def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
-    """Same metric through the public API with host buffers: the graph is
-    uploaded from pinned host memory, the three algorithms run, the results
-    (depth, label, rank) are read back to pinned host memory, every step."""
+    """Same metric through the public API with host buffers: every step
+    uploads the graph from pinned host memory (g2_load_csr, PageRank's layouts
+    prepared in the background), runs the three algorithms and reads the
+    results (depth, label, rank) back to pinned host memory.  The steps are
+    pipelined the way a stream of graphs would be served: a loader thread
+    uploads step k+1's graph on a stream of its own while step k computes
+    (two graphs resident), so the host link overlaps the kernels.  The timed
+    region holds every step's upload (the first one included), compute and
+    read-back; `serial_ms_per_step` is the same step run one after another."""
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     n, m = G.n, G.m
     h_rp = torch.from_numpy(G.rowptr).pin_memory()
     h_col = torch.from_numpy(G.col).pin_memory()
+    rp_np = np.frombuffer(h_rp.numpy().data, dtype=np.int32)
+    col_np = np.frombuffer(h_col.numpy().data, dtype=np.int32)
     h_depth = torch.empty(n, dtype=torch.int32).pin_memory()
     h_label = torch.empty(n, dtype=torch.int32).pin_memory()
     h_rank = torch.empty(n, dtype=torch.float32).pin_memory()
     depth = torch.empty(n, dtype=torch.int32, device="cuda")
     label = torch.empty(n, dtype=torch.int32, device="cuda")
     rank_t = torch.empty(n, dtype=torch.float32, device="cuda")
-
+    main = torch.cuda.current_stream()
     side = torch.cuda.Stream()
+    load_stream = torch.cuda.Stream()
 
-    def step():
-        # PageRank's layouts are built in the background while BFS and CC run
-        dg = g2.g2_load_csr(n, np.frombuffer(h_rp.numpy().data, dtype=np.int32),
-                            np.frombuffer(h_col.numpy().data, dtype=np.int32), None, True,
-                            prepare_pagerank=True)
+    def load():
+        return g2.g2_load_csr(n, rp_np, col_np, None, True, stream=load_stream,
+                              prepare_pagerank=True, overlap=True)
+
+    def compute(dg):
         g2.g2_bfs(dg, src, depth, None, sb)
         g2.g2_cc(dg, label, sc)
         # g2 calls return after their work completes: the BFS and CC results
@@ -318,22 +328,40 @@ def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
             h_label.copy_(label, non_blocking=True)
         g2.g2_pagerank(dg, DAMPING, PR_ITERS, rank_t)
         h_rank.copy_(rank_t, non_blocking=True)
-        torch.cuda.synchronize()
+        main.synchronize()
+        side.synchronize()
         dg.free()
 
-    step()
-    k = max(2, min(args.steps, 5))
+    k = max(3, min(args.steps, 6))
+    compute(load())  # warm-up
+    # one after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        compute(load())
+    serial_ms = (time.perf_counter() - t0) * 1e3 / 2
+    # pipelined: step k+1 uploads while step k computes
+    ex = ThreadPoolExecutor(1)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(k):
-        step()
+    t0 = time.perf_counter()
+    fut = ex.submit(load)
+    for i in range(k):
+        dg = fut.result()
+        if i + 1 < k:
+            fut = ex.submit(load)
+        compute(dg)
+    torch.cuda.synchronize()
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / k
+    wall_ms = (time.perf_counter() - t0) * 1e3 / k
+    ex.shutdown()
+    ms = max(e0.elapsed_time(e1) / k, wall_ms)
     return {"value": round(edges_per_step / (ms * 1e-3) / 1e9, 2), "unit": "GTEPS",
-            "ms_per_step": round(ms, 3), "steps": k,
+            "ms_per_step": round(ms, 3), "steps": k, "pipelined": True,
+            "serial_ms_per_step": round(serial_ms, 3),
             "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 12 * n}
 
 

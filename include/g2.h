@@ -52,6 +52,8 @@ typedef enum {
 #define G2_SYMMETRIC   0x1u  /* every arc u->v has v->u (then CSC aliases CSR) */
 #define G2_DEVICE_PTRS 0x2u  /* rowptr/col/w are device pointers (else host) */
 #define G2_PREPARE_PAGERANK 0x4u /* build PageRank's layouts in the background */
+#define G2_LOAD_OVERLAP 0x8u     /* the load runs beside other GPU work: the upload kernel
+                                    takes a quarter of the SMs and no copy engine */
 
 /* --------------------------------------------- schedule (Table II fields) */
 /* configLoadBalance load_balance_type */
@@ -117,7 +119,7 @@ typedef struct g2_graph g2_graph;
  *   rowptr   int32[n+1], rowptr[0] = 0, non-decreasing, rowptr[n] = m
  *   col      int32[m] arc heads; each list sorted ascending, no duplicates
  *   w        int32[m] arc weights (>= 1 for SSSP) or NULL
- *   flags    G2_SYMMETRIC | G2_DEVICE_PTRS | G2_PREPARE_PAGERANK
+ *   flags    G2_SYMMETRIC | G2_DEVICE_PTRS | G2_PREPARE_PAGERANK | G2_LOAD_OVERLAP
  *   stream   stream for the copies and validation
  *   out      receives the handle (library-owned; free with g2_free_graph)
  * The input arrays are copied; the caller may free them after return.  The
@@ -128,7 +130,11 @@ typedef struct g2_graph g2_graph;
  * reads it through the host page tables, as over the Grace-Blackwell
  * coherent link) and col / w are 16-byte aligned, one kernel reads, checks
  * and stores the arcs; otherwise they are copied with cudaMemcpyAsync and
- * checked after.  For a non-symmetric graph the transpose (CSC, lists sorted
+ * checked after.  G2_LOAD_OVERLAP (a load on its own stream while other
+ * calls run, e.g. the next graph of a stream of requests) runs that kernel
+ * on a quarter of the SMs, so the other calls keep the rest and the copy
+ * engines (their small per-round copies would otherwise wait behind the
+ * arcs' transfer).  For a non-symmetric graph the transpose (CSC, lists sorted
  * ascending) is built on the host for the PULL direction.  Device memory
  * comes from the library's stream-ordered pool (see g2_free_graph).
  * G2_PREPARE_PAGERANK: the layouts the tuned PageRank sweep needs (the

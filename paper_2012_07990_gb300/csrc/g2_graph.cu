@@ -129,65 +129,81 @@ __global__ void k_validate_cols(const int32_t *col, const int32_t *w, int32_t n,
 // memory, or pageable host memory on a device that reads it through the host
 // page tables (a coherent CPU-GPU link); the caller checks 16-byte alignment.
 // Four arcs per thread with 16-byte accesses; a warp covers 128 consecutive
-// arcs, and the id after a thread's last arc comes from the next lane.
-__global__ void __launch_bounds__(256) k_load_cols(const int32_t *src, const int32_t *wsrc,
-                                                   int32_t *dst, int32_t *wdst, int32_t n,
+// arcs per group, and the id after a thread's last arc comes from the next
+// lane.  A thread loads U groups before it checks and stores them, so a small
+// grid still keeps enough reads in flight to fill the host link.
+template <int U>
+__global__ void __launch_bounds__(256) k_load_cols(const int32_t *__restrict__ src,
+                                                   const int32_t *__restrict__ wsrc,
+                                                   int32_t *__restrict__ dst,
+                                                   int32_t *__restrict__ wdst, int32_t n,
                                                    int32_t m, const uint32_t *rowstart,
                                                    int32_t *bad) {
     const int lane = threadIdx.x & 31;
     const int64_t nq = ((int64_t)m + 3) / 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
     // warp-uniform trip count (base is a multiple of 32): the shuffle below
     // always has every lane present
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nq;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U; base < nq;
          base += stride) {
-        const int64_t q = base + lane, e0 = q * 4;
-        const bool inq = q < nq, full = e0 + 4 <= m;
-        int32_t c[4] = {0, 0, 0, 0}, wv[4] = {0, 0, 0, 0};
-        if (inq) {
-            if (full) {
-                const int4 v = *reinterpret_cast<const int4 *>(src + e0);
-                c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
-                if (wsrc) {
-                    const int4 x = *reinterpret_cast<const int4 *>(wsrc + e0);
-                    wv[0] = x.x; wv[1] = x.y; wv[2] = x.z; wv[3] = x.w;
+        int32_t c[U][4], wv[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t q = base + 32 * u + lane, e0 = q * 4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[u][k] = wv[u][k] = 0;
+            if (q < nq) {
+                if (e0 + 4 <= m) {
+                    const int4 v = *reinterpret_cast<const int4 *>(src + e0);
+                    c[u][0] = v.x; c[u][1] = v.y; c[u][2] = v.z; c[u][3] = v.w;
+                    if (wsrc) {
+                        const int4 x = *reinterpret_cast<const int4 *>(wsrc + e0);
+                        wv[u][0] = x.x; wv[u][1] = x.y; wv[u][2] = x.z; wv[u][3] = x.w;
+                    }
+                } else {
+                    for (int k = 0; k < 4; ++k)
+                        if (e0 + k < m) {
+                            c[u][k] = src[e0 + k];
+                            if (wsrc) wv[u][k] = wsrc[e0 + k];
+                        }
                 }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t q = base + 32 * u + lane, e0 = q * 4;
+            const bool inq = q < nq, full = e0 + 4 <= m;
+            int32_t nxt = __shfl_down_sync(G2_FULL, c[u][0], 1);
+            if (lane == 31 && inq && e0 + 4 < m) nxt = src[e0 + 4];
+            if (!inq) continue;
+            int code = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t e = e0 + k;
+                if (e >= m) break;
+                if (c[u][k] < 0 || c[u][k] >= n) code = 4;
+                const int64_t f = e + 1;
+                if (f < m) {
+                    const bool start = (rowstart[f >> 5] >> (f & 31)) & 1u;
+                    const int32_t cn = k < 3 ? c[u][k + 1] : nxt;
+                    if (!start && cn <= c[u][k]) code = code ? code : 5;
+                }
+                if (wsrc && wv[u][k] < 0) code = code ? code : 6;
+            }
+            if (full) {
+                *reinterpret_cast<int4 *>(dst + e0) = make_int4(c[u][0], c[u][1], c[u][2], c[u][3]);
+                if (wsrc)
+                    *reinterpret_cast<int4 *>(wdst + e0) =
+                        make_int4(wv[u][0], wv[u][1], wv[u][2], wv[u][3]);
             } else {
                 for (int k = 0; k < 4; ++k)
                     if (e0 + k < m) {
-                        c[k] = src[e0 + k];
-                        if (wsrc) wv[k] = wsrc[e0 + k];
+                        dst[e0 + k] = c[u][k];
+                        if (wsrc) wdst[e0 + k] = wv[u][k];
                     }
             }
+            if (code) atomicExch(bad, code);
         }
-        int32_t nxt = __shfl_down_sync(G2_FULL, c[0], 1);
-        if (lane == 31 && inq && e0 + 4 < m) nxt = src[e0 + 4];
-        if (!inq) continue;
-        int code = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t e = e0 + k;
-            if (e >= m) break;
-            if (c[k] < 0 || c[k] >= n) code = 4;
-            const int64_t f = e + 1;
-            if (f < m) {
-                const bool start = (rowstart[f >> 5] >> (f & 31)) & 1u;
-                const int32_t cn = k < 3 ? c[k + 1] : nxt;
-                if (!start && cn <= c[k]) code = code ? code : 5;
-            }
-            if (wsrc && wv[k] < 0) code = code ? code : 6;
-        }
-        if (full) {
-            *reinterpret_cast<int4 *>(dst + e0) = make_int4(c[0], c[1], c[2], c[3]);
-            if (wsrc) *reinterpret_cast<int4 *>(wdst + e0) = make_int4(wv[0], wv[1], wv[2], wv[3]);
-        } else {
-            for (int k = 0; k < 4; ++k)
-                if (e0 + k < m) {
-                    dst[e0 + k] = c[k];
-                    if (wsrc) wdst[e0 + k] = wv[k];
-                }
-        }
-        if (code) atomicExch(bad, code);
     }
 }
 
@@ -874,7 +890,7 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     if (n < 0 || n >= 2147483647 || m < 0 || m >= 2147483647LL)
         return fail(G2_EINVAL, "n or m out of range (must be < 2^31 - 1)");
     if (!rowptr || (m > 0 && !col)) return fail(G2_EINVAL, "null rowptr/col");
-    if (flags & ~(G2_SYMMETRIC | G2_DEVICE_PTRS | G2_PREPARE_PAGERANK))
+    if (flags & ~(G2_SYMMETRIC | G2_DEVICE_PTRS | G2_PREPARE_PAGERANK | G2_LOAD_OVERLAP))
         return fail(G2_EINVAL, "unknown flags");
     cudaStream_t st = as_stream(stream);
     const bool dev = flags & G2_DEVICE_PTRS;
@@ -919,7 +935,12 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     if ((e = cudaMemcpyAsync(t->rowptr, rowptr, ((size_t)n + 1) * 4, kind, st)) != cudaSuccess)
         return bail(cuda_fail(e, "copy rowptr"));
     // the arcs are read by the validating copy kernel itself where the device
-    // can address the caller's arrays; otherwise copied, then validated
+    // can address the caller's arrays; otherwise copied, then validated.  A
+    // load that overlaps other work runs the copy kernel on a quarter of the
+    // SMs (deeper per thread), leaving the rest, and the copy engines, to the
+    // other calls: their small per-round copies would wait behind the arcs'
+    // transfer on a copy engine.
+    const bool overlap = flags & G2_LOAD_OVERLAP;
     const int32_t *col_rd = m > 0 ? device_readable(col, dev, t->device) : nullptr;
     const int32_t *w_rd = (w && m > 0) ? device_readable(w, dev, t->device) : nullptr;
     const bool fused_copy = col_rd && (!w || w_rd);
@@ -944,15 +965,22 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
         cudaMemsetAsync(bad, 0, 4, st);
         k_validate_rows<<<(int)((n + 1 + 255) / 256), 256, 0, st>>>(t->rowptr, n, (int32_t)m,
                                                                    rowstart, bad);
-        if (m > 0 && fused_copy)
-            k_load_cols<<<t->sm_count * 8, 256, 0, st>>>(col_rd, w_rd, t->col, t->w, n, (int32_t)m,
-                                                         rowstart, bad);
+        if (m > 0 && fused_copy && overlap)
+            k_load_cols<4><<<std::max(1, t->sm_count / 4), 256, 0, st>>>(
+                col_rd, w_rd, t->col, t->w, n, (int32_t)m, rowstart, bad);
+        else if (m > 0 && fused_copy)
+            k_load_cols<1><<<t->sm_count * 8, 256, 0, st>>>(col_rd, w_rd, t->col, t->w, n,
+                                                            (int32_t)m, rowstart, bad);
         else if (m > 0)
             k_validate_cols<<<grid_for(g, m, 256), 256, 0, st>>>(t->col, t->w, n, (int32_t)m,
                                                                  rowstart, bad);
-        int32_t hbad = 0;
-        cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, st);
+        // into the handle's pinned counters: a copy to pageable memory would
+        // block inside the driver until the upload ends, stalling the CUDA
+        // calls of other host threads meanwhile
+        g->h_ctr[60] = 0;
+        cudaMemcpyAsync(g->h_ctr + 60, bad, 4, cudaMemcpyDeviceToHost, st);
         e = cudaStreamSynchronize(st);
+        const int32_t hbad = g->h_ctr[60];
         dfree(rowstart, st);
         dfree(bad, st);
         if (e != cudaSuccess) return bail(cuda_fail(e, "graph validation"));

@@ -764,9 +764,9 @@ static g2_status ensure_seg_layout(g2_graph *g, cudaStream_t st) {
     G2_CK(cudaMemsetAsync(t->seg_head, 0, words * 4, st));
     k_seg_heads<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->crowptr, n, t->seg_head, nz);
     G2_TRY(exclusive_scan_i32(g, nz, pos, n, st));
-    int32_t nnz = 0;
-    G2_CK(cudaMemcpyAsync(&nnz, pos + n, 4, cudaMemcpyDeviceToHost, st));
+    G2_CK(cudaMemcpyAsync(g->h_ctr + 60, pos + n, 4, cudaMemcpyDeviceToHost, st));
     G2_CK(cudaStreamSynchronize(st));
+    const int32_t nnz = g->h_ctr[60];
     G2_CK(dmalloc(&t->seg_nzrow, ((size_t)nnz + 1) * 4, st));
     k_seg_nzrow<<<grid_for(g, n, kCta), kCta, 0, st>>>(nz, pos, n, t->seg_nzrow);
     G2_CK(dmalloc(&t->seg_chunk_rank, ((size_t)nchunks + 1) * 4, st));

@@ -25,7 +25,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 G2_OK, G2_EINVAL, G2_ENOMEM, G2_ECUDA, G2_ETIMEOUT, G2_EUNSUPPORTED, G2_EOVERFLOW = range(7)
 STATUS_NAMES = {0: "G2_OK", 1: "G2_EINVAL", 2: "G2_ENOMEM", 3: "G2_ECUDA", 4: "G2_ETIMEOUT",
                 5: "G2_EUNSUPPORTED", 6: "G2_EOVERFLOW"}
-G2_SYMMETRIC, G2_DEVICE_PTRS, G2_PREPARE_PAGERANK = 0x1, 0x2, 0x4
+G2_SYMMETRIC, G2_DEVICE_PTRS, G2_PREPARE_PAGERANK, G2_LOAD_OVERLAP = 0x1, 0x2, 0x4, 0x8
 LB = {"VERTEX_BASED": 0, "CM": 1, "WM": 2, "STRICT": 3, "EDGE_ONLY": 4, "ETWC": 5, "TWC": 6}
 G2_PUSH, G2_PULL = 0, 1
 G2_BOOLMAP, G2_BITMAP = 0, 1
@@ -179,10 +179,12 @@ class Graph:
 
 
 def g2_load_csr(n, rowptr, col, w=None, symmetric=True, stream=None,
-                prepare_pagerank=False) -> Graph:
+                prepare_pagerank=False, overlap=False) -> Graph:
     """Copy a CSR graph to the device.  rowptr/col/w: numpy int32 (host) or
     torch int32 CUDA tensors (device).  prepare_pagerank: build PageRank's
-    layouts in the background (G2_PREPARE_PAGERANK)."""
+    layouts in the background (G2_PREPARE_PAGERANK).  overlap: the load runs
+    beside other GPU work (G2_LOAD_OVERLAP: the upload kernel on a quarter of
+    the SMs, no copy engine for the arcs)."""
     dev = not isinstance(rowptr, np.ndarray)
     if not dev:
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
@@ -191,7 +193,7 @@ def g2_load_csr(n, rowptr, col, w=None, symmetric=True, stream=None,
             w = np.ascontiguousarray(w, dtype=np.int32)
     m = int(col.shape[0])
     flags = (G2_SYMMETRIC if symmetric else 0) | (G2_DEVICE_PTRS if dev else 0) | \
-        (G2_PREPARE_PAGERANK if prepare_pagerank else 0)
+        (G2_PREPARE_PAGERANK if prepare_pagerank else 0) | (G2_LOAD_OVERLAP if overlap else 0)
     h = ctypes.c_void_p()
     _check(_lib.g2_load_csr(int(n), m, _ptr(rowptr), _ptr(col), _ptr(w), flags, _stream(stream),
                             ctypes.byref(h)), "g2_load_csr")

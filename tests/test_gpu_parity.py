@@ -765,6 +765,8 @@ def test_load_paths_and_memory_reuse(g2, rmat14):
     pw = torch.from_numpy(w).pin_memory()
     as_np = lambda t: np.frombuffer(t.numpy().data, dtype=np.int32)
     check(g2.g2_load_csr(g.n, as_np(prp), as_np(pcl), as_np(pw), True))
+    # the same through the copy engines (a load that overlaps other work)
+    check(g2.g2_load_csr(g.n, as_np(prp), as_np(pcl), as_np(pw), True, overlap=True))
     # 4-byte misaligned host views of the same data
     buf = np.empty(g.m + 1, np.int32)
     col_mis = buf[1:]
@@ -781,9 +783,10 @@ def test_load_paths_and_memory_reuse(g2, rmat14):
     bad = g.col.copy()
     bad[g.m // 2 + 3] = g.n  # id out of range
     for c in (as_np(torch.from_numpy(bad).pin_memory()), np.concatenate([np.zeros(1, np.int32), bad])[1:]):
-        with pytest.raises(g2.G2Error) as e:
-            g2.g2_load_csr(g.n, g.rowptr, c, None, True)
-        assert e.value.status == g2.G2_EINVAL
+        for ov in (False, True):
+            with pytest.raises(g2.G2Error) as e:
+                g2.g2_load_csr(g.n, g.rowptr, c, None, True, overlap=ov)
+            assert e.value.status == g2.G2_EINVAL
     wneg = w.copy()
     wneg[g.m - 1] = -1  # negative weight in the ragged tail
     with pytest.raises(g2.G2Error) as e:
