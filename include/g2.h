@@ -334,7 +334,8 @@ typedef struct {
     int32_t iterations;     /* frontier rounds (or PR rounds, CC rounds, buckets) */
     int32_t push_rounds;    /* rounds run PUSH */
     int32_t pull_rounds;    /* rounds run PULL */
-    int32_t launches;       /* kernels launched */
+    int32_t launches;       /* kernels launched (not counting the one-warp kernels that
+                               store a call's few host-side values, e.g. the source) */
     int64_t arcs_examined;  /* arcs read by the traversal (0 unless counted) */
     int32_t barriers;       /* grid or cluster barriers passed in fused kernels */
     int32_t reserved;

@@ -433,9 +433,7 @@ g2_status sssp_plain(g2_graph *g, int32_t src, int32_t delta, int32_t *dist, con
     }
     k_fill_i32<<<grid_for(g, n, kCta), kCta, 0, st>>>(dist, n, G2_INF32);
     int32_t zero = 0, one = 1;
-    G2_CK(cudaMemcpyAsync(dist + src, &zero, 4, cudaMemcpyHostToDevice, st));
-    G2_CK(cudaMemcpyAsync(nq[0], &src, 4, cudaMemcpyHostToDevice, st));
-    G2_CK(cudaMemcpyAsync(ctrs + 0, &one, 4, cudaMemcpyHostToDevice, st));
+    G2_TRY(put_i32(st, {{dist + src, zero}, {nq[0], src}, {ctrs + 0, one}}));
     stats().launches += 1;
     int64_t T = delta;  // bucket 0 = [0, delta)
     int fp = 0;
@@ -484,7 +482,7 @@ g2_status sssp_plain(g2_graph *g, int32_t src, int32_t delta, int32_t *dist, con
         if (nfar == 0) break;
         int32_t Told = (int32_t)std::min<int64_t>(T, G2_INF32);
         int32_t inf = G2_INF32;
-        G2_CK(cudaMemcpyAsync(ctrs + 6, &inf, 4, cudaMemcpyHostToDevice, st));
+        G2_TRY(put_i32(st, {{ctrs + 6, inf}}));
         k_far_min<<<grid_for(g, nfar, kCta), kCta, 0, st>>>(far[fp], nfar, dist, Told, ctrs + 6);
         G2_TRY(read_counters(g, ctrs, 8, st, d_err));
         int32_t dmin = g->h_ctr[6];

@@ -211,7 +211,7 @@ static g2_status bfs_batch_fused(g2_graph *g, const int32_t *srcs, int32_t k, in
     G2_CK(cudaMemsetAsync(a.F[0], 0, (size_t)n * 8, st));
     G2_CK(cudaMemsetAsync(a.F[1], 0, (size_t)n * 8, st));
     G2_CK(cudaMemsetAsync(depth, 0xFF, (size_t)k * n * 4, st));
-    G2_CK(cudaMemcpyAsync(dsrc, srcs, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    G2_TRY(put_array(dsrc, srcs, k, st));
     a.cnt = ctrs + 20;  // [20..22]; zero from begin_call
     a.levels = ctrs + 24;
     k_ms_seed<<<1, 64, 0, st>>>(dsrc, k, a.visit, a.F[0], depth, n, a.list[0], a.cnt);
@@ -250,7 +250,7 @@ g2_status bfs_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *de
     G2_CK(cudaMemsetAsync(F[0], 0, (size_t)n * 8, st));
     G2_CK(cudaMemsetAsync(F[1], 0, (size_t)n * 8, st));
     G2_CK(cudaMemsetAsync(depth, 0xFF, (size_t)k * n * 4, st));
-    G2_CK(cudaMemcpyAsync(dsrc, srcs, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    G2_TRY(put_array(dsrc, srcs, k, st));
     k_ms_seed<<<1, 64, 0, st>>>(dsrc, k, visit, F[0], depth, n, list[0], ctrs + 0);
     stats().launches += 1;
     G2_TRY(read_counters(g, ctrs, 4, st, d_err));
@@ -567,13 +567,13 @@ static g2_status sssp_batch_fused(g2_graph *g, const int32_t *srcs, int32_t k, i
     for (int i = 0; i < 3; ++i) G2_CK(cudaMemsetAsync(a.M[i], 0, (size_t)n * 4, st));
     G2_CK(cudaMemsetAsync(a.far, 0, (size_t)n * 4, st));
     k_fill_i32_b<<<grid_for(g, (int64_t)k * n, kCta), kCta, 0, st>>>(dist, (int64_t)k * n, G2_INF32);
-    G2_CK(cudaMemcpyAsync(dsrc, srcs, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    G2_TRY(put_array(dsrc, srcs, k, st));
     a.ncnt = ctrs + 36;   // [36..38], zero from begin_call
     a.fcnt = ctrs + 39;   // [39..40]
     a.dmin = ctrs + 41;   // [41..42]
     a.result = ctrs + 43; // [43..44]
     const int32_t inf = G2_INF32;
-    G2_CK(cudaMemcpyAsync(a.dmin, &inf, 4, cudaMemcpyHostToDevice, st));
+    G2_TRY(put_i32(st, {{a.dmin, inf}}));
     k_msr_seed<<<1, 32, 0, st>>>(dsrc, k, dist, n, a.M[0], a.NL[0], a.ncnt);
     a.delta = delta;
     a.bar = GridBarrier{reinterpret_cast<unsigned long long *>(ctrs + 28)};
@@ -612,7 +612,7 @@ g2_status sssp_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t de
     G2_CK(cudaMemsetAsync(M[1], 0, (size_t)n * 4, st));
     G2_CK(cudaMemsetAsync(far, 0, (size_t)n * 4, st));
     k_fill_i32_b<<<grid_for(g, (int64_t)k * n, kCta), kCta, 0, st>>>(dist, (int64_t)k * n, G2_INF32);
-    G2_CK(cudaMemcpyAsync(dsrc, srcs, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    G2_TRY(put_array(dsrc, srcs, k, st));
     k_msr_seed<<<1, 32, 0, st>>>(dsrc, k, dist, n, M[0], nl[0], ctrs + 0);
     stats().launches += 2;
     G2_TRY(read_counters(g, ctrs, 8, st, d_err));
@@ -658,7 +658,7 @@ g2_status sssp_batch_run(g2_graph *g, const int32_t *srcs, int32_t k, int32_t de
         if (!bucketed || nfar == 0) break;
         int32_t Told = (int32_t)std::min<int64_t>(T, G2_INF32);
         int32_t inf = G2_INF32;
-        G2_CK(cudaMemcpyAsync(ctrs + 6, &inf, 4, cudaMemcpyHostToDevice, st));
+        G2_TRY(put_i32(st, {{ctrs + 6, inf}}));
         k_msr_far_min<<<grid_for(g, nfar, kCta), kCta, 0, st>>>(fl[fp], nfar, far, dist, n, Told,
                                                                ctrs + 6);
         G2_TRY(read_counters(g, ctrs, 8, st, d_err));

@@ -618,8 +618,7 @@ static g2_status bc_one_fused(g2_graph *g, const BcState &s, const g2_schedule &
     a.result = ctrs + 24;
     k_bc_init<<<grid_for(g, n, kCta), kCta, 0, st>>>(s, n, ctrs + 20);
     stats().launches += 1;
-    int32_t init_off[2] = {0, 1};
-    G2_CK(cudaMemcpyAsync(a.off, init_off, 8, cudaMemcpyHostToDevice, st));
+    G2_TRY(put_i32(st, {{a.off, 0}, {a.off + 1, 1}}));
     G2_CK(cudaMemsetAsync(ctrs + 28, 0, 8, st));  // barrier words
     G2_TRY(launch_bc_grid(g, sc, a, st));
     G2_TRY(read_counters(g, ctrs + 24, 2, st, d_err));
@@ -695,8 +694,7 @@ static g2_status bc_one_cluster(g2_graph *g, const BcState &s, const g2_schedule
                 count = g->h_ctr[0];
             }
         } else {
-            int32_t o2[2] = {start, start + count};
-            G2_CK(cudaMemcpyAsync(off + level, o2, 8, cudaMemcpyHostToDevice, st));
+            G2_TRY(put_i32(st, {{off + level, start}, {off + level + 1, start + count}}));
             G2_CK(cudaMemsetAsync(a.cnt3, 0, 12, st));
             a.fwd = 1;
             a.bwd = 0;

@@ -711,10 +711,8 @@ g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     if (parent) G2_CK(cudaMemsetAsync(parent, 0xFF, (size_t)n * 4, st));
     G2_CK(cudaMemsetAsync(depth, 0xFF, (size_t)n * 4, st));
     int32_t zero = 0, one = 1;
-    G2_CK(cudaMemcpyAsync(depth + src, &zero, 4, cudaMemcpyHostToDevice, st));
-    if (parent) G2_CK(cudaMemcpyAsync(parent + src, &src, 4, cudaMemcpyHostToDevice, st));
-    G2_CK(cudaMemcpyAsync(a.q[0], &src, 4, cudaMemcpyHostToDevice, st));
-    G2_CK(cudaMemcpyAsync(a.cnt, &one, 4, cudaMemcpyHostToDevice, st));
+    G2_TRY(put_i32(st, {{depth + src, zero}, {parent ? parent + src : nullptr, src}, {a.q[0], src},
+                        {a.cnt, one}}));
     // WM rounds start in one cluster and move between it and the grid-wide
     // loop as the levels grow and shrink; the other strategies (and a device
     // without room for the cluster) run the grid-wide loop throughout.
@@ -812,12 +810,11 @@ g2_status sssp_fused(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
     a.limit_ns = barrier_limit_ns();
     a.ctr = nullptr;
     if (count_arcs_enabled()) G2_TRY(ws(g, B_ARCS, 2, &a.ctr));
-    int32_t init[8] = {1, 0, 0, 0, 0, G2_INF32, G2_INF32, 0};  // ncnt[3], fcnt[2], dmin[2]
-    G2_CK(cudaMemcpyAsync(ctrs + 20, init, 7 * 4, cudaMemcpyHostToDevice, st));
+    // ncnt[3] = {1, 0, 0}, fcnt[2] = 0 (counters are zero at entry), dmin[2] = inf
+    G2_TRY(put_i32(st, {{ctrs + 20, 1}, {ctrs + 25, G2_INF32}, {ctrs + 26, G2_INF32}}));
     k_fill_dist<<<grid_for(g, n, kCta), kCta, 0, st>>>(dist, n);
     int32_t zero = 0;
-    G2_CK(cudaMemcpyAsync(dist + src, &zero, 4, cudaMemcpyHostToDevice, st));
-    G2_CK(cudaMemcpyAsync(a.nq[0], &src, 4, cudaMemcpyHostToDevice, st));
+    G2_TRY(put_i32(st, {{dist + src, zero}, {a.nq[0], src}}));
     // WM buckets start in one cluster; near rounds above `hi` vertices move to
     // the grid-wide loop, which hands back at a bucket boundary with at most
     // `lo_far` pile entries (never more than the next near list can start
@@ -870,8 +867,8 @@ g2_status sssp_fused(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
             if (r + e == 0) return fail(G2_ECUDA, "cluster SSSP made no progress");
             if (why == CL_OVERFLOW) {
                 // near list and pile of the bucket below T from the distances
-                const int32_t reset[7] = {0, 0, 0, 0, 0, G2_INF32, G2_INF32};
-                G2_CK(cudaMemcpyAsync(ctrs + 20, reset, 7 * 4, cudaMemcpyHostToDevice, st));
+                G2_TRY(put_i32(st, {{ctrs + 20, 0}, {ctrs + 21, 0}, {ctrs + 22, 0}, {ctrs + 23, 0},
+                                    {ctrs + 24, 0}, {ctrs + 25, G2_INF32}, {ctrs + 26, G2_INF32}}));
                 ++epoch0;
                 k_sssp_rebuild<<<grid_for(g, n, kCta), kCta, 0, st>>>(
                     dist, n, T, delta, a.nq[0], a.ncnt, a.fq[0], a.fcnt, a.stamp2, epoch0, d_err);

@@ -539,6 +539,50 @@ g2_status read_counters(g2_graph *g, const int32_t *d, int count, cudaStream_t s
     return sync_and_check(g, st, d_err);
 }
 
+struct PutArgs {
+    int32_t *dst[kPutMax];
+    int32_t val[kPutMax];
+};
+struct PutArrayArgs {
+    int32_t *dst;
+    int32_t count;
+    int32_t val[kPutArrayMax];
+};
+__global__ void k_put(PutArgs a) {
+    const int i = threadIdx.x;
+    if (i < kPutMax && a.dst[i]) *a.dst[i] = a.val[i];
+}
+__global__ void k_put_array(PutArrayArgs a) {
+    for (int i = threadIdx.x; i < a.count; i += blockDim.x) a.dst[i] = a.val[i];
+}
+
+g2_status put_i32(cudaStream_t st, std::initializer_list<PutItem> items) {
+    if (items.size() > (size_t)kPutMax) return fail(G2_EINVAL, "too many values for put_i32");
+    PutArgs a;
+    memset(&a, 0, sizeof(a));
+    int i = 0;
+    for (const PutItem &it : items) {
+        a.dst[i] = it.dst;
+        a.val[i] = it.val;
+        ++i;
+    }
+    k_put<<<1, 32, 0, st>>>(a);
+    G2_CK(cudaGetLastError());
+    return G2_OK;
+}
+
+g2_status put_array(int32_t *dst, const int32_t *src, int count, cudaStream_t st) {
+    if (count < 0 || count > kPutArrayMax) return fail(G2_EINVAL, "too many values for put_array");
+    if (count == 0) return G2_OK;
+    PutArrayArgs a;
+    a.dst = dst;
+    a.count = count;
+    memcpy(a.val, src, (size_t)count * 4);
+    k_put_array<<<1, 256, 0, st>>>(a);
+    G2_CK(cudaGetLastError());
+    return G2_OK;
+}
+
 g2_status exclusive_scan_i32(g2_graph *g, const int32_t *in, int32_t *out, int32_t count,
                              cudaStream_t st) {
     int32_t ntiles = (int32_t)((count + (int64_t)kScanTile - 1) / kScanTile);
@@ -1150,7 +1194,7 @@ g2_status g2_frontier_set(g2_frontier *f, const int32_t *verts, int32_t k, void 
             f->cap = k;
         }
         if (k > 0) G2_CK(cudaMemcpyAsync(f->q, tmp, (size_t)k * 4, cudaMemcpyDeviceToDevice, st));
-        G2_CK(cudaMemcpyAsync(f->cnt, &src.size, 4, cudaMemcpyHostToDevice, st));
+        G2_TRY(put_i32(st, {{f->cnt, src.size}}));
     } else {
         VSet dst{f->format == G2_FRONTIER_BITMAP ? (int)OUT_BITMAP : (int)OUT_BOOLMAP, nullptr, 0,
                  nullptr, f->bitmap, f->boolmap, 0};

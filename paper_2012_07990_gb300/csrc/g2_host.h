@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <initializer_list>
 #include <mutex>
 #include <thread>
 #include <cstdlib>
@@ -189,6 +190,20 @@ g2_status end_call(g2_graph *g, cudaStream_t st, int32_t *d_err);
 // Read `count` device int32 counters into g->h_ctr (synchronises) and check
 // the error word.
 g2_status read_counters(g2_graph *g, const int32_t *d, int count, cudaStream_t st, int32_t *d_err);
+
+// Small host values stored to device memory by a one-warp kernel that takes
+// them as launch arguments: no copy reads host memory, so nothing waits for a
+// pageable staging copy or for a copy engine busy with another call's
+// transfer.  put_i32: up to kPutMax (address, value) pairs (null addresses
+// skipped); put_array: count <= kPutArrayMax consecutive values.
+constexpr int kPutMax = 8;
+constexpr int kPutArrayMax = 256;
+struct PutItem {
+    int32_t *dst;
+    int32_t val;
+};
+g2_status put_i32(cudaStream_t st, std::initializer_list<PutItem> items);
+g2_status put_array(int32_t *dst, const int32_t *src, int count, cudaStream_t st);
 
 // COO source array of the CSR arcs (built on first use).
 g2_status ensure_coo(g2_graph *g, cudaStream_t st);
