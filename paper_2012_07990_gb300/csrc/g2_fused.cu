@@ -381,7 +381,10 @@ __global__ void __launch_bounds__(kClCta, 1) k_bfs_cluster(ClusterBfsArgs a) {
 // slice of the cluster's near list (read through distributed shared memory),
 // four arcs per lane in flight; an improvement below the bucket threshold
 // joins the CTA's next near list, one at or above it joins the CTA's far pile
-// (deduplicated per round / epoch by the same stamps as the grid loop).  When
+// (deduplicated per round / epoch by the same stamps as the grid loop; on a
+// bounded-degree graph the near lists skip the stamp, whose atomic would sit
+// on every round's chain: a vertex improved twice in a round is then relaxed
+// twice in the next, with its current distance both times).  When
 // the near list empties, every CTA takes the smallest live distance of its
 // own pile, the cluster minimum (read through distributed shared memory)
 // fixes the next bucket, and each CTA splits its own pile into its near list
@@ -414,6 +417,7 @@ struct ClusterSsspArgs {
     int32_t *stamp2;         // far dedup: the pile of epoch e carries epoch0 + e
     int32_t epoch0;
     int32_t hi;              // stop before a near round with more vertices
+    int32_t dedup_near;      // 0: near lists keep repeats (bounded-degree graphs)
     int32_t *nq_out;         // hand-over: near list ...
     int32_t *fq_out;         // ... and far pile for the grid loop
     int32_t *ncnt;           // the grid loop's near lengths [3], far lengths [2],
@@ -570,7 +574,7 @@ __global__ void __launch_bounds__(kClCta, 1) k_sssp_cluster(ClusterSsspArgs a) {
                         const bool better = v[j] >= 0 && nv[j] < old[j];
                         bool to_near = better && nv[j] < T;
                         bool to_far = better && nv[j] >= T;
-                        if (to_near) to_near = atomicExch(a.stamp + v[j], rid) != rid;
+                        if (to_near && a.dedup_near) to_near = atomicExch(a.stamp + v[j], rid) != rid;
                         if (to_far) to_far = atomicExch(a.stamp2 + v[j], eid) != eid;
                         cta_append(nxt, &s_ncnt[nb], kCsQn, v[j], to_near, lane);
                         cta_append(far, &s_fcnt[fp], kCsQf, v[j], to_far, lane);
@@ -829,6 +833,9 @@ g2_status sssp_fused(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
     c.stamp = a.stamp;
     c.stamp2 = a.stamp2;
     c.hi = env_i32("G2_CLUSTER_HI", 1024 * cl);
+    int32_t dmax = 0;
+    if (cl) G2_TRY(max_out_degree(g, st, &dmax));
+    c.dedup_near = !(t->symmetric && dmax <= kBoundedDegree);
     c.nq_out = a.nq[0];
     c.fq_out = a.fq[0];
     c.ncnt = a.ncnt;
