@@ -833,6 +833,48 @@ def test_diag_gather_sums_and_rejects_bad_indices(g2):
     assert e.value.status == g2.G2_EINVAL
 
 
+def test_pipelined_overlapped_loads(g2, rmat14):
+    """A stream of requests served the way bench.py's end-to-end line is: a
+    loader thread uploads graph k+1 (pinned host arrays, G2_LOAD_OVERLAP, its
+    own stream, PageRank preparation in the background) while BFS, CC and
+    PageRank of graph k run on the caller's stream.  Every graph gives the
+    oracle's results; two different graphs alternate so that a mix-up of the
+    resident graphs would show."""
+    from concurrent.futures import ThreadPoolExecutor
+    ga, gb = rmat14, gg.road_grid(160, seed=9)
+    want = {}
+    for g in (ga, gb):
+        want[g.name] = (oracle.bfs_graph(g, 3)[0], oracle.cc_graph(g), oracle.pagerank_graph(g, 0.85, 20))
+    pinned = {}
+    for g in (ga, gb):
+        rp = torch.from_numpy(g.rowptr).pin_memory()
+        cl = torch.from_numpy(g.col).pin_memory()
+        pinned[g.name] = (rp, cl, np.frombuffer(rp.numpy().data, dtype=np.int32),
+                          np.frombuffer(cl.numpy().data, dtype=np.int32))
+    side = torch.cuda.Stream()
+
+    def load(g):
+        _, _, rp, cl = pinned[g.name]
+        return g2.g2_load_csr(g.n, rp, cl, None, True, stream=side, prepare_pagerank=True,
+                              overlap=True), g
+
+    order = [ga, gb, ga, gb, gb, ga]
+    with ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(load, order[0])
+        for i in range(len(order)):
+            dg, g = fut.result()
+            if i + 1 < len(order):
+                fut = ex.submit(load, order[i + 1])
+            d, lab, r = dev(g.n), dev(g.n), dev(g.n, torch.float32)
+            g2.g2_bfs(dg, 3, d, None, None)
+            g2.g2_cc(dg, lab, None)
+            g2.g2_pagerank(dg, 0.85, 20, r)
+            od, ol, opr = want[g.name]
+            assert np.array_equal(host(d), od) and np.array_equal(host(lab), ol), (i, g.name)
+            assert np.abs(host(r).astype(np.float64) - opr).sum() <= PR_L1, (i, g.name)
+            dg.free()
+
+
 def test_background_pagerank_preparation(g2, rmat14):
     """G2_PREPARE_PAGERANK: PageRank's layouts are built by a background thread
     on its own stream while BFS and CC run on the caller's; PageRank waits for
