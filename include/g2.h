@@ -259,9 +259,12 @@ g2_status g2_cc(g2_graph *g, int32_t *label, const g2_hybrid *sched, void *strea
 /* Delta-stepping SSSP with a two-bucket (near/far) priority queue
  * (Sec. III and V, configDelta): dist int32[n] device, INT32_MAX unreachable.
  * delta > 0 overrides the schedule's delta.  Needs weights >= 1.
- * G2_EOVERFLOW if a distance would reach INT32_MAX.  NULL schedule: STRICT
- * PUSH, unfused; fused WM PUSH on a bounded-degree graph (largest out-degree
- * <= 32). */
+ * G2_EOVERFLOW if a distance would reach INT32_MAX.  With kernel fusion and
+ * WM, buckets run inside one thread-block cluster (near lists and far piles in
+ * shared memory) while near rounds hold at most 1,024 vertices per cluster CTA,
+ * and in the grid-wide kernel otherwise (back at a bucket boundary with a
+ * small far pile), one launch per hand-over.  NULL schedule: STRICT PUSH,
+ * unfused; fused WM PUSH on a bounded-degree graph (largest out-degree <= 32). */
 g2_status g2_sssp_delta(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
                         const g2_hybrid *sched, void *stream);
 
@@ -280,7 +283,10 @@ g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, float *rank,
  * are extended-range floats (fp64 mantissa, int32 exponent per vertex), so
  * they neither overflow nor underflow on high-diameter graphs.  Each level's
  * discovery follows the (hybrid) schedule; with kernel fusion each source
- * runs in one persistent cooperative kernel.  NULL schedule: the
+ * runs in one persistent cooperative kernel, and with fused WM on a symmetric
+ * bounded-degree graph the levels of at most 256 vertices per cluster CTA run
+ * inside one thread-block cluster (forward and backward), the larger ones in
+ * the grid-wide kernel.  NULL schedule: the
  * direction-optimising hybrid of g2_bfs; fused WM PUSH on a bounded-degree
  * graph (largest out-degree <= 32). */
 g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc,
