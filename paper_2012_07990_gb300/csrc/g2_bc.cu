@@ -9,14 +9,18 @@
 // Path counts grow like binomials on grids (C(2k, k) after 2k levels) and two
 // vertices of one level can differ by more than the fp64 range, so sigma is an
 // extended-range float: an fp64 mantissa in [0.5, 1) and an int32 exponent per
-// vertex.  Dependency ratios sigma_v / sigma_w are <= 1 and are formed as
-// ldexp(m_v / m_w, e_v - e_w).
+// vertex.  The dependency sum delta_v = sum_w sigma_v / sigma_w (1 + delta_w)
+// is formed as m_v * sum_w c_w 2^(e_v - e_w) with c_w = (1 + delta_w) / m_w
+// kept per vertex (one fp64 division per vertex, when its sigma is known),
+// so an arc costs a power-of-two scaling and an add (fp64 is slow on this
+// GPU).
 //
 // Schedules: each level's discovery is one edgeset.apply round (PUSH or PULL
 // per the hybrid schedule); with kernel fusion the whole source runs in one
-// persistent cooperative kernel with three grid barriers per level.  The
-// sigma and delta pulls give a warp to every vertex and a whole CTA to the
-// vertices with at least kBigDeg arcs.
+// persistent cooperative kernel with one grid barrier per level and pass.
+// The sigma and delta pulls give a warp to every vertex and a whole CTA to
+// the vertices with at least kBigDeg arcs, or a thread to every vertex on a
+// symmetric bounded-degree graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,13 +40,17 @@ struct BigF {
     int e;
 };
 
-__device__ __forceinline__ BigF bf_make(double m, int e) {
-    if (m == 0.0) return BigF{0.0, 0};
-    int k;
-    double f = frexp(m, &k);
-    return BigF{f, e + k};
+// x * 2^k for k <= 1023, by a multiply with the power of two built from its
+// exponent bits; 0 below 2^-1022 (a term that small is below the rounding of
+// every sum it joins).
+__device__ __forceinline__ double scale2(double x, int k) {
+    if (k < -1022) return 0.0;
+    return x * __hiloint2double((k + 1023) << 20, 0);
 }
 
+// a + b: the smaller operand scaled to the larger one's exponent (exactly, or
+// dropped when it lies below half an ulp of the larger), the sum in [0.5, 2)
+// brought back into [0.5, 1) — the value frexp / ldexp give, without them.
 __device__ __forceinline__ BigF bf_add(BigF a, BigF b) {
     if (a.m == 0.0) return b;
     if (b.m == 0.0) return a;
@@ -51,9 +59,14 @@ __device__ __forceinline__ BigF bf_add(BigF a, BigF b) {
         a = b;
         b = t;
     }
-    int d = a.e - b.e;
-    double s = a.m + (d > 1100 ? 0.0 : ldexp(b.m, -d));
-    return bf_make(s, a.e);
+    const int d = a.e - b.e;
+    double s = d > 60 ? a.m : a.m + scale2(b.m, -d);
+    int e = a.e;
+    if (s >= 1.0) {
+        s *= 0.5;
+        ++e;
+    }
+    return BigF{s, e};
 }
 
 __device__ __forceinline__ BigF bf_shfl_xor(BigF a, int d) {
@@ -65,7 +78,10 @@ struct BcState {
     int32_t *depth;
     double *sm;  // sigma mantissas
     int32_t *se; // sigma exponents
-    double *delta;
+    // (1 + delta_v) / m_v: 1 / m_v once sigma_v is known, then (1 + delta_v) /
+    // m_v once delta_v is, so that delta_u = m_u * sum over successors w of
+    // coef_w * 2^(e_u - e_w): per arc a scaling and an add, no division
+    double *coef;
     double *bc;
     int32_t *lvl;  // all levels, in order
     int32_t src;
@@ -87,17 +103,32 @@ __device__ __forceinline__ BigF bc_sigma_part(const BcState &s, int32_t w, int32
     return acc;
 }
 
-// delta of vertex v at level d: sum over out-neighbours w at level d+1
+// delta of vertex v at level d, over its out-neighbours w at level d+1:
+// the sum of coef_w * 2^(e_v - e_w) (bc_finish_delta multiplies by m_v)
 __device__ __forceinline__ double bc_delta_part(const BcState &s, int32_t v, int32_t d, int32_t b,
                                                 int32_t e, int32_t step, int32_t off) {
-    const double mv = s.sm[v];
     const int ev = s.se[v];
     double acc = 0.0;
     for (int32_t k = b + off; k < e; k += step) {
         int32_t w = s.g.col[k];
-        if (s.depth[w] == d + 1) acc += ldexp(mv / s.sm[w], ev - s.se[w]) * (1.0 + s.delta[w]);
+        if (s.depth[w] == d + 1) acc += scale2(s.coef[w], ev - s.se[w]);
     }
     return acc;
+}
+
+// delta_v from the sum of its successors' terms: added to bc (but for the
+// source) and kept as the coefficient the level above uses
+__device__ __forceinline__ void bc_finish_delta(const BcState &s, int32_t v, double sum) {
+    const double dl = s.sm[v] * sum;
+    if (v != s.src) s.bc[v] += dl;
+    s.coef[v] *= 1.0 + dl;
+}
+
+// sigma_v found: stored, and 1 / m_v as the first coefficient
+__device__ __forceinline__ void bc_finish_sigma(const BcState &s, int32_t v, BigF a) {
+    s.sm[v] = a.m;
+    s.se[v] = a.e;
+    s.coef[v] = 1.0 / a.m;
 }
 
 // The same sums for one thread over a whole (short) list, four arcs' loads in
@@ -124,7 +155,6 @@ __device__ __forceinline__ BigF bc_sigma_thread(const BcState &s, int32_t w, int
 
 __device__ __forceinline__ double bc_delta_thread(const BcState &s, int32_t v, int32_t d) {
     const int32_t b = s.g.rowptr[v], e = s.g.rowptr[v + 1];
-    const double mv = s.sm[v];
     const int ev = s.se[v];
     double acc = 0.0;
     for (int32_t k = b; k < e; k += 4) {
@@ -133,18 +163,17 @@ __device__ __forceinline__ double bc_delta_thread(const BcState &s, int32_t v, i
         for (int j = 0; j < 4; ++j) w[j] = k + j < e ? s.g.col[k + j] : -1;
 #pragma unroll
         for (int j = 0; j < 4; ++j) dw[j] = w[j] >= 0 ? s.depth[w[j]] : -2;
-        double mw[4], dl[4];
+        double cw[4];
         int ew[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const bool on = dw[j] == d + 1;
-            mw[j] = on ? s.sm[w[j]] : 1.0;
+            cw[j] = on ? s.coef[w[j]] : 0.0;
             ew[j] = on ? s.se[w[j]] : 0;
-            dl[j] = on ? s.delta[w[j]] : 0.0;
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (dw[j] == d + 1) acc += ldexp(mv / mw[j], ev - ew[j]) * (1.0 + dl[j]);
+            if (dw[j] == d + 1) acc += scale2(cw[j], ev - ew[j]);
     }
     return acc;
 }
@@ -158,15 +187,8 @@ __device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt
         const int64_t nt = (int64_t)nb * blockDim.x;
         for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < cnt; i += nt) {
             const int32_t v = list[i];
-            if (SIGMA) {
-                const BigF a = bc_sigma_thread(s, v, d);
-                s.sm[v] = a.m;
-                s.se[v] = a.e;
-            } else {
-                const double a = bc_delta_thread(s, v, d);
-                s.delta[v] = a;
-                if (v != s.src) s.bc[v] += a;
-            }
+            if (SIGMA) bc_finish_sigma(s, v, bc_sigma_thread(s, v, d));
+            else bc_finish_delta(s, v, bc_delta_thread(s, v, d));
         }
         return;
     }
@@ -182,18 +204,12 @@ __device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt
             BigF a = bc_sigma_part(s, v, d, b, e, 32, lane);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) a = bf_add(a, bf_shfl_xor(a, o));
-            if (lane == 0) {
-                s.sm[v] = a.m;
-                s.se[v] = a.e;
-            }
+            if (lane == 0) bc_finish_sigma(s, v, a);
         } else {
             double a = bc_delta_part(s, v, d, b, e, 32, lane);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(G2_FULL, a, o);
-            if (lane == 0) {
-                s.delta[v] = a;
-                if (v != s.src) s.bc[v] += a;
-            }
+            if (lane == 0) bc_finish_delta(s, v, a);
         }
     }
     // CTAs: vertices with at least kBigDeg arcs
@@ -217,8 +233,7 @@ __device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt
             if (threadIdx.x == 0) {
                 BigF t{0.0, 0};
                 for (int k = 0; k < kWarps; ++k) t = bf_add(t, BigF{s_m[k], s_e[k]});
-                s.sm[v] = t.m;
-                s.se[v] = t.e;
+                bc_finish_sigma(s, v, t);
             }
         } else {
             double a = bc_delta_part(s, v, d, b, e, kCta, threadIdx.x);
@@ -229,8 +244,7 @@ __device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt
             if (threadIdx.x == 0) {
                 double t = 0.0;
                 for (int k = 0; k < kWarps; ++k) t += s_m[k];
-                s.delta[v] = t;
-                if (v != s.src) s.bc[v] += t;
+                bc_finish_delta(s, v, t);
             }
         }
         __syncthreads();
@@ -250,7 +264,7 @@ __global__ void k_bc_init(BcState s, int32_t n, int32_t *cnt3) {
         s.depth[v] = is_src ? 0 : -1;
         s.sm[v] = is_src ? 0.5 : 0.0;  // sigma(src) = 1 = 0.5 * 2^1
         s.se[v] = is_src ? 1 : 0;
-        s.delta[v] = 0.0;
+        s.coef[v] = is_src ? 2.0 : 0.0;  // 1 / m_src
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         s.lvl[0] = s.src;
@@ -382,9 +396,7 @@ __global__ void __launch_bounds__(kClCta, 1) k_bc_cluster(ClusterBcArgs a) {
             const int32_t hi = (int32_t)((int64_t)cnt * (rank + 1) / CL);
             for (int32_t i = lo + threadIdx.x; i < hi; i += kClCta) {
                 const int32_t v = s.lvl[b0 + i];
-                const double dl = bc_delta_thread(s, v, L);
-                s.delta[v] = dl;
-                if (v != s.src) s.bc[v] += dl;
+                bc_finish_delta(s, v, bc_delta_thread(s, v, L));
             }
             cl_barrier();  // level L's dependencies visible to level L-1
         }
@@ -450,11 +462,7 @@ __global__ void __launch_bounds__(kClCta, 1) k_bc_cluster(ClusterBcArgs a) {
                 }
                 beg = __ldg(rowptr + u);
                 deg = __ldg(rowptr + u + 1) - beg;
-                if (d > 0) {
-                    const BigF sg = bc_sigma_thread(s, u, d - 1);
-                    s.sm[u] = sg.m;
-                    s.se[u] = sg.e;
-                }
+                if (d > 0) bc_finish_sigma(s, u, bc_sigma_thread(s, u, d - 1));
             }
             int32_t incl = deg;
 #pragma unroll
@@ -756,7 +764,7 @@ g2_status bc_run(g2_graph *g, const int32_t *srcs, int32_t k, double *bc, const 
     G2_TRY(ws(g, B_I0, (size_t)std::max(n, 1), &s.depth));
     G2_TRY(ws(g, B_LVL, (size_t)std::max(n, 1), &s.lvl));
     G2_TRY(ws(g, B_D0, (size_t)std::max(n, 1), &s.sm));
-    G2_TRY(ws(g, B_D1, (size_t)std::max(n, 1), &s.delta));
+    G2_TRY(ws(g, B_D1, (size_t)std::max(n, 1), &s.coef));
     G2_TRY(ws(g, B_F2, (size_t)std::max(n, 1), &s.se));
     G2_CK(cudaMemsetAsync(bc, 0, (size_t)n * 8, st));
     std::vector<int32_t> off;
