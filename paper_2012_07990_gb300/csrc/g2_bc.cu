@@ -33,7 +33,8 @@
 
 namespace g2 {
 
-constexpr int32_t kBigDeg = 4096;
+constexpr int32_t kBigDeg = 4096;    // a CTA per vertex from this many arcs
+constexpr int32_t kThreadDeg = 32;   // a thread per vertex below this many arcs
 
 struct BigF {
     double m;  // 0 or in [0.5, 1)
@@ -194,12 +195,25 @@ __device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gw = bid * kWarps + wid, nw = nb * kWarps;
-    // warps: vertices with fewer than kBigDeg arcs
+    // threads: vertices with fewer than kThreadDeg arcs (on a power-law
+    // graph most of a level, whose few arcs would leave a warp nearly idle)
+    {
+        const int64_t nt = (int64_t)nb * blockDim.x;
+        for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < cnt; i += nt) {
+            const int32_t v = list[i];
+            const int32_t deg = SIGMA ? s.g.crowptr[v + 1] - s.g.crowptr[v]
+                                      : s.g.rowptr[v + 1] - s.g.rowptr[v];
+            if (deg >= kThreadDeg) continue;
+            if (SIGMA) bc_finish_sigma(s, v, bc_sigma_thread(s, v, d));
+            else bc_finish_delta(s, v, bc_delta_thread(s, v, d));
+        }
+    }
+    // warps: vertices with kThreadDeg .. kBigDeg - 1 arcs
     for (int32_t i = gw; i < cnt; i += nw) {
         int32_t v = list[i];
         int32_t b = SIGMA ? s.g.crowptr[v] : s.g.rowptr[v];
         int32_t e = SIGMA ? s.g.crowptr[v + 1] : s.g.rowptr[v + 1];
-        if (e - b >= kBigDeg) continue;
+        if (e - b < kThreadDeg || e - b >= kBigDeg) continue;
         if (SIGMA) {
             BigF a = bc_sigma_part(s, v, d, b, e, 32, lane);
 #pragma unroll
