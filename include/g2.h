@@ -280,7 +280,8 @@ g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, float *rank,
 
 /* Betweenness centrality (Brandes) summed over the k sources srcs (host
  * int32[k]): bc double[n] device, no normalisation, no halving.  Path counts
- * are extended-range floats (fp64 mantissa, int32 exponent per vertex), so
+ * are extended-range numbers (64-bit integer mantissa, int32 exponent per
+ * vertex), so
  * they neither overflow nor underflow on high-diameter graphs.  Each level's
  * discovery follows the (hybrid) schedule; with kernel fusion each source
  * runs in one persistent cooperative kernel, and with fused WM on a symmetric

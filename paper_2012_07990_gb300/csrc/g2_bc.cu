@@ -8,7 +8,7 @@
 //
 // Path counts grow like binomials on grids (C(2k, k) after 2k levels) and two
 // vertices of one level can differ by more than the fp64 range, so sigma is an
-// extended-range float: an fp64 mantissa in [0.5, 1) and an int32 exponent per
+// extended-range number: a 64-bit integer mantissa and an int32 exponent per
 // vertex.  The dependency sum delta_v = sum_w sigma_v / sigma_w (1 + delta_w)
 // is formed as m_v * sum_w c_w 2^(e_v - e_w) with c_w = (1 + delta_w) / m_w
 // kept per vertex (one fp64 division per vertex, when its sigma is known),
@@ -36,10 +36,19 @@ namespace g2 {
 constexpr int32_t kBigDeg = 4096;    // a CTA per vertex from this many arcs
 constexpr int32_t kThreadDeg = 32;   // a thread per vertex below this many arcs
 
+// Extended-range path count: an integer mantissa m, 0 or in [2^62, 2^63),
+// and an exponent e; the value is m * 2^(e - 63).  Sums take integer shifts
+// and adds only (no fp64 on the per-arc path; fp64 is slow on this GPU), with
+// 63 mantissa bits.
 struct BigF {
-    double m;  // 0 or in [0.5, 1)
+    unsigned long long m;
     int e;
 };
+
+// m * 2^-63 in [0.5, 1) as fp64 (once per vertex)
+__device__ __forceinline__ double bf_mant(unsigned long long m) {
+    return (double)m * 0x1p-63;
+}
 
 // x * 2^k for k <= 1023, by a multiply with the power of two built from its
 // exponent bits; 0 below 2^-1022 (a term that small is below the rounding of
@@ -49,25 +58,25 @@ __device__ __forceinline__ double scale2(double x, int k) {
     return x * __hiloint2double((k + 1023) << 20, 0);
 }
 
-// a + b: the smaller operand scaled to the larger one's exponent (exactly, or
-// dropped when it lies below half an ulp of the larger), the sum in [0.5, 2)
-// brought back into [0.5, 1) — the value frexp / ldexp give, without them.
+// a + b: the smaller mantissa shifted to the larger one's exponent (the
+// bits shifted out are dropped: below 2^-62 of the sum), the sum brought back
+// under 2^63.
 __device__ __forceinline__ BigF bf_add(BigF a, BigF b) {
-    if (a.m == 0.0) return b;
-    if (b.m == 0.0) return a;
+    if (a.m == 0) return b;
+    if (b.m == 0) return a;
     if (a.e < b.e) {
         BigF t = a;
         a = b;
         b = t;
     }
     const int d = a.e - b.e;
-    double s = d > 60 ? a.m : a.m + scale2(b.m, -d);
+    unsigned long long sum = d > 63 ? a.m : a.m + (b.m >> d);
     int e = a.e;
-    if (s >= 1.0) {
-        s *= 0.5;
+    if (sum >> 63) {
+        sum >>= 1;
         ++e;
     }
-    return BigF{s, e};
+    return BigF{sum, e};
 }
 
 __device__ __forceinline__ BigF bf_shfl_xor(BigF a, int d) {
@@ -77,7 +86,7 @@ __device__ __forceinline__ BigF bf_shfl_xor(BigF a, int d) {
 struct BcState {
     DevGraph g;
     int32_t *depth;
-    double *sm;  // sigma mantissas
+    unsigned long long *sm;  // sigma mantissas (BigF)
     int32_t *se; // sigma exponents
     // (1 + delta_v) / m_v: 1 / m_v once sigma_v is known, then (1 + delta_v) /
     // m_v once delta_v is, so that delta_u = m_u * sum over successors w of
@@ -96,7 +105,7 @@ struct BcState {
 // sigma of vertex w at level d+1: sum over in-neighbours u at level d
 __device__ __forceinline__ BigF bc_sigma_part(const BcState &s, int32_t w, int32_t d, int32_t b,
                                               int32_t e, int32_t step, int32_t off) {
-    BigF acc{0.0, 0};
+    BigF acc{0, 0};
     for (int32_t k = b + off; k < e; k += step) {
         int32_t u = s.g.ccol[k];
         if (s.depth[u] == d) acc = bf_add(acc, BigF{s.sm[u], s.se[u]});
@@ -120,7 +129,7 @@ __device__ __forceinline__ double bc_delta_part(const BcState &s, int32_t v, int
 // delta_v from the sum of its successors' terms: added to bc (but for the
 // source) and kept as the coefficient the level above uses
 __device__ __forceinline__ void bc_finish_delta(const BcState &s, int32_t v, double sum) {
-    const double dl = s.sm[v] * sum;
+    const double dl = bf_mant(s.sm[v]) * sum;
     if (v != s.src) s.bc[v] += dl;
     s.coef[v] *= 1.0 + dl;
 }
@@ -129,7 +138,7 @@ __device__ __forceinline__ void bc_finish_delta(const BcState &s, int32_t v, dou
 __device__ __forceinline__ void bc_finish_sigma(const BcState &s, int32_t v, BigF a) {
     s.sm[v] = a.m;
     s.se[v] = a.e;
-    s.coef[v] = 1.0 / a.m;
+    s.coef[v] = 1.0 / bf_mant(a.m);
 }
 
 // The same sums for one thread over a whole (short) list, four arcs' loads in
@@ -137,7 +146,7 @@ __device__ __forceinline__ void bc_finish_sigma(const BcState &s, int32_t v, Big
 // one bc_sigma_part / bc_delta_part give with step 1.
 __device__ __forceinline__ BigF bc_sigma_thread(const BcState &s, int32_t w, int32_t d) {
     const int32_t b = s.g.crowptr[w], e = s.g.crowptr[w + 1];
-    BigF acc{0.0, 0};
+    BigF acc{0, 0};
     for (int32_t k = b; k < e; k += 4) {
         int32_t u[4], du[4];
 #pragma unroll
@@ -147,7 +156,7 @@ __device__ __forceinline__ BigF bc_sigma_thread(const BcState &s, int32_t w, int
         BigF t[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            t[j] = du[j] == d ? BigF{s.sm[u[j]], s.se[u[j]]} : BigF{0.0, 0};
+            t[j] = du[j] == d ? BigF{s.sm[u[j]], s.se[u[j]]} : BigF{0, 0};
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc = bf_add(acc, t[j]);
     }
@@ -228,6 +237,7 @@ __device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt
     }
     // CTAs: vertices with at least kBigDeg arcs
     __shared__ double s_m[kWarps];
+    __shared__ unsigned long long s_mu[kWarps];
     __shared__ int s_e[kWarps];
     if (!s.big) return;  // uniform: no vertex has that many arcs
     for (int32_t i = bid; i < cnt; i += nb) {
@@ -240,13 +250,13 @@ __device__ void bc_level_pass(const BcState &s, const int32_t *list, int32_t cnt
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) a = bf_add(a, bf_shfl_xor(a, o));
             if (lane == 0) {
-                s_m[wid] = a.m;
+                s_mu[wid] = a.m;
                 s_e[wid] = a.e;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
-                BigF t{0.0, 0};
-                for (int k = 0; k < kWarps; ++k) t = bf_add(t, BigF{s_m[k], s_e[k]});
+                BigF t{0, 0};
+                for (int k = 0; k < kWarps; ++k) t = bf_add(t, BigF{s_mu[k], s_e[k]});
                 bc_finish_sigma(s, v, t);
             }
         } else {
@@ -276,7 +286,7 @@ __global__ void k_bc_init(BcState s, int32_t n, int32_t *cnt3) {
          v += (int64_t)gridDim.x * blockDim.x) {
         bool is_src = v == s.src;
         s.depth[v] = is_src ? 0 : -1;
-        s.sm[v] = is_src ? 0.5 : 0.0;  // sigma(src) = 1 = 0.5 * 2^1
+        s.sm[v] = is_src ? (1ull << 62) : 0ull;  // sigma(src) = 1 = 2^62 * 2^(1 - 63)
         s.se[v] = is_src ? 1 : 0;
         s.coef[v] = is_src ? 2.0 : 0.0;  // 1 / m_src
     }
