@@ -178,6 +178,35 @@ def test_bfs_in_one_cluster(g2, rmat14, grid, monkeypatch, hi, lo):
             assert np.array_equal(host(d2), od), (g.name, src)
 
 
+def test_eight_cta_clusters(g2, grid, monkeypatch):
+    """The one-cluster loops with 8-CTA clusters (the portable size, used
+    where a 16-CTA cluster does not fit): BFS, delta-stepping SSSP and BC on
+    road grids, with low hand-over thresholds so that the grid-wide kernels
+    take part too."""
+    monkeypatch.setenv("G2_FUSED_CLUSTER", "8")
+    monkeypatch.setenv("G2_CLUSTER_HI", "200")
+    monkeypatch.setenv("G2_CLUSTER_LO", "100")
+    monkeypatch.setenv("G2_CLUSTER_FAR_LO", "100")
+    monkeypatch.setenv("G2_CLUSTER_BC_HI", "200")
+    monkeypatch.setenv("G2_CLUSTER_BC_LO", "100")
+    s = g2.schedule("WM", kernel_fusion=True)
+    for g in (grid, gg.road_grid(300, seed=4)):
+        w = gg.pair_weights(g, 1000, seed=6)
+        dg = g2.load_graph(g, w)
+        for src in (0, g.n // 2):
+            od, op = oracle.bfs_graph(g, src)
+            d, p = dev(g.n), dev(g.n)
+            g2.g2_bfs(dg, src, d, p, s)
+            assert np.array_equal(host(d), od) and np.array_equal(host(p), op), (g.name, src)
+            dist = dev(g.n)
+            g2.g2_sssp_delta(dg, src, 700, dist, s)
+            assert np.array_equal(host(dist), oracle.sssp_graph(g, w, src)), (g.name, src)
+        srcs = np.array([0, g.n - 1, g.n // 3], dtype=np.int32)
+        bc = dev(g.n, torch.float64)
+        g2.g2_bc(dg, srcs, bc, s)
+        assert bc_close(host(bc), oracle.bc_graph(g, srcs)), g.name
+
+
 def test_null_schedule_follows_the_degree_bound(g2, rmat14, grid):
     """With no schedule, a bounded-degree graph (road grid, largest degree
     <= 32) runs BFS, SSSP and BC as one fused kernel; a power-law graph runs
