@@ -59,8 +59,9 @@ __device__ __forceinline__ void cta_append(int32_t *q, int32_t *cnt, int32_t cap
     if (pred && pos < cap) q[pos] = v;
 }
 
-// In a cluster whose CTA `owner` of the first CL prefix entries holds list
-// entries [off[owner], off[owner + 1]): the CTA that holds entry i.
+// The cluster CTA that holds entry i of the concatenated list, where CTA r
+// holds entries [off[r], off[r + 1]) (off: the CL + 1 prefix sums of the
+// CTAs' list lengths).
 template <int CL>
 __device__ __forceinline__ int cl_owner(const int32_t *off, int32_t i) {
     int r = 0;
@@ -72,7 +73,7 @@ __device__ __forceinline__ int cl_owner(const int32_t *off, int32_t i) {
 // The vertices at depth `lvl`, appended to q (the frontier of a level the
 // cluster loop could not hold).
 static __global__ void k_level_list(const int32_t *depth, int32_t n, int32_t lvl, int32_t *q,
-                             int32_t *cnt, int32_t *err) {
+                                    int32_t *cnt, int32_t *err) {
     const int lane = threadIdx.x & 31;
     for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < n;
          base += (int64_t)gridDim.x * blockDim.x) {
