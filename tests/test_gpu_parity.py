@@ -864,27 +864,28 @@ def test_diag_gather_sums_and_rejects_bad_indices(g2):
 
 def test_pipelined_overlapped_loads(g2, rmat14):
     """A stream of requests served the way bench.py's end-to-end line is: a
-    loader thread uploads graph k+1 (pinned host arrays, G2_LOAD_OVERLAP, its
-    own stream, PageRank preparation in the background) while BFS, CC and
-    PageRank of graph k run on the caller's stream.  Every graph gives the
+    loader thread uploads graph k+1 (pinned host arrays with weights,
+    G2_LOAD_OVERLAP, its own stream, PageRank preparation in the background)
+    while BFS, CC, PageRank and SSSP of graph k run on the caller's stream.  Every graph gives the
     oracle's results; two different graphs alternate so that a mix-up of the
     resident graphs would show."""
     from concurrent.futures import ThreadPoolExecutor
     ga, gb = rmat14, gg.road_grid(160, seed=9)
-    want = {}
+    want, pinned = {}, {}
     for g in (ga, gb):
-        want[g.name] = (oracle.bfs_graph(g, 3)[0], oracle.cc_graph(g), oracle.pagerank_graph(g, 0.85, 20))
-    pinned = {}
-    for g in (ga, gb):
+        w = gg.pair_weights(g, 255, seed=11)
+        want[g.name] = (oracle.bfs_graph(g, 3)[0], oracle.cc_graph(g), oracle.pagerank_graph(g, 0.85, 20),
+                        oracle.sssp_graph(g, w, 3))
         rp = torch.from_numpy(g.rowptr).pin_memory()
         cl = torch.from_numpy(g.col).pin_memory()
-        pinned[g.name] = (rp, cl, np.frombuffer(rp.numpy().data, dtype=np.int32),
-                          np.frombuffer(cl.numpy().data, dtype=np.int32))
+        pw = torch.from_numpy(w).pin_memory()
+        as_np = lambda t: np.frombuffer(t.numpy().data, dtype=np.int32)
+        pinned[g.name] = (rp, cl, pw, as_np(rp), as_np(cl), as_np(pw))
     side = torch.cuda.Stream()
 
     def load(g):
-        _, _, rp, cl = pinned[g.name]
-        return g2.g2_load_csr(g.n, rp, cl, None, True, stream=side, prepare_pagerank=True,
+        _, _, _, rp, cl, w = pinned[g.name]
+        return g2.g2_load_csr(g.n, rp, cl, w, True, stream=side, prepare_pagerank=True,
                               overlap=True), g
 
     order = [ga, gb, ga, gb, gb, ga]
@@ -894,13 +895,15 @@ def test_pipelined_overlapped_loads(g2, rmat14):
             dg, g = fut.result()
             if i + 1 < len(order):
                 fut = ex.submit(load, order[i + 1])
-            d, lab, r = dev(g.n), dev(g.n), dev(g.n, torch.float32)
+            d, lab, r, dist = dev(g.n), dev(g.n), dev(g.n, torch.float32), dev(g.n)
             g2.g2_bfs(dg, 3, d, None, None)
             g2.g2_cc(dg, lab, None)
             g2.g2_pagerank(dg, 0.85, 20, r)
-            od, ol, opr = want[g.name]
+            g2.g2_sssp_delta(dg, 3, 0, dist, None)
+            od, ol, opr, osd = want[g.name]
             assert np.array_equal(host(d), od) and np.array_equal(host(lab), ol), (i, g.name)
             assert np.abs(host(r).astype(np.float64) - opr).sum() <= PR_L1, (i, g.name)
+            assert np.array_equal(host(dist), osd), (i, g.name)
             dg.free()
 
 
