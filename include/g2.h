@@ -100,7 +100,10 @@ typedef struct {
 
 /* HybridGPUSchedule (Sec. V, Table III).  criteria G2_CRITERIA_NONE: always
  * s1.  G2_INPUT_VERTEXSET_SIZE: s1 when |input frontier| < threshold * n,
- * else s2 (threshold read as a fraction of the vertex count). */
+ * else s2 (threshold read as a fraction of the vertex count).  With kernel
+ * fusion (s1.kernel_fusion) the whole loop is one persistent kernel that runs
+ * s1's rounds throughout: the criterion is not evaluated inside it, and for
+ * a hybrid criterion s2 must request fusion too (G2_EUNSUPPORTED otherwise). */
 #define G2_CRITERIA_NONE 0
 #define G2_INPUT_VERTEXSET_SIZE 1
 typedef struct {

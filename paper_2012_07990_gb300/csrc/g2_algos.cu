@@ -596,6 +596,8 @@ g2_status g2_sssp_delta(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
     cudaStream_t st = as_stream(stream);
     g2_hybrid h = sched ? *sched : tuned_sssp_hybrid(g, st);
     if (delta <= 0) delta = h.s1.delta > 0 ? h.s1.delta : 1;
+    if (h.s1.kernel_fusion && h.criteria != G2_CRITERIA_NONE && !h.s2.kernel_fusion)
+        return fail(G2_EUNSUPPORTED, "kernel fusion must be set on both hybrid schedules");
     int32_t *d_err;
     G2_TRY(begin_call(g, st, &d_err));
     if (h.s1.kernel_fusion) {

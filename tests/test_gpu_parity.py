@@ -178,6 +178,30 @@ def test_bfs_in_one_cluster(g2, rmat14, grid, monkeypatch, hi, lo):
             assert np.array_equal(host(d2), od), (g.name, src)
 
 
+def test_half_fused_hybrid_is_rejected(g2, grid):
+    """A hybrid whose s1 asks for kernel fusion and whose s2 does not is
+    rejected by BFS, SSSP and BC (a fused loop runs s1 throughout); with s2
+    fused as well it runs, and gives the oracle's result."""
+    w = gg.pair_weights(grid, 100, seed=2)
+    dg = g2.load_graph(grid, w)
+    fused = g2.schedule("WM", kernel_fusion=True)
+    half = g2.hybrid(fused, g2.schedule("VERTEX_BASED"), 0.02)
+    calls = (lambda s: g2.g2_bfs(dg, 0, dev(grid.n), None, s),
+             lambda s: g2.g2_sssp_delta(dg, 0, 64, dev(grid.n), s),
+             lambda s: g2.g2_bc(dg, [0], dev(grid.n, torch.float64), s))
+    for call in calls:
+        with pytest.raises(g2.G2Error) as e:
+            call(half)
+        assert e.value.status == g2.G2_EUNSUPPORTED
+    both = g2.hybrid(fused, fused, 0.02)
+    d = dev(grid.n)
+    g2.g2_bfs(dg, 0, d, None, both)
+    assert np.array_equal(host(d), oracle.bfs_graph(grid, 0)[0])
+    dist = dev(grid.n)
+    g2.g2_sssp_delta(dg, 0, 64, dist, both)
+    assert np.array_equal(host(dist), oracle.sssp_graph(grid, w, 0))
+
+
 def test_eight_cta_clusters(g2, grid, monkeypatch):
     """The one-cluster loops with 8-CTA clusters (the portable size, used
     where a 16-CTA cluster does not fit): BFS, delta-stepping SSSP and BC on
