@@ -269,6 +269,9 @@ def run_ours(args):
                 "launches": pr_launches, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "vertex_pass_us": round(pv_ms_total / max(pv_launches, 1) * 1e3, 2)}
 
+    pool.shutdown()
+    for v in views.values():
+        v.free()
     e2e = run_e2e(args, g2, G, src, sb, sc, edges_per_step) if not args.no_e2e else None
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
