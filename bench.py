@@ -254,20 +254,28 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = job_gteps(ws, edges_per_step, args.steps, total_ms)
 
-    # roofline of the dominant kernel: the PageRank arc sweep k_pr_seg (PULL +
-    # EDGE_ONLY), algorithmic bytes per launch = 4 m (CSC column ids) + 4 n
-    # (each vertex's share read once) + 4 n (row sums written)
+    # roofline of the dominant kernel: the PageRank arc sweep (PULL + EDGE_ONLY
+    # over the source-blocked layout, k_pr_blk).  Algorithmic bytes of one
+    # sweep = 4 m (a column id per arc) + 4 n (each share read once) + 4 n
+    # (each row sum written once); of a whole round (sweep + vertex pass) =
+    # 4 m + 4 (n + 1) + 16 n (column ids, row offsets, shares written, rank
+    # read and written, out-degrees).
     peak, peak_kind = read_peaks()
     alg_bytes = 4 * m + 8 * n
+    round_bytes = 4 * m + 4 * (n + 1) + 16 * n
     avg_launch_ms = pr_ms_total / max(pr_launches, 1)
+    avg_vertex_ms = pv_ms_total / max(pv_launches, 1)
     achieved = alg_bytes / (avg_launch_ms * 1e-3) / 1e9
+    round_achieved = round_bytes / ((avg_launch_ms + avg_vertex_ms) * 1e-3) / 1e9
     traffic = read_traffic("pr_round", G)
-    roofline = {"kernel": "k_pr_seg (PageRank round: segmented CSC arc sweep)", "bound": "hbm",
+    roofline = {"kernel": "k_pr_blk (PageRank round: source-blocked CSC arc sweep)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_launch_ms * 1e3, 2),
                 "launches": pr_launches, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "vertex_pass_us": round(pv_ms_total / max(pv_launches, 1) * 1e3, 2)}
+                "vertex_pass_us": round(avg_vertex_ms * 1e3, 2),
+                "round": {"bytes": int(round_bytes), "us": round((avg_launch_ms + avg_vertex_ms) * 1e3, 2),
+                          "achieved": round(round_achieved, 1), "frac": round(round_achieved / peak, 4)}}
 
     pool.shutdown()
     for v in views.values():

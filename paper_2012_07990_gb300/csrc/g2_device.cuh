@@ -18,6 +18,19 @@ constexpr int kCta = 256;        // threads per CTA in the traversal kernels
 constexpr int kWarps = kCta / 32;
 constexpr int kPad = 256;        // spare zeroed elements after every device graph array
 
+// Degree bucket of a vertex: exact below 16, then 8 buckets per power of two
+// (kDegBuckets buckets cover every int32 degree).
+constexpr int kDegBuckets = 256;
+__host__ __device__ inline int deg_bucket(int32_t d) {
+    if (d < 16) return d;
+#ifdef __CUDA_ARCH__
+    const int e = 31 - __clz(d);  // floor(log2 d), 4..30
+#else
+    const int e = 31 - __builtin_clz((unsigned)d);
+#endif
+    return 16 + 8 * (e - 4) + ((d >> (e - 3)) & 7);
+}
+
 // ----------------------------------------------------------------- graph view
 struct DevGraph {
     int32_t n;

@@ -130,6 +130,20 @@ struct Topology {
     int32_t *seg_nzrow;
     int32_t *seg_chunk_rank;
     int32_t seg_nnzrow;
+    // source-blocked sweep layout (g2_pr_blk.cu): sources per block (0 = not
+    // built), blocks, 256-arc chunks, runs; per arc the source's rank within
+    // its block; run-head flags; runs before every chunk; destination rank of
+    // every run; first chunk of every block; vertex of every rank and its
+    // out-degree
+    int32_t blk_S;
+    int32_t blk_nb;
+    int32_t blk_G;            // CTAs of the sweep (one per SM)
+    int64_t blk_nchunks;
+    int32_t blk_nruns;
+    uint16_t *blk_loc;
+    uint32_t *blk_head;
+    int32_t *blk_chunk_rank, *blk_nzrow, *blk_bchunk, *blk_order, *blk_deg;
+    int32_t *blk_cta;         // first chunk of every CTA of the sweep (blk_G + 1)
     DevGraph view() const {
         DevGraph d;
         d.n = n; d.m = m;
@@ -213,6 +227,12 @@ int32_t default_block_size(const g2_graph *g, int bytes_per_vertex);
 
 // PageRank layouts for handle h, built on stream st (defined with PageRank).
 g2_status pr_build_layouts(g2_graph *h, cudaStream_t st);
+// Source-blocked PageRank (g2_pr_blk.cu): whether its layout applies with
+// blocks of S sources, the layout itself, and `iters` rounds over it.
+bool pr_blk_applies(const Topology *t, int32_t S);
+g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st);
+g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *rank, int32_t S,
+                           cudaStream_t st);
 // Start the background preparation for g's topology / wait for it (joins the
 // thread, releases its handle and stream; returns its status).
 g2_status pr_prepare_start(g2_graph *g);

@@ -28,6 +28,7 @@
 
 #include "g2_host.h"
 #include "g2_lb.cuh"
+#include "g2_pr_blk.cuh"
 #include "g2_pr_seg.cuh"
 
 namespace g2 {
@@ -546,6 +547,7 @@ __global__ void __launch_bounds__(kCta, MIN_BLOCKS) k_pr_seg_vertex(const int32_
 
 // ---------------------------------------------------------------- host side
 struct PrCfg {
+    int blk;        // blocks of this many sources: the source-blocked sweep (0: off)
     int merge;      // 1: merge-path tile kernel, 0: segmented arc sweep
     int ipt;        // merge kernel: 8 or 16 items per thread
     int hot;        // cached shares (0 = none)
@@ -554,13 +556,20 @@ struct PrCfg {
     int vtx_full;   // vertex pass: 8 resident CTAs per SM (32 registers) or 6
 };
 
-// Defaults (measured on GB300 with RMAT-22): segmented sweep, 1024-thread
-// CTAs, shares of the 16,384 highest-degree vertices cached in shared memory
-// (64 KB per CTA, two CTAs per SM).  The environment overrides them for
-// tuning sweeps.
+// Defaults (measured on GB300 with RMAT-22): the source-blocked sweep with
+// blocks of 49,152 sources (192 KB of shares per CTA, one CTA per SM) where
+// its layout applies (at most 1,024 blocks); else the segmented sweep with
+// 1024-thread CTAs and the shares of the 16,384 highest-degree vertices
+// cached in shared memory (64 KB per CTA, two CTAs per SM).  The environment
+// overrides them for tuning sweeps: G2_PR_KERNEL = blk | seg | merge.
 static PrCfg pr_config(const g2_graph *g) {
-    PrCfg c{0, 8, 16384, 0, 1024, 1};
-    if (const char *e = getenv("G2_PR_KERNEL")) c.merge = strcmp(e, "merge") == 0;
+    PrCfg c{kBlkDefaultS, 0, 8, 16384, 0, 1024, 1};
+    if (const char *e = getenv("G2_PR_BLK_S")) c.blk = atoi(e);
+    if (const char *e = getenv("G2_PR_KERNEL")) {
+        c.merge = strcmp(e, "merge") == 0;
+        if (strcmp(e, "blk") != 0) c.blk = 0;
+    }
+    if (c.blk > 0 && !pr_blk_applies(g->topo, c.blk)) c.blk = 0;
     if (const char *e = getenv("G2_PR_IPT")) c.ipt = atoi(e) == 16 ? 16 : 8;
     if (const char *e = getenv("G2_PR_HOT")) c.hot = std::max(0, atoi(e));
     if (const char *e = getenv("G2_PR_CTAS_PER_SM")) c.per_sm = std::max(0, atoi(e));
@@ -581,18 +590,8 @@ static PrCfg pr_config(const g2_graph *g) {
 // 2^15), and two scans give each vertex its slot.  Which vertices share a
 // slot range does not change any sum: the sweep adds each row's arcs in CSC
 // order whatever the slot numbers are.
-constexpr int kHotBins1 = 256;
+constexpr int kHotBins1 = kDegBuckets;
 constexpr int kHotBins2 = 4096;
-
-__host__ __device__ inline int hot_bin(int32_t d) {
-    if (d < 16) return d;
-#ifdef __CUDA_ARCH__
-    const int e = 31 - __clz(d);  // floor(log2 d), 4..30
-#else
-    const int e = 31 - __builtin_clz((unsigned)d);
-#endif
-    return 16 + 8 * (e - 4) + ((d >> (e - 3)) & 7);
-}
 
 // first degree of coarse bin b and its width (a power of two)
 static inline void hot_bin_range(int b, int64_t *lo, int64_t *width) {
@@ -612,7 +611,7 @@ __global__ void __launch_bounds__(kCta) k_hot_hist1(const int32_t *rowptr, int32
     __syncthreads();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        atomicAdd(&s[hot_bin(__ldg(rowptr + v + 1) - __ldg(rowptr + v))], 1);
+        atomicAdd(&s[deg_bucket(__ldg(rowptr + v + 1) - __ldg(rowptr + v))], 1);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kHotBins1; i += blockDim.x)
@@ -848,6 +847,7 @@ g2_status pagerank_run(g2_graph *g, float damping, int32_t iters, float *rank, c
         if (s.kernel_fusion) return fail(G2_EUNSUPPORTED, "PageRank has no fused variant");
     }
     PrCfg cfg = pr_config(g);
+    if (merge && cfg.blk > 0) return pagerank_blk_run(g, damping, iters, rank, cfg.blk, st);
     ShareMap sm{0, 0, nullptr};
     const int32_t *ccol = t->ccol;
     if (merge && cfg.hot > 0) G2_TRY(ensure_pr_hot_layout(g, cfg.hot, st, &sm, &ccol));
@@ -992,6 +992,7 @@ namespace g2 {
 g2_status pr_build_layouts(g2_graph *g, cudaStream_t st) {
     g->st = st;
     const PrCfg cfg = pr_config(g);
+    if (cfg.blk > 0) return ensure_blk_layout(g, cfg.blk, st);
     if (cfg.hot > 0) {
         ShareMap sm{0, 0, nullptr};
         const int32_t *ccol = nullptr;

@@ -1,0 +1,537 @@
+// g2_pr_blk.cu — PageRank over the source-blocked layout (the sweep kernel is
+// in g2_pr_blk.cuh).  Round t of Sec. VII's topology-driven PageRank,
+//   x_t[v] = (1-d)/n + d * ( sum_{u->v} x_{t-1}[u]/outdeg(u) + D_{t-1}/n ),
+// runs in rank space: every per-vertex array is indexed by the vertex's rank
+// (the stable degree-bucket order of the layout), so the shares of one
+// source block are contiguous and the vertex pass streams.  x_0 = 1/n needs
+// no permutation; the last vertex pass writes x_t back in vertex order.
+//
+// The layout build is an EdgeBlocking preprocessing step (Algorithm 1: a
+// stable counting sort of the arcs by block), here keyed by the source's
+// block and done on the device by a warp-tiled stable partition:
+//   1. rank of every vertex: stable partition of the vertices by degree
+//      bucket (highest bucket first);
+//   2. rank of every arc's source, its block = rank / S;
+//   3. stable partition of the CSC arcs by block, every block padded to
+//      whole chunks;
+//   4. per arc its rank within the block (16 bits) and its destination's
+//      rank (a temporary), then the run heads, the run destinations and the
+//      runs before every chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+#include "g2_host.h"
+#include "g2_pr_blk.cuh"
+
+namespace g2 {
+
+// ------------------------------------------------------- stable partition
+// Items 0..count-1 with keys vals[i] / div in [0, nkeys) get positions such
+// that the items of key k occupy [start_k, start_k + size_k) in index order,
+// and start_k = the sum over j < k of size_j rounded up to a multiple of pad.
+// A warp owns a tile of kPartTile consecutive items and walks it 32 at a
+// time; counts live in the warp's slice of shared memory (nkeys ints).
+constexpr int kPartTile = 2048;
+constexpr int kPartMaxKeys = 1024;
+constexpr int kPartCta = 256;
+
+__global__ void __launch_bounds__(kPartCta) k_part_count(const int32_t *vals, int32_t div,
+                                                         int64_t count, int32_t nkeys,
+                                                         int32_t ntiles, int32_t *counts) {
+    extern __shared__ int32_t s_part[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *c = s_part + wid * nkeys;
+    const int32_t wpc = kPartCta / 32;
+    for (int32_t tile = blockIdx.x * wpc + wid; tile < ntiles; tile += gridDim.x * wpc) {
+        for (int k = lane; k < nkeys; k += 32) c[k] = 0;
+        __syncwarp();
+        const int64_t base = (int64_t)tile * kPartTile;
+        for (int s = 0; s < kPartTile / 32; ++s) {
+            const int64_t i = base + s * 32 + lane;
+            if (i < count) atomicAdd(&c[vals[i] / div], 1);
+        }
+        __syncwarp();
+        for (int k = lane; k < nkeys; k += 32) counts[(int64_t)k * ntiles + tile] = c[k];
+        __syncwarp();
+    }
+}
+
+// scan = exclusive scan of counts (key-major); one CTA: padded key starts,
+// shift[k] = padded start - unpadded start, pstart[nkeys] = padded total
+__global__ void k_part_starts(const int32_t *scan, int32_t ntiles, int32_t nkeys, int32_t pad,
+                              int32_t *shift, int32_t *pstart, int32_t *total) {
+    __shared__ int32_t s_beg[kPartMaxKeys + 1];
+    for (int k = threadIdx.x; k <= nkeys; k += blockDim.x) s_beg[k] = scan[(int64_t)k * ntiles];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int k = 0; k < nkeys; ++k) {
+            const int64_t size = s_beg[k + 1] - s_beg[k];
+            pstart[k] = (int32_t)acc;
+            shift[k] = (int32_t)(acc - s_beg[k]);
+            acc += (size + pad - 1) / pad * pad;
+        }
+        pstart[nkeys] = (int32_t)acc;
+        *total = (int32_t)acc;
+    }
+}
+
+__global__ void __launch_bounds__(kPartCta) k_part_pos(const int32_t *vals, int32_t div,
+                                                       int64_t count, int32_t nkeys, int32_t ntiles,
+                                                       const int32_t *scan, const int32_t *shift,
+                                                       int32_t *pos) {
+    extern __shared__ int32_t s_part[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    int32_t *c = s_part + wid * nkeys;
+    const int32_t wpc = kPartCta / 32;
+    for (int32_t tile = blockIdx.x * wpc + wid; tile < ntiles; tile += gridDim.x * wpc) {
+        for (int k = lane; k < nkeys; k += 32) c[k] = scan[(int64_t)k * ntiles + tile] + shift[k];
+        __syncwarp();
+        const int64_t base = (int64_t)tile * kPartTile;
+        for (int s = 0; s < kPartTile / 32; ++s) {
+            const int64_t i = base + s * 32 + lane;
+            const int key = i < count ? vals[i] / div : -1;
+            const unsigned peers = __match_any_sync(G2_FULL, key);
+            const int r = __popc(peers & lt);
+            if (key >= 0) pos[i] = c[key] + r;
+            __syncwarp();
+            if (key >= 0 && r == 0) c[key] += __popc(peers);
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------- layout kernels
+// degree bucket key, highest bucket first (bucket 0 = no out-arcs, last)
+__global__ void k_blk_vkey(const int32_t *rowptr, int32_t n, int32_t *key) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        key[v] = kDegBuckets - 1 - deg_bucket(rowptr[v + 1] - rowptr[v]);
+}
+
+// order[rank[v]] = v, deg[rank[v]] = outdeg(v)
+__global__ void k_blk_order(const int32_t *rowptr, const int32_t *rank, int32_t n, int32_t *order,
+                            int32_t *deg) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = rank[v];
+        order[r] = (int32_t)v;
+        deg[r] = rowptr[v + 1] - rowptr[v];
+    }
+}
+
+// rank of the source of every CSC arc
+__global__ void k_blk_arc_rank(const int32_t *ccol, const int32_t *rank, int32_t m, int32_t *out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = rank[ccol[e]];
+}
+
+static __global__ void k_fill_i32_blk(int32_t *p, int64_t count, int32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// a warp per CSC row v: every arc e of the row goes to pos[e] with its
+// source's rank within the block and v's rank
+__global__ void k_blk_scatter(const int32_t *crowptr, int32_t n, const int32_t *rank,
+                              const int32_t *srank, const int32_t *pos, int32_t S, uint16_t *loc,
+                              int32_t *dst) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = gw; v < n; v += nw) {
+        const int32_t b = crowptr[v], e = crowptr[v + 1];
+        if (b == e) continue;
+        const int32_t rv = rank[v];
+        for (int32_t k = b + lane; k < e; k += 32) {
+            const int32_t p = pos[k];
+            loc[p] = (uint16_t)(srank[k] % S);
+            dst[p] = rv;
+        }
+    }
+}
+
+// head bit of position p: its destination differs from position p-1's
+// (block starts are marked by k_blk_mark_starts)
+__global__ void k_blk_heads(const int32_t *dst, int64_t total, uint32_t *head) {
+    const int64_t words = total / 32;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p0 = w * 32;
+        int32_t prev = p0 > 0 ? dst[p0 - 1] : -1;
+        uint32_t bits = 0;
+        for (int j = 0; j < 32; ++j) {
+            const int32_t d = dst[p0 + j];
+            if (d != prev) bits |= 1u << j;
+            prev = d;
+        }
+        head[w] = bits;
+    }
+}
+
+__global__ void k_blk_mark_starts(const int32_t *pstart, int32_t nb, int64_t total, uint32_t *head,
+                                  int32_t *bchunk) {
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += gridDim.x * blockDim.x) {
+        const int32_t p = pstart[b];
+        bchunk[b] = p / kBlkArcs;
+        if (b < nb && p < total && pstart[b + 1] > p) atomicOr(head + (p >> 5), 1u << (p & 31));
+    }
+}
+
+__global__ void k_blk_chunk_heads(const uint32_t *head, int64_t nchunks, int32_t *cnt) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int s = 0;
+        for (int j = 0; j < kBlkHeadWords; ++j) s += __popc(head[c * kBlkHeadWords + j]);
+        cnt[c] = s;
+    }
+}
+
+// nzrow[k] = destination rank of the k-th run
+__global__ void k_blk_nzrow(const uint32_t *head, const int32_t *chunk_rank, const int32_t *dst,
+                            int64_t words, int32_t *nzrow) {
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = w / kBlkHeadWords;
+        int32_t r = chunk_rank[c];
+        for (int64_t j = c * kBlkHeadWords; j < w; ++j) r += __popc(head[j]);
+        uint32_t bits = head[w];
+        while (bits) {
+            const int j = __ffs(bits) - 1;
+            bits &= bits - 1;
+            nzrow[r++] = dst[w * 32 + j];
+        }
+    }
+}
+
+// cta_chunk[i] = the first chunk of CTA i: the least c with
+// kBlkArcs * c + runcost * (runs before c) >= i / G of the sweep's total cost
+__global__ void k_blk_cta_split(const int32_t *chunk_rank, int64_t nchunks, int32_t G,
+                                int32_t runcost, int32_t *cta_chunk) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > G) return;
+    const int64_t total = kBlkArcs * nchunks + (int64_t)runcost * chunk_rank[nchunks];
+    const int64_t target = total * i / G;
+    int64_t lo = 0, hi = nchunks;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (kBlkArcs * mid + (int64_t)runcost * chunk_rank[mid] >= target) hi = mid;
+        else lo = mid + 1;
+    }
+    cta_chunk[i] = (int32_t)lo;
+}
+
+// --------------------------------------------------------- vertex passes
+// x0 = 1/n (written in vertex order: the same value everywhere), the first
+// shares in rank order and D0 = (#vertices without out-arcs)/n into the slots.
+__global__ void __launch_bounds__(kCta) k_pr_blk_init(const int32_t *deg, int32_t n, float *share,
+                                                      double *dslots, float *x, double inv_n) {
+    const int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const float x0 = (float)inv_n;
+    float dangling = 0.f;
+    for (int k = 0; k < 4; ++k) {
+        const int64_t r = r0 + k;
+        if (r >= n) break;
+        const int32_t od = deg[r];
+        share[r] = od > 0 ? x0 / (float)od : 0.f;
+        if (od == 0) dangling += 1.f;
+        if (x) x[r] = x0;
+    }
+    // at most 128 per warp: exact in fp32; scaled by 1/n in fp64
+    for (int o = 16; o > 0; o >>= 1) dangling += __shfl_xor_sync(G2_FULL, dangling, o);
+    if ((threadIdx.x & 31) == 0 && dangling != 0.f) {
+        const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        atomicAdd(dslots + (gw % kDSlots) * kDStride, (double)dangling * inv_n);
+    }
+}
+
+// After a sweep: x_t from y, the next shares, the next D; y back to zero.
+// Four consecutive ranks per thread with 16-byte loads and stores; the last
+// round also writes x_t to the caller's array in vertex order.
+template <bool WRITE_X>
+__global__ void __launch_bounds__(kCta, 6) k_pr_blk_vertex(const int32_t *deg, const int32_t *order,
+                                                           int32_t n, float *y, float *share_next,
+                                                           float *x, const double *dprev,
+                                                           double *dslots, float base, float damp,
+                                                           double inv_n) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const bool full = r0 + 4 <= n;
+    int32_t od[4] = {0, 0, 0, 0};
+    float yv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (full) {
+        const int4 d4 = *reinterpret_cast<const int4 *>(deg + r0);
+        const float4 y4 = *reinterpret_cast<const float4 *>(y + r0);
+        od[0] = d4.x; od[1] = d4.y; od[2] = d4.z; od[3] = d4.w;
+        yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
+    } else if (r0 < n) {
+        for (int k = 0; k < 4; ++k)
+            if (r0 + k < n) {
+                od[k] = deg[r0 + k];
+                yv[k] = y[r0 + k];
+            }
+    }
+    const float dterm = (float)(*dprev * inv_n);
+    float dsum = 0.f;
+    if (r0 < n) {
+        float xs[4], sh[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            xs[k] = base + damp * (yv[k] + dterm);
+            sh[k] = 0.f;
+            if (r0 + k >= n) continue;
+            if (od[k] > 0) sh[k] = xs[k] / (float)od[k];
+            else dsum += xs[k];
+        }
+        if (full) {
+            *reinterpret_cast<float4 *>(share_next + r0) = make_float4(sh[0], sh[1], sh[2], sh[3]);
+            *reinterpret_cast<float4 *>(y + r0) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            for (int k = 0; k < 4; ++k)
+                if (r0 + k < n) {
+                    share_next[r0 + k] = sh[k];
+                    y[r0 + k] = 0.f;
+                }
+        }
+        if (WRITE_X) {
+            if (full) {
+                const int4 o4 = *reinterpret_cast<const int4 *>(order + r0);
+                x[o4.x] = xs[0];
+                x[o4.y] = xs[1];
+                x[o4.z] = xs[2];
+                x[o4.w] = xs[3];
+            } else {
+                for (int k = 0; k < 4; ++k)
+                    if (r0 + k < n) x[order[r0 + k]] = xs[k];
+            }
+        }
+    }
+    // D partial of the warp into one of the fp64 slots; the next sweep folds them
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(G2_FULL, dsum, o);
+    if (lane == 0 && dsum != 0.f) {
+        const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        atomicAdd(dslots + (gw % kDSlots) * kDStride, (double)dsum);
+    }
+}
+
+// ------------------------------------------------------------ host side
+constexpr int kBlkCta = 1024;
+
+static int part_grid(const g2_graph *g, int32_t ntiles) {
+    const int wpc = kPartCta / 32;
+    int64_t b = ((int64_t)ntiles + wpc - 1) / wpc;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)g->topo->sm_count * 8));
+}
+
+// Positions of a stable partition (see k_part_count); pstart gets nkeys + 1
+// padded starts; *total the padded item count.
+static g2_status stable_partition(g2_graph *g, const int32_t *vals, int32_t div, int64_t count,
+                                  int32_t nkeys, int32_t pad, int32_t *pos, int32_t *pstart,
+                                  int64_t *total, cudaStream_t st) {
+    const int32_t ntiles = (int32_t)std::max<int64_t>(1, (count + kPartTile - 1) / kPartTile);
+    const int64_t cells = (int64_t)nkeys * ntiles;
+    if (cells >= 2147483647LL) return fail(G2_EUNSUPPORTED, "partition table too large");
+    int32_t *counts = nullptr, *scan = nullptr, *shift = nullptr, *d_total;
+    G2_CK(dmalloc(&counts, (size_t)(cells + 1) * 4, st));
+    G2_CK(dmalloc(&scan, (size_t)(cells + 1) * 4, st));
+    G2_CK(dmalloc(&shift, (size_t)nkeys * 4, st));
+    G2_TRY(ws(g, B_CTR, 64, &d_total));
+    d_total += 50;
+    const size_t smem = (size_t)(kPartCta / 32) * nkeys * 4;
+    const int grid = part_grid(g, ntiles);
+    k_part_count<<<grid, kPartCta, smem, st>>>(vals, div, count, nkeys, ntiles, counts);
+    G2_TRY(exclusive_scan_i32(g, counts, scan, (int32_t)cells, st));
+    k_part_starts<<<1, 1024, 0, st>>>(scan, ntiles, nkeys, pad, shift, pstart, d_total);
+    k_part_pos<<<grid, kPartCta, smem, st>>>(vals, div, count, nkeys, ntiles, scan, shift, pos);
+    G2_CK(cudaGetLastError());
+    G2_CK(cudaMemcpyAsync(g->h_ctr + 50, d_total, 4, cudaMemcpyDeviceToHost, st));
+    G2_CK(cudaStreamSynchronize(st));
+    *total = g->h_ctr[50];
+    stats().launches += 3;
+    dfree(counts, st);
+    dfree(scan, st);
+    dfree(shift, st);
+    return G2_OK;
+}
+
+static void free_blk(Topology *t, cudaStream_t st) {
+    void *blocks[] = {t->blk_loc, t->blk_head, t->blk_chunk_rank, t->blk_nzrow, t->blk_bchunk,
+                      t->blk_order, t->blk_deg, t->blk_cta};
+    for (void *p : blocks) dfree(p, st);
+    t->blk_loc = nullptr;
+    t->blk_head = nullptr;
+    t->blk_chunk_rank = t->blk_nzrow = t->blk_bchunk = t->blk_order = t->blk_deg = nullptr;
+    t->blk_cta = nullptr;
+    t->blk_S = 0;
+}
+
+// Whether the source-blocked layout applies to t with blocks of S sources.
+bool pr_blk_applies(const Topology *t, int32_t S) {
+    if (S < 256 || S > kBlkMaxS || (S & 3)) return false;
+    const int64_t nb = ((int64_t)t->n + S - 1) / S;
+    if (t->n == 0 || nb > kPartMaxKeys) return false;
+    // padded arcs must stay int32-addressable
+    return (int64_t)t->m + nb * kBlkArcs + kPad < 2147483647LL;
+}
+
+g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
+    Topology *t = g->topo;
+    std::lock_guard<std::recursive_mutex> lk(t->pr_mu);
+    if (t->blk_S == S) return G2_OK;
+    if (!pr_blk_applies(t, S)) return fail(G2_EUNSUPPORTED, "source-blocked layout does not apply");
+    free_blk(t, st);
+    const int32_t n = t->n, m = t->m;
+    const int32_t nb = (int32_t)(((int64_t)n + S - 1) / S);
+    const int grid = grid_for(g, n, kCta);
+    int32_t *vkey = nullptr, *rank = nullptr, *vstart = nullptr;
+    G2_CK(dmalloc(&vkey, (size_t)n * 4, st));
+    G2_CK(dmalloc(&rank, (size_t)n * 4, st));
+    G2_CK(dmalloc(&vstart, (size_t)(kDegBuckets + 1) * 4, st));
+    G2_CK(dmalloc(&t->blk_order, ((size_t)n + kPad) * 4, st));
+    G2_CK(dmalloc(&t->blk_deg, ((size_t)n + kPad) * 4, st));
+    G2_CK(dmalloc(&t->blk_bchunk, ((size_t)nb + 1) * 4, st));
+    // one CTA per SM; the sweep's chunks are divided among them by cost
+    const int32_t G = std::max(1, t->sm_count);
+    G2_CK(dmalloc(&t->blk_cta, ((size_t)G + 1) * 4, st));
+    // 1. vertex ranks
+    k_blk_vkey<<<grid, kCta, 0, st>>>(t->rowptr, n, vkey);
+    int64_t vtotal = 0;
+    G2_TRY(stable_partition(g, vkey, 1, n, kDegBuckets, 1, rank, vstart, &vtotal, st));
+    k_blk_order<<<grid, kCta, 0, st>>>(t->rowptr, rank, n, t->blk_order, t->blk_deg);
+    G2_CK(cudaMemsetAsync(t->blk_order + n, 0, kPad * 4, st));
+    G2_CK(cudaMemsetAsync(t->blk_deg + n, 0, kPad * 4, st));
+    stats().launches += 2;
+    dfree(vkey, st);
+    dfree(vstart, st);
+    int64_t total = 0;
+    int32_t *pstart = nullptr;
+    G2_CK(dmalloc(&pstart, ((size_t)nb + 1) * 4, st));
+    if (m > 0) {
+        // 2-3. source ranks, partition by source block
+        int32_t *srank = nullptr, *pos = nullptr, *dst = nullptr;
+        G2_CK(dmalloc(&srank, (size_t)m * 4, st));
+        G2_CK(dmalloc(&pos, (size_t)m * 4, st));
+        k_blk_arc_rank<<<grid_for(g, m, kCta), kCta, 0, st>>>(t->ccol, rank, m, srank);
+        stats().launches += 1;
+        G2_TRY(stable_partition(g, srank, S, m, nb, kBlkArcs, pos, pstart, &total, st));
+        // 4. per-position block rank and destination rank; padding keeps
+        // rank 0 in its block and points at the spare slot n
+        G2_CK(dmalloc(&t->blk_loc, ((size_t)total + kPad) * 2, st));
+        G2_CK(dmalloc(&dst, (size_t)total * 4, st));
+        G2_CK(cudaMemsetAsync(t->blk_loc, 0, ((size_t)total + kPad) * 2, st));
+        k_fill_i32_blk<<<grid_for(g, total, kCta), kCta, 0, st>>>(dst, total, n);
+        k_blk_scatter<<<grid_for(g, (int64_t)n * 32, kCta), kCta, 0, st>>>(t->crowptr, n, rank,
+                                                                            srank, pos, S,
+                                                                            t->blk_loc, dst);
+        dfree(srank, st);
+        dfree(pos, st);
+        const int64_t words = total / 32, nchunks = total / kBlkArcs;
+        G2_CK(dmalloc(&t->blk_head, ((size_t)words + kPad) * 4, st));
+        G2_CK(cudaMemsetAsync(t->blk_head + words, 0, kPad * 4, st));
+        k_blk_heads<<<grid_for(g, words, kCta), kCta, 0, st>>>(dst, total, t->blk_head);
+        k_blk_mark_starts<<<(nb + 1 + kCta - 1) / kCta, kCta, 0, st>>>(pstart, nb, total,
+                                                                       t->blk_head, t->blk_bchunk);
+        int32_t *ccount = nullptr;
+        G2_CK(dmalloc(&ccount, (size_t)nchunks * 4, st));
+        G2_CK(dmalloc(&t->blk_chunk_rank, ((size_t)nchunks + 1) * 4, st));
+        k_blk_chunk_heads<<<grid_for(g, nchunks, kCta), kCta, 0, st>>>(t->blk_head, nchunks, ccount);
+        G2_TRY(exclusive_scan_i32(g, ccount, t->blk_chunk_rank, (int32_t)nchunks, st));
+        G2_CK(cudaMemcpyAsync(g->h_ctr + 51, t->blk_chunk_rank + nchunks, 4, cudaMemcpyDeviceToHost,
+                              st));
+        G2_CK(cudaStreamSynchronize(st));
+        const int32_t nruns = g->h_ctr[51];
+        G2_CK(dmalloc(&t->blk_nzrow, ((size_t)nruns + 1) * 4, st));
+        k_blk_nzrow<<<grid_for(g, words, kCta), kCta, 0, st>>>(t->blk_head, t->blk_chunk_rank, dst,
+                                                               words, t->blk_nzrow);
+        int32_t runcost = kBlkRunCost;
+        if (const char *e = getenv("G2_PR_BLK_RUNCOST")) runcost = std::max(0, atoi(e));
+        k_blk_cta_split<<<(G + 1 + kCta - 1) / kCta, kCta, 0, st>>>(t->blk_chunk_rank, nchunks, G,
+                                                                    runcost, t->blk_cta);
+        stats().launches += 8;
+        dfree(ccount, st);
+        dfree(dst, st);
+        t->blk_nruns = nruns;
+    } else {
+        G2_CK(cudaMemsetAsync(t->blk_bchunk, 0, ((size_t)nb + 1) * 4, st));
+        G2_CK(cudaMemsetAsync(t->blk_cta, 0, ((size_t)G + 1) * 4, st));
+        t->blk_nruns = 0;
+    }
+    G2_CK(cudaGetLastError());
+    G2_CK(cudaStreamSynchronize(st));
+    dfree(rank, st);
+    dfree(pstart, st);
+    t->blk_nb = nb;
+    t->blk_G = G;
+    t->blk_nchunks = total / kBlkArcs;
+    t->blk_S = S;
+    return G2_OK;
+}
+
+g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *rank, int32_t S,
+                           cudaStream_t st) {
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    G2_TRY(ensure_blk_layout(g, S, st));
+    const double inv_n = 1.0 / (double)n;
+    const float base = (float)((1.0 - damping) * inv_n);
+    // shares in rank order, padded with zeros to whole blocks; y in rank
+    // order with the spare slot n (the padding runs' target)
+    const size_t nshare_alloc = (size_t)t->blk_nb * S + 4;
+    float *cbuf[2], *y;
+    G2_TRY(ws(g, B_F0, nshare_alloc, &cbuf[0]));
+    G2_TRY(ws(g, B_F1, nshare_alloc, &cbuf[1]));
+    G2_TRY(ws(g, B_F2, (size_t)n + 4, &y));
+    for (int i = 0; i < 2; ++i)
+        G2_CK(cudaMemsetAsync(cbuf[i] + n, 0, (nshare_alloc - n) * 4, st));
+    G2_CK(cudaMemsetAsync(y, 0, ((size_t)n + 4) * 4, st));
+    constexpr size_t R = (size_t)kDSlots * kDStride;
+    double *dd;
+    G2_TRY(ws(g, B_D1, 8 + R, &dd));
+    G2_CK(cudaMemsetAsync(dd, 0, (8 + R) * sizeof(double), st));
+    const int qblocks = (int)((((int64_t)n + 3) / 4 + kCta - 1) / kCta);
+    k_pr_blk_init<<<qblocks, kCta, 0, st>>>(t->blk_deg, n, cbuf[0], dd + 8, rank, inv_n);
+    stats().launches += 1;
+    if (iters <= 0) return G2_OK;
+    const size_t smem = blk_smem_bytes(S);
+    auto kern = k_pr_blk<kBlkCta>;
+    G2_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // one CTA per SM (the block's shares take most of its shared memory),
+    // each with the range of chunks the layout assigned it; launched even
+    // without arcs: its first warp folds the dangling mass
+    const int grid = t->blk_G;
+    const int64_t nshare = ((int64_t)n + 3) & ~(int64_t)3;
+    for (int32_t it = 0; it < iters; ++it) {
+        double *dprev = dd + 2 + (it & 1);
+        KTime kt;
+        ktime_begin(kt, "pr_round", st);
+        kern<<<grid, kBlkCta, smem, st>>>(reinterpret_cast<const uint4 *>(t->blk_loc), t->blk_head,
+                                          t->blk_chunk_rank, t->blk_nzrow, t->blk_bchunk,
+                                          t->blk_nb, t->blk_cta, S, nshare, cbuf[it & 1], y,
+                                          dd + 8, dprev);
+        ktime_end(kt, st);
+        KTime kv;
+        ktime_begin(kv, "pr_vertex", st);
+        if (it == iters - 1)
+            k_pr_blk_vertex<true><<<qblocks, kCta, 0, st>>>(t->blk_deg, t->blk_order, n, y,
+                                                            cbuf[(it + 1) & 1], rank, dprev,
+                                                            dd + 8, base, damping, inv_n);
+        else
+            k_pr_blk_vertex<false><<<qblocks, kCta, 0, st>>>(t->blk_deg, t->blk_order, n, y,
+                                                             cbuf[(it + 1) & 1], rank, dprev,
+                                                             dd + 8, base, damping, inv_n);
+        ktime_end(kv, st);
+        stats().launches += 2;
+        stats().iterations++;
+        stats().pull_rounds++;
+    }
+    G2_CK(cudaGetLastError());
+    return G2_OK;
+}
+
+}  // namespace g2

@@ -1,0 +1,187 @@
+// g2_pr_blk.cuh — the source-blocked PageRank arc sweep (Sec. VII: one PULL
+// + EDGE_ONLY round; EdgeBlocking, Sec. VI-D and Algorithms 1-2, applied to
+// the sources of the pull instead of the destinations of the push).
+// Kept in a file of its own so that a profile of this kernel can name the
+// exact source it was taken on.
+//
+// Layout (built once per topology in g2_pr_blk.cu).  Vertices are numbered
+// by rank: a stable order by degree bucket, highest first.  The sources are
+// cut into blocks of S consecutive ranks, S sized so that one block's shares
+// fill a CTA's shared memory.  The CSC arcs are partitioned stably by the
+// block of their source, so inside a block the arcs of one destination stay
+// contiguous (a run); each block is padded to whole chunks of kBlkArcs arcs.
+// Per arc: the source's rank within its block (16 bits) and a head bit (the
+// first arc of a run, and the first arc of every block).  Per run: its
+// destination's rank (nzrow; padding runs point at the spare slot n).  Per
+// chunk: the number of runs that start before it.
+//
+// One CTA per SM takes an equal range of chunks.  For each block its range
+// touches it copies that block's shares into shared memory once, then its
+// warps sweep the block's chunks: every gather is a shared-memory load, and a
+// run costs one reduction into y.  On a power-law graph a block's arcs
+// concentrate on few destinations (RMAT-22, S = 49,152: 12.3M runs for
+// 128.3M arcs), so the scattered L2 traffic per arc falls by an order of
+// magnitude against a gather per arc.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "g2_device.cuh"
+#include "g2_pr_seg.cuh"
+
+namespace g2 {
+
+constexpr int kBlkArcs = 256;               // arcs per warp chunk, 8 per lane
+constexpr int kBlkHeadWords = kBlkArcs / 32;
+// largest block: 16-bit ranks within a block, and the shares of one block
+// within a CTA's shared memory (227 KB on sm_103)
+constexpr int kBlkMaxS = 57344;
+// default block: 192 KB of shares, measured best on RMAT-22
+constexpr int kBlkDefaultS = 49152;
+
+// Cost of a chunk for the division of the sweep among CTAs: its arcs plus
+// kBlkRunCost per run (a run costs a row lookup and a reduction into y, about
+// four arcs' worth of gathers and sums, measured on RMAT-21).  Sparse blocks
+// (low-degree sources, a run per arc or two) would otherwise leave the CTAs
+// that draw them several times behind the others.
+constexpr int kBlkRunCost = 4;
+
+// shared memory of a launch with blocks of S sources
+__host__ __device__ constexpr size_t blk_smem_bytes(int S) { return (size_t)S * 4; }
+
+template <int CTA>
+__global__ void __launch_bounds__(CTA, 1) k_pr_blk(const uint4 *loc4, const uint32_t *head,
+                                                   const int32_t *chunk_rank, const int32_t *nzrow,
+                                                   const int32_t *bchunk, int32_t nb,
+                                                   const int32_t *cta_chunk, int32_t S,
+                                                   int64_t nshare, const float *share, float *y,
+                                                   double *dslots, double *dfin) {
+    extern __shared__ __align__(16) float s_sh[];
+    // The previous vertex pass left D in kDSlots slots: the first warp of
+    // block 0 adds them into *dfin and zeroes them.
+    if (dslots && blockIdx.x == 0 && threadIdx.x < 32) fold_dslots(dslots, dfin);
+    constexpr int W = CTA / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // this CTA's chunks: an equal share of the cost (arcs + runs)
+    int64_t c0 = cta_chunk[blockIdx.x];
+    const int64_t c1 = cta_chunk[blockIdx.x + 1];
+    if (c0 >= c1) return;
+    // block of chunk c0: the last b with bchunk[b] <= c0 (bchunk[0] = 0)
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bchunk[mid] <= c0) lo = mid;
+        else hi = mid - 1;
+    }
+    int b = lo;
+    const int sh = (lane & 3) * 8;  // this lane's byte in its chunk's head word lane / 4
+    const int hword = lane >> 2;
+    while (c0 < c1) {
+        const int64_t cend = min(c1, (int64_t)bchunk[b + 1]);
+        if (cend > c0) {
+            __syncthreads();  // every warp is done with the previous block's shares
+            const int64_t s0 = (int64_t)b * S;
+            const int32_t len4 = (int32_t)(min((int64_t)S, nshare - s0) >> 2);
+            const float4 *src = reinterpret_cast<const float4 *>(share + s0);
+            float4 *dst = reinterpret_cast<float4 *>(s_sh);
+            for (int i = threadIdx.x; i < len4; i += CTA) dst[i] = __ldg(src + i);
+            __syncthreads();
+            // software pipeline: the next chunk's ids, head byte and run base
+            // are loaded, and its run rows prefetched into L1, while this
+            // chunk is summed
+            int64_t c = c0 + warp;
+            uint4 nl = make_uint4(0, 0, 0, 0);
+            uint32_t nhw = 0;
+            int32_t nrk = 0;
+            if (c < cend) {
+                nl = loc4[c * 32 + lane];
+                nhw = head[c * kBlkHeadWords + hword];
+                nrk = chunk_rank[c];
+            }
+            for (; c < cend; c += W) {
+                const uint4 l = nl;
+                const uint32_t hf = (nhw >> sh) & 0xFFu;
+                const int32_t base_rank = nrk;
+                if (c + W < cend) {
+                    nl = loc4[(c + W) * 32 + lane];
+                    nhw = head[(c + W) * kBlkHeadWords + hword];
+                    nrk = chunk_rank[c + W];
+                }
+                float v[8];
+                v[0] = s_sh[l.x & 0xFFFFu];
+                v[1] = s_sh[l.x >> 16];
+                v[2] = s_sh[l.y & 0xFFFFu];
+                v[3] = s_sh[l.y >> 16];
+                v[4] = s_sh[l.z & 0xFFFFu];
+                v[5] = s_sh[l.z >> 16];
+                v[6] = s_sh[l.w & 0xFFFFu];
+                v[7] = s_sh[l.w >> 16];
+                // heads before this lane in the chunk, and in the whole chunk
+                const int nh = __popc(hf);
+                const int incl = warp_incl_scan(nh);
+                const int prefix = incl - nh;
+                const int total_heads = __shfl_sync(G2_FULL, incl, 31);
+                // lane-local pieces: A = arcs before the first head, inner
+                // complete runs (one reduction each), T = arcs from the last
+                // head on
+                float A = 0.f, run = 0.f;
+                int seen = 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if ((hf >> k) & 1u) {
+                        if (seen == 0) {
+                            A = run;
+                        } else if (run != 0.f) {
+                            atomicAdd(y + nzrow[base_rank + prefix + seen - 1], run);
+                        }
+                        run = 0.f;
+                        ++seen;
+                    }
+                    run += v[k];
+                }
+                if (seen == 0) A = run;
+                const bool has_head = seen > 0;
+                // segmented inclusive scan over lanes (shares are >= 0, so the
+                // head flag travels in the sign bit: one shuffle per step)
+                float q = has_head ? run : A;
+                bool f = has_head;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t enc = __float_as_uint(q) | (f ? 0x80000000u : 0u);
+                    const uint32_t o = __shfl_up_sync(G2_FULL, enc, d);
+                    if (lane >= d && !f) {
+                        q += __uint_as_float(o & 0x7fffffffu);
+                        f = (o >> 31) != 0u;
+                    }
+                }
+                float qprev = __shfl_up_sync(G2_FULL, q, 1);
+                if (lane == 0) qprev = 0.f;
+                if (has_head) {
+                    // the run that ends just before this lane's first head
+                    const float tot = qprev + A;
+                    const int32_t rk = base_rank + prefix - 1;
+                    if (tot != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], tot);
+                }
+                if (lane == 31) {
+                    // the run that reaches the end of the chunk (it may go on
+                    // in the next chunk of the same block)
+                    const int32_t rk = base_rank + total_heads - 1;
+                    if (q != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], q);
+                }
+                if (c + W < cend) {
+                    // rows of the next chunk's runs: nzrow[nrk - 1 ..
+                    // nrk + its heads), one 32-byte sector per lane
+                    const int nt = __reduce_add_sync(G2_FULL, __popc((nhw >> sh) & 0xFFu));
+                    const int64_t r = (int64_t)nrk - 1 + 8 * lane;
+                    if (r >= 0 && 8 * lane <= nt)
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(nzrow + r));
+                }
+            }
+        }
+        c0 = cend;
+        ++b;
+    }
+}
+
+}  // namespace g2

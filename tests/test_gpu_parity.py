@@ -421,6 +421,28 @@ def test_pagerank_tile_configs(g2, rmat14, grid, monkeypatch, kernel, ipt, cta, 
         assert np.abs(host(rank).astype(np.float64) - ref).sum() <= PR_L1, (g.name, ipt, hot)
 
 
+@pytest.mark.parametrize("S", ["256", "1024", "4096", "12288", "49152"])
+def test_pagerank_source_blocked(g2, rmat14, grid, monkeypatch, S):
+    """The source-blocked sweep (EdgeBlocking by source block, shares staged
+    in shared memory) at block sizes from 256 sources (64 blocks on RMAT-14,
+    so runs cross chunk and block boundaries and most blocks carry padding)
+    to the largest; directed and degenerate graphs included."""
+    monkeypatch.setenv("G2_PR_KERNEL", "blk")
+    monkeypatch.setenv("G2_PR_BLK_S", S)
+    graphs = [rmat14, grid, gg.gnp(300, 0.02, 9, symmetric=False), gg.star(3000), gg.path(1000),
+              gg.from_arcs(5, [], []), gg.from_arcs(1, [], []),
+              gg.disjoint_union(gg.complete(30), gg.star(700), gg.from_arcs(3, [], []))]
+    for g in graphs:
+        ref = oracle.pagerank_graph(g, 0.85, 20)
+        dg = g2.load_graph(g)
+        for iters in (20, 0, 1):
+            want = ref if iters == 20 else oracle.pagerank_graph(g, 0.85, iters)
+            rank = dev(g.n, torch.float32)
+            g2.g2_pagerank(dg, 0.85, iters, rank)
+            l1 = np.abs(host(rank).astype(np.float64) - want).sum()
+            assert l1 <= PR_L1, (g.name, S, iters, l1)
+
+
 def test_pagerank_iteration_counts(g2, rmat14):
     dg = g2.load_graph(rmat14)
     for iters in (0, 1, 2, 7):
