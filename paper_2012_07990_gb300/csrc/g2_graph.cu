@@ -759,7 +759,7 @@ static void topo_release(Topology *t) {
     void *blocks[] = {t->rowptr, t->col, t->w, t->symmetric ? nullptr : t->crowptr,
                       t->symmetric ? nullptr : t->ccol, t->symmetric ? nullptr : t->cw,
                       t->coo_src, t->eb_src, t->eb_dst, t->eb_seg, t->pr_slot_of, t->pr_ccol,
-                      t->seg_head, t->seg_nzrow, t->seg_chunk_rank, t->blk_loc, t->blk_head,
+                      t->seg_head, t->seg_nzrow, t->seg_chunk_rank, t->blk_loc, t->blk_lane_heads,
                       t->blk_chunk_rank, t->blk_nzrow, t->blk_bchunk, t->blk_order, t->blk_deg,
                       t->blk_cta};
     for (void *b : blocks) dfree(b, nullptr);
@@ -953,7 +953,7 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     t->pr_hot = -1; t->pr_hot_min_deg = 0; t->pr_slot_of = t->pr_ccol = nullptr;
     t->seg_head = nullptr; t->seg_nzrow = t->seg_chunk_rank = nullptr; t->seg_nnzrow = 0;
     t->blk_S = 0; t->blk_nb = 0; t->blk_nchunks = 0; t->blk_nruns = 0;
-    t->blk_loc = nullptr; t->blk_head = nullptr;
+    t->blk_loc = nullptr; t->blk_lane_heads = nullptr;
     t->blk_chunk_rank = t->blk_nzrow = t->blk_bchunk = t->blk_order = t->blk_deg = nullptr;
     t->blk_cta = nullptr; t->blk_G = 0;
     g2_graph *g = new_handle(t);

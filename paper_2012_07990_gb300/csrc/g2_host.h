@@ -132,16 +132,16 @@ struct Topology {
     int32_t seg_nnzrow;
     // source-blocked sweep layout (g2_pr_blk.cu): sources per block (0 = not
     // built), blocks, 256-arc chunks, runs; per arc the source's rank within
-    // its block; run-head flags; runs before every chunk; destination rank of
-    // every run; first chunk of every block; vertex of every rank and its
-    // out-degree
+    // its block; per lane of a chunk its head flags and the heads before it;
+    // runs before every chunk; destination rank of every run; first chunk of
+    // every block; vertex of every rank and its out-degree
     int32_t blk_S;
     int32_t blk_nb;
     int32_t blk_G;            // CTAs of the sweep (one per SM)
     int64_t blk_nchunks;
     int32_t blk_nruns;
     uint16_t *blk_loc;
-    uint32_t *blk_head;
+    uint16_t *blk_lane_heads;
     int32_t *blk_chunk_rank, *blk_nzrow, *blk_bchunk, *blk_order, *blk_deg;
     int32_t *blk_cta;         // first chunk of every CTA of the sweep (blk_G + 1)
     DevGraph view() const {

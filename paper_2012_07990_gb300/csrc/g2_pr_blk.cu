@@ -193,6 +193,19 @@ __global__ void k_blk_chunk_heads(const uint32_t *head, int64_t nchunks, int32_t
     }
 }
 
+// per lane of every chunk: its 8 head flags and the heads before it in the
+// chunk, (prefix << 8) | flags
+__global__ void k_blk_lane_heads(const uint32_t *head, int64_t lanes, uint16_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lanes;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = i >> 2, w0 = (i >> 5) * kBlkHeadWords;
+        const int sh = (int)(i & 3) * 8;
+        int prefix = __popc(head[w] & ((1u << sh) - 1u));
+        for (int64_t j = w0; j < w; ++j) prefix += __popc(head[j]);
+        out[i] = (uint16_t)((prefix << 8) | ((head[w] >> sh) & 0xFFu));
+    }
+}
+
 // nzrow[k] = destination rank of the k-th run
 __global__ void k_blk_nzrow(const uint32_t *head, const int32_t *chunk_rank, const int32_t *dst,
                             int64_t words, int32_t *nzrow) {
@@ -361,11 +374,11 @@ static g2_status stable_partition(g2_graph *g, const int32_t *vals, int32_t div,
 }
 
 static void free_blk(Topology *t, cudaStream_t st) {
-    void *blocks[] = {t->blk_loc, t->blk_head, t->blk_chunk_rank, t->blk_nzrow, t->blk_bchunk,
+    void *blocks[] = {t->blk_loc, t->blk_lane_heads, t->blk_chunk_rank, t->blk_nzrow, t->blk_bchunk,
                       t->blk_order, t->blk_deg, t->blk_cta};
     for (void *p : blocks) dfree(p, st);
     t->blk_loc = nullptr;
-    t->blk_head = nullptr;
+    t->blk_lane_heads = nullptr;
     t->blk_chunk_rank = t->blk_nzrow = t->blk_bchunk = t->blk_order = t->blk_deg = nullptr;
     t->blk_cta = nullptr;
     t->blk_S = 0;
@@ -432,30 +445,35 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
         dfree(srank, st);
         dfree(pos, st);
         const int64_t words = total / 32, nchunks = total / kBlkArcs;
-        G2_CK(dmalloc(&t->blk_head, ((size_t)words + kPad) * 4, st));
-        G2_CK(cudaMemsetAsync(t->blk_head + words, 0, kPad * 4, st));
-        k_blk_heads<<<grid_for(g, words, kCta), kCta, 0, st>>>(dst, total, t->blk_head);
-        k_blk_mark_starts<<<(nb + 1 + kCta - 1) / kCta, kCta, 0, st>>>(pstart, nb, total,
-                                                                       t->blk_head, t->blk_bchunk);
+        uint32_t *head = nullptr;
+        G2_CK(dmalloc(&head, ((size_t)words + kPad) * 4, st));
+        G2_CK(cudaMemsetAsync(head + words, 0, kPad * 4, st));
+        k_blk_heads<<<grid_for(g, words, kCta), kCta, 0, st>>>(dst, total, head);
+        k_blk_mark_starts<<<(nb + 1 + kCta - 1) / kCta, kCta, 0, st>>>(pstart, nb, total, head,
+                                                                       t->blk_bchunk);
         int32_t *ccount = nullptr;
         G2_CK(dmalloc(&ccount, (size_t)nchunks * 4, st));
-        G2_CK(dmalloc(&t->blk_chunk_rank, ((size_t)nchunks + 1) * 4, st));
-        k_blk_chunk_heads<<<grid_for(g, nchunks, kCta), kCta, 0, st>>>(t->blk_head, nchunks, ccount);
+        G2_CK(dmalloc(&t->blk_chunk_rank, ((size_t)nchunks + kPad) * 4, st));
+        k_blk_chunk_heads<<<grid_for(g, nchunks, kCta), kCta, 0, st>>>(head, nchunks, ccount);
         G2_TRY(exclusive_scan_i32(g, ccount, t->blk_chunk_rank, (int32_t)nchunks, st));
         G2_CK(cudaMemcpyAsync(g->h_ctr + 51, t->blk_chunk_rank + nchunks, 4, cudaMemcpyDeviceToHost,
                               st));
         G2_CK(cudaStreamSynchronize(st));
         const int32_t nruns = g->h_ctr[51];
         G2_CK(dmalloc(&t->blk_nzrow, ((size_t)nruns + 1) * 4, st));
-        k_blk_nzrow<<<grid_for(g, words, kCta), kCta, 0, st>>>(t->blk_head, t->blk_chunk_rank, dst,
-                                                               words, t->blk_nzrow);
+        k_blk_nzrow<<<grid_for(g, words, kCta), kCta, 0, st>>>(head, t->blk_chunk_rank, dst, words,
+                                                               t->blk_nzrow);
+        const int64_t lanes = nchunks * 32;
+        G2_CK(dmalloc(&t->blk_lane_heads, ((size_t)lanes + kPad) * 2, st));
+        k_blk_lane_heads<<<grid_for(g, lanes, kCta), kCta, 0, st>>>(head, lanes, t->blk_lane_heads);
         int32_t runcost = kBlkRunCost;
         if (const char *e = getenv("G2_PR_BLK_RUNCOST")) runcost = std::max(0, atoi(e));
         k_blk_cta_split<<<(G + 1 + kCta - 1) / kCta, kCta, 0, st>>>(t->blk_chunk_rank, nchunks, G,
                                                                     runcost, t->blk_cta);
-        stats().launches += 8;
+        stats().launches += 9;
         dfree(ccount, st);
         dfree(dst, st);
+        dfree(head, st);
         t->blk_nruns = nruns;
     } else {
         G2_CK(cudaMemsetAsync(t->blk_bchunk, 0, ((size_t)nb + 1) * 4, st));
@@ -510,7 +528,7 @@ g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *ran
         double *dprev = dd + 2 + (it & 1);
         KTime kt;
         ktime_begin(kt, "pr_round", st);
-        kern<<<grid, kBlkCta, smem, st>>>(reinterpret_cast<const uint4 *>(t->blk_loc), t->blk_head,
+        kern<<<grid, kBlkCta, smem, st>>>(reinterpret_cast<const uint4 *>(t->blk_loc), t->blk_lane_heads,
                                           t->blk_chunk_rank, t->blk_nzrow, t->blk_bchunk,
                                           t->blk_nb, t->blk_cta, S, nshare, cbuf[it & 1], y,
                                           dd + 8, dprev);

@@ -10,10 +10,11 @@
 // fill a CTA's shared memory.  The CSC arcs are partitioned stably by the
 // block of their source, so inside a block the arcs of one destination stay
 // contiguous (a run); each block is padded to whole chunks of kBlkArcs arcs.
-// Per arc: the source's rank within its block (16 bits) and a head bit (the
-// first arc of a run, and the first arc of every block).  Per run: its
-// destination's rank (nzrow; padding runs point at the spare slot n).  Per
-// chunk: the number of runs that start before it.
+// Per arc: the source's rank within its block (16 bits).  Per lane of a
+// chunk (8 arcs): its head flags (bit k: arc k is the first of a run, or of a
+// block) and the heads before it in the chunk, in one 16-bit word.  Per run:
+// its destination's rank (nzrow; padding runs point at the spare slot n).
+// Per chunk: the number of runs that start before it.
 //
 // One CTA per SM takes an equal range of chunks.  For each block its range
 // touches it copies that block's shares into shared memory once, then its
@@ -44,14 +45,15 @@ constexpr int kBlkDefaultS = 49152;
 // kBlkRunCost per run (a run costs a row lookup and a reduction into y, about
 // four arcs' worth of gathers and sums, measured on RMAT-21).  Sparse blocks
 // (low-degree sources, a run per arc or two) would otherwise leave the CTAs
-// that draw them several times behind the others.
-constexpr int kBlkRunCost = 4;
+// that draw them several times behind the others.  (4-5 measured best on
+// RMAT-22.)
+constexpr int kBlkRunCost = 5;
 
 // shared memory of a launch with blocks of S sources
 __host__ __device__ constexpr size_t blk_smem_bytes(int S) { return (size_t)S * 4; }
 
 template <int CTA>
-__global__ void __launch_bounds__(CTA, 1) k_pr_blk(const uint4 *loc4, const uint32_t *head,
+__global__ void __launch_bounds__(CTA, 1) k_pr_blk(const uint4 *loc4, const uint16_t *lane_heads,
                                                    const int32_t *chunk_rank, const int32_t *nzrow,
                                                    const int32_t *bchunk, int32_t nb,
                                                    const int32_t *cta_chunk, int32_t S,
@@ -63,9 +65,10 @@ __global__ void __launch_bounds__(CTA, 1) k_pr_blk(const uint4 *loc4, const uint
     if (dslots && blockIdx.x == 0 && threadIdx.x < 32) fold_dslots(dslots, dfin);
     constexpr int W = CTA / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // this CTA's chunks: an equal share of the cost (arcs + runs)
-    int64_t c0 = cta_chunk[blockIdx.x];
-    const int64_t c1 = cta_chunk[blockIdx.x + 1];
+    // this CTA's chunks: an equal share of the cost (arcs + runs); chunk
+    // indices fit 32 bits (fewer than 2^31 arcs, 256 per chunk)
+    int32_t c0 = cta_chunk[blockIdx.x];
+    const int32_t c1 = cta_chunk[blockIdx.x + 1];
     if (c0 >= c1) return;
     // block of chunk c0: the last b with bchunk[b] <= c0 (bchunk[0] = 0)
     int lo = 0, hi = nb - 1;
@@ -75,10 +78,8 @@ __global__ void __launch_bounds__(CTA, 1) k_pr_blk(const uint4 *loc4, const uint
         else hi = mid - 1;
     }
     int b = lo;
-    const int sh = (lane & 3) * 8;  // this lane's byte in its chunk's head word lane / 4
-    const int hword = lane >> 2;
     while (c0 < c1) {
-        const int64_t cend = min(c1, (int64_t)bchunk[b + 1]);
+        const int32_t cend = min(c1, bchunk[b + 1]);
         if (cend > c0) {
             __syncthreads();  // every warp is done with the previous block's shares
             const int64_t s0 = (int64_t)b * S;
@@ -87,26 +88,32 @@ __global__ void __launch_bounds__(CTA, 1) k_pr_blk(const uint4 *loc4, const uint
             float4 *dst = reinterpret_cast<float4 *>(s_sh);
             for (int i = threadIdx.x; i < len4; i += CTA) dst[i] = __ldg(src + i);
             __syncthreads();
-            // software pipeline: the next chunk's ids, head byte and run base
-            // are loaded, and its run rows prefetched into L1, while this
-            // chunk is summed
-            int64_t c = c0 + warp;
+            // software pipeline: the next chunk's ids, head word and run base
+            // are loaded while this chunk is summed
+            int32_t c = c0 + warp;
+            const uint4 *lp = loc4 + (size_t)c * 32 + lane;
+            const uint16_t *hp = lane_heads + (size_t)c * 32 + lane;
+            const int32_t *rp = chunk_rank + c;
             uint4 nl = make_uint4(0, 0, 0, 0);
-            uint32_t nhw = 0;
+            uint32_t nh = 0;
             int32_t nrk = 0;
             if (c < cend) {
-                nl = loc4[c * 32 + lane];
-                nhw = head[c * kBlkHeadWords + hword];
-                nrk = chunk_rank[c];
+                nl = *lp;
+                nh = *hp;
+                nrk = *rp;
             }
             for (; c < cend; c += W) {
                 const uint4 l = nl;
-                const uint32_t hf = (nhw >> sh) & 0xFFu;
+                const uint32_t hf = nh & 0xFFu;         // heads among this lane's arcs
+                const int32_t prefix = (int32_t)(nh >> 8);  // heads before this lane
                 const int32_t base_rank = nrk;
+                lp += W * 32;
+                hp += W * 32;
+                rp += W;
                 if (c + W < cend) {
-                    nl = loc4[(c + W) * 32 + lane];
-                    nhw = head[(c + W) * kBlkHeadWords + hword];
-                    nrk = chunk_rank[c + W];
+                    nl = *lp;
+                    nh = *hp;
+                    nrk = *rp;
                 }
                 float v[8];
                 v[0] = s_sh[l.x & 0xFFFFu];
@@ -117,48 +124,52 @@ __global__ void __launch_bounds__(CTA, 1) k_pr_blk(const uint4 *loc4, const uint
                 v[5] = s_sh[l.z >> 16];
                 v[6] = s_sh[l.w & 0xFFFFu];
                 v[7] = s_sh[l.w >> 16];
-                // heads before this lane in the chunk, and in the whole chunk
-                const int nh = __popc(hf);
-                const int incl = warp_incl_scan(nh);
-                const int prefix = incl - nh;
-                const int total_heads = __shfl_sync(G2_FULL, incl, 31);
-                // lane-local pieces: A = arcs before the first head, inner
-                // complete runs (one reduction each), T = arcs from the last
-                // head on
+                const int32_t total_heads = __shfl_sync(G2_FULL, prefix + __popc(hf), 31);
+                // row of the run open at this lane's first arc, then one per head
+                const int32_t *nzb = nzrow + (base_rank + prefix - 1);
+                // lane-local pieces: A = arcs before the lane's first head (all
+                // of them without a head), inner runs closed by a later head of
+                // the lane (one reduction each), run = arcs from the last head on
                 float A = 0.f, run = 0.f;
-                int seen = 0;
+                const int f = hf ? __ffs(hf) - 1 : 8;  // first head (8: none)
+                if (!__any_sync(G2_FULL, __popc(hf) >= 2)) {
+                    // no lane of the chunk closes a run inside itself (the usual
+                    // case in the blocks of high-degree sources)
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if ((hf >> k) & 1u) {
-                        if (seen == 0) {
-                            A = run;
-                        } else if (run != 0.f) {
-                            atomicAdd(y + nzrow[base_rank + prefix + seen - 1], run);
-                        }
-                        run = 0.f;
-                        ++seen;
+                    for (int k = 0; k < 8; ++k) {
+                        if (k < f) A += v[k];
+                        else run += v[k];
                     }
-                    run += v[k];
+                } else {
+                    int j = 0;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const bool h = (hf >> k) & 1u;
+                        if (h && k > f) atomicAdd(y + nzb[j], run);
+                        if (k == f) A = run;
+                        j += h;
+                        run = h ? v[k] : run + v[k];
+                    }
+                    if (f == 8) A = run;
                 }
-                if (seen == 0) A = run;
-                const bool has_head = seen > 0;
+                const bool has_head = hf != 0;
                 // segmented inclusive scan over lanes (shares are >= 0, so the
                 // head flag travels in the sign bit: one shuffle per step)
                 float q = has_head ? run : A;
-                bool f = has_head;
+                bool fl = has_head;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t enc = __float_as_uint(q) | (f ? 0x80000000u : 0u);
+                    const uint32_t enc = __float_as_uint(q) | (fl ? 0x80000000u : 0u);
                     const uint32_t o = __shfl_up_sync(G2_FULL, enc, d);
-                    if (lane >= d && !f) {
+                    if (lane >= d && !fl) {
                         q += __uint_as_float(o & 0x7fffffffu);
-                        f = (o >> 31) != 0u;
+                        fl = (o >> 31) != 0u;
                     }
                 }
                 float qprev = __shfl_up_sync(G2_FULL, q, 1);
                 if (lane == 0) qprev = 0.f;
                 if (has_head) {
-                    // the run that ends just before this lane's first head
+                    // the run that ends at this lane's first head
                     const float tot = qprev + A;
                     const int32_t rk = base_rank + prefix - 1;
                     if (tot != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], tot);
@@ -168,14 +179,6 @@ __global__ void __launch_bounds__(CTA, 1) k_pr_blk(const uint4 *loc4, const uint
                     // in the next chunk of the same block)
                     const int32_t rk = base_rank + total_heads - 1;
                     if (q != 0.f && rk >= 0) atomicAdd(y + nzrow[rk], q);
-                }
-                if (c + W < cend) {
-                    // rows of the next chunk's runs: nzrow[nrk - 1 ..
-                    // nrk + its heads), one 32-byte sector per lane
-                    const int nt = __reduce_add_sync(G2_FULL, __popc((nhw >> sh) & 0xFFu));
-                    const int64_t r = (int64_t)nrk - 1 + 8 * lane;
-                    if (r >= 0 && 8 * lane <= nt)
-                        asm volatile("prefetch.global.L1 [%0];" ::"l"(nzrow + r));
                 }
             }
         }
