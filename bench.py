@@ -171,6 +171,7 @@ def run_ours(args):
     src = G.max_degree_vertex()
     dg = g2.load_graph(G)
     depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
     label = torch.empty(n, dtype=torch.int32, device="cuda")
     rank_t = torch.empty(n, dtype=torch.float32, device="cuda")
     sb, sc = bfs_schedule(g2), cc_schedule(g2)
@@ -185,7 +186,7 @@ def run_ours(args):
     pool = ThreadPoolExecutor(2)
 
     def bfs_job():
-        g2.g2_bfs(views["bfs"], src, depth, None, sb, stream=streams["bfs"])
+        g2.g2_bfs(views["bfs"], src, depth, parent, sb, stream=streams["bfs"])
         return g2.g2_last_stats()["launches"]
 
     def cc_job():
@@ -201,7 +202,7 @@ def run_ours(args):
         # the per-algorithm split: the three one after another on this stream
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         evs[0].record()
-        g2.g2_bfs(dg, src, depth, None, sb)
+        g2.g2_bfs(dg, src, depth, parent, sb)
         evs[1].record()
         g2.g2_cc(dg, label, sc)
         evs[2].record()
@@ -281,6 +282,9 @@ def run_ours(args):
     for v in views.values():
         v.free()
     e2e = run_e2e(args, g2, G, src, sb, sc, edges_per_step) if not args.no_e2e else None
+    extras = None
+    if rank == 0 and ws == 1 and not args.no_extras:
+        extras = run_extras(g2, G, dg, src, sb, sc)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(G, src, budget_s=args.cpu_budget)
@@ -296,6 +300,7 @@ def run_ours(args):
                        "graph": f"RMAT scale {args.scale}, ef 16, (0.57,0.19,0.19,0.05), seed 1, symmetric",
                        "n": n, "m": m, "src": src, "pr_rounds": PR_ITERS, "damping": DAMPING,
                        "edges_per_step": edges_per_step, "bfs_reached_arcs": m_bfs,
+                       "bfs_parent": True,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (CSR 513 MB vs 129 MB L2); no flush"},
             "per_algo": {"bfs_ms": round(bfs_ms, 4), "cc_ms": round(cc_ms, 4), "pr_ms": round(pr_ms, 4),
@@ -303,6 +308,7 @@ def run_ours(args):
                          "cc_gteps": round(m / cc_ms / 1e6, 2),
                          "pr_gteps": round(PR_ITERS * m / pr_ms / 1e6, 2)},
             "roofline": roofline,
+            "workloads": extras,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": launches["n"],
@@ -323,7 +329,8 @@ def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
     (two graphs resident), so the host link overlaps the kernels; within a
     step BFS and CC run beside PageRank, as in the device-timed step.  The timed
     region holds every step's upload (the first one included), compute and
-    read-back; `serial_ms_per_step` is the same step run one after another."""
+    read-back; `serial_ms_per_step` is the same step run one after another.
+    Results read back per step: BFS depth and parent, CC labels, PageRank."""
     import torch
     from concurrent.futures import ThreadPoolExecutor
     n, m = G.n, G.m
@@ -332,6 +339,8 @@ def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
     rp_np = np.frombuffer(h_rp.numpy().data, dtype=np.int32)
     col_np = np.frombuffer(h_col.numpy().data, dtype=np.int32)
     h_depth = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_parent = torch.empty(n, dtype=torch.int32).pin_memory()
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
     h_label = torch.empty(n, dtype=torch.int32).pin_memory()
     h_rank = torch.empty(n, dtype=torch.float32).pin_memory()
     depth = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -347,9 +356,10 @@ def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
                               prepare_pagerank=True, overlap=True)
 
     def bfs_job(v):
-        g2.g2_bfs(v, src, depth, None, sb, stream=s_bfs)
+        g2.g2_bfs(v, src, depth, parent, sb, stream=s_bfs)
         with torch.cuda.stream(s_bfs):
             h_depth.copy_(depth, non_blocking=True)
+            h_parent.copy_(parent, non_blocking=True)
         s_bfs.synchronize()
 
     def cc_job(v):
@@ -403,7 +413,170 @@ def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
     return {"value": round(edges_per_step / (ms * 1e-3) / 1e9, 2), "unit": "GTEPS",
             "ms_per_step": round(ms, 3), "steps": k, "pipelined": True,
             "serial_ms_per_step": round(serial_ms, 3),
-            "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 12 * n}
+            "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 16 * n}
+
+
+def run_extras(g2, G22, dg22, src22, sb, sc):
+    """The rest of the workloads the metric is quoted on, each timed with CUDA
+    events after a warm-up call (bounded to well under a minute in all):
+
+    * RMAT-22 BFS (tuned, with parent) and CC (tuned): arcs examined from a
+      separate counting pass, algorithmic bytes (BFS 4 per examined arc + 12 n;
+      CC 4 per examined arc + 8 n) over the measured time against the
+      measured HBM peak;
+    * RMAT-14 BFS, the plain single-query path;
+    * the 4096 x 4096 road grid: BFS and delta-stepping SSSP (delta 1024 and
+      16384), fused persistent loop against plain per-round launches;
+    * RMAT-21 batched: 64-source BFS in one traversal against 64 single-source
+      calls (tuned schedule and the fixed TWC PUSH schedule), 32-source SSSP
+      against 32 single calls, BC from 16 sources;
+    * serving over the resident pool (RMAT 16-22, grids 512^2-4096^2):
+      continuous batching against one launch per query, at 2,000 requests/s
+      (more than one GPU serves: latency is mostly queueing) and at 500/s."""
+    import torch
+    from paper_2012_07990_gb300 import graphgen as gg
+    from paper_2012_07990_gb300 import serve
+    t_start = time.time()
+    peak, _ = read_peaks()
+    out = {}
+
+    def dev(k, dtype=torch.int32):
+        return torch.empty(k, dtype=dtype, device="cuda")
+
+    def reached_arcs(G, vals, unreached):
+        return int(G.degrees()[vals.cpu().numpy() != unreached].sum())
+
+    def bfs_cc_rows(G, dg, src, with_cc):
+        n = G.n
+        depth, parent, label = dev(n), dev(n), dev(n)
+        g2.g2_set_count_arcs(True)
+        g2.g2_bfs(dg, src, depth, parent, sb)
+        bfs_arcs = g2.g2_last_stats()["arcs_examined"]
+        cc_arcs = 0
+        if with_cc:
+            g2.g2_cc(dg, label, sc)
+            cc_arcs = g2.g2_last_stats()["arcs_examined"]
+        g2.g2_set_count_arcs(False)
+        ms = _timed(lambda: g2.g2_bfs(dg, src, depth, parent, sb), reps=7)
+        ms_np = _timed(lambda: g2.g2_bfs(dg, src, depth, None, sb), reps=7)
+        reached = reached_arcs(G, depth, -1)
+        b = 4 * bfs_arcs + 12 * n
+        rows = {"bfs": {"ms": round(ms, 4), "gteps": round(reached / ms / 1e6, 2), "reached_arcs": reached,
+                        "arcs_examined": int(bfs_arcs), "bytes": int(b),
+                        "achieved_gbs": round(b / ms / 1e6, 1), "frac": round(b / ms / 1e6 / peak, 4),
+                        "ms_without_parent": round(ms_np, 4)}}
+        if with_cc:
+            ms = _timed(lambda: g2.g2_cc(dg, label, sc), reps=7)
+            b = 4 * cc_arcs + 8 * n
+            rows["cc"] = {"ms": round(ms, 4), "gteps_nominal": round(G.m / ms / 1e6, 2),
+                          "arcs_examined": int(cc_arcs), "bytes": int(b),
+                          "achieved_gbs": round(b / ms / 1e6, 1), "frac": round(b / ms / 1e6 / peak, 4),
+                          "note": "gteps_nominal = all arcs / time; the tuned CC links only the arcs examined"}
+        return rows
+
+    # RMAT-22 BFS and CC
+    r = bfs_cc_rows(G22, dg22, src22, True)
+    out["rmat22_bfs"], out["rmat22_cc"] = r["bfs"], r["cc"]
+    # RMAT-14, plain single-query BFS
+    G14 = gg.rmat(14, seed=1)
+    dg14 = g2.load_graph(G14)
+    out["rmat14_bfs"] = bfs_cc_rows(G14, dg14, G14.max_degree_vertex(), False)["bfs"]
+    dg14.free()
+
+    # road grid 4096^2, fused against plain
+    Gg = gg.road_grid(4096, seed=1)
+    wg = gg.pair_weights(Gg, 1000, seed=1)
+    dgg = g2.load_graph(Gg, wg)
+    depth, dist = dev(Gg.n), dev(Gg.n)
+    strict = g2.schedule("STRICT")
+    grid = {}
+    for name, s_, reps in (("fused", None, 3), ("plain", strict, 2)):
+        ms = _timed(lambda: g2.g2_bfs(dgg, 0, depth, None, s_), reps=reps)
+        st = g2.g2_last_stats()
+        grid[f"bfs_{name}"] = {"ms": round(ms, 3), "levels": st["iterations"], "launches": st["launches"],
+                               "gteps": round(reached_arcs(Gg, depth, -1) / ms / 1e6, 3)}
+    for delta, names in ((1024, (("fused", None, 2), ("plain", strict, 1))), (16384, (("fused", None, 2),))):
+        for name, s_, reps in names:
+            ms = _timed(lambda: g2.g2_sssp_delta(dgg, 0, delta, dist, s_), reps=reps)
+            st = g2.g2_last_stats()
+            grid[f"sssp_d{delta}_{name}"] = {
+                "ms": round(ms, 3), "rounds": st["iterations"], "launches": st["launches"],
+                "gteps": round(reached_arcs(Gg, dist, 2**31 - 1) / ms / 1e6, 3)}
+    grid["fused_vs_plain"] = {"bfs": round(grid["bfs_plain"]["ms"] / grid["bfs_fused"]["ms"], 2),
+                              "sssp_d1024": round(grid["sssp_d1024_plain"]["ms"] / grid["sssp_d1024_fused"]["ms"], 2)}
+    out["grid4096"] = grid
+    dgg.free()
+
+    # RMAT-21 batched
+    G21 = gg.rmat(21, seed=1)
+    w21 = gg.pair_weights(G21, 255, seed=1)
+    dg21 = g2.load_graph(G21, w21)
+    srcs = gg.random_sources(G21, 64, seed=1)
+    deg = G21.degrees()
+    b = {}
+    d64 = dev(64 * G21.n)
+    ms = _timed(lambda: g2.g2_bfs_batch(dg21, srcs, d64, None), reps=3)
+    d = d64.cpu().numpy().reshape(64, G21.n)
+    edges = int(sum(deg[d[i] >= 0].sum() for i in range(64)))
+    b["bfs64_batched"] = {"ms": round(ms, 3), "gteps": round(edges / ms / 1e6, 2)}
+    one = dev(G21.n)
+    for name, s_ in (("tuned", None), ("twc_push", g2.schedule("TWC"))):
+        def loop(s_=s_):
+            for v in srcs:
+                g2.g2_bfs(dg21, int(v), one, None, s_)
+        ms1 = _timed(loop, reps=1)
+        b[f"bfs64_serial_{name}"] = {"ms": round(ms1, 3), "gteps": round(edges / ms1 / 1e6, 2)}
+    d32 = dev(32 * G21.n)
+    ms = _timed(lambda: g2.g2_sssp_batch(dg21, srcs[:32], 64, d32, None), reps=2)
+    dd = d32.cpu().numpy().reshape(32, G21.n)
+    edges32 = int(sum(deg[dd[i] < 2**31 - 1].sum() for i in range(32)))
+    b["sssp32_batched"] = {"ms": round(ms, 3), "gteps": round(edges32 / ms / 1e6, 2)}
+
+    def loop_sssp():
+        for v in srcs[:32]:
+            g2.g2_sssp_delta(dg21, int(v), 64, one, None)
+    ms1 = _timed(loop_sssp, reps=1)
+    b["sssp32_serial"] = {"ms": round(ms1, 3), "gteps": round(edges32 / ms1 / 1e6, 2)}
+    bc = dev(G21.n, torch.float64)
+    ms = _timed(lambda: g2.g2_bc(dg21, srcs[:16], bc, None), reps=1)
+    edges16 = int(sum(deg[d[i] >= 0].sum() for i in range(16)))
+    b["bc16"] = {"ms": round(ms, 3), "gteps": round(2 * edges16 / ms / 1e6, 2),
+                 "note": "forward and backward sweeps counted"}
+    b["speedup"] = {"bfs64_vs_serial_tuned": round(b["bfs64_serial_tuned"]["ms"] / b["bfs64_batched"]["ms"], 2),
+                    "bfs64_vs_serial_twc_push": round(b["bfs64_serial_twc_push"]["ms"] / b["bfs64_batched"]["ms"], 2),
+                    "sssp32_vs_serial": round(b["sssp32_serial"]["ms"] / b["sssp32_batched"]["ms"], 2)}
+    out["rmat21_batched"] = b
+    dg21.free()
+    del d64, d32
+
+    # serving over the full pool (RMAT-22 and the 4096^2 grid reuse the
+    # graphs generated above)
+    cached = {"rmat22": G22, "grid4096": Gg}
+    specs = serve.default_pool_specs()
+    for sp in specs:
+        if sp.name in cached:
+            sp.make = (lambda G=cached[sp.name]: G)
+    pool = serve.GraphPool(g2, specs)
+    sv = {}
+    ex4 = serve.GpuExecutor(g2, pool, slots=4)
+    ex1 = serve.GpuExecutor(g2, pool, slots=1)
+    for rate, duration in ((2000.0, 0.25), (500.0, 1.0)):
+        trace = serve.make_trace(pool, rate=rate, duration=duration, seed=1)
+        srv = serve.Server(ex4, pool, policy="hrrn")
+        srv.run(trace[: min(128, len(trace))])  # warm views, workspaces and the cost model
+        cb = srv.run(trace).summary()
+        serial = serve.Server(ex1, pool, max_batch=dict(bfs=1, sssp=1, bc=1), policy="fifo").run(trace).summary()
+        sv[f"rate{int(rate)}"] = {"requests": len(trace), "duration_s": duration,
+                                  "continuous_batching": cb, "serial_plain": serial}
+    out["serving"] = sv
+    for ex in (ex4, ex1):
+        for views in ex.views:
+            for v in views.values():
+                v.free()
+    for g in pool.graphs.values():
+        g.handle.free()
+    out["seconds"] = round(time.time() - t_start, 1)
+    return out
 
 
 def read_traffic(kernel: str, G):
@@ -842,6 +1015,8 @@ def main():
     ap.add_argument("--scale", type=int, default=22)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (RMAT-14, grid, batched, serving) in the default line")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     args = ap.parse_args()
     if args.profile_case:

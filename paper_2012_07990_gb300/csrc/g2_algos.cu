@@ -78,11 +78,19 @@ __device__ __forceinline__ void cc_link(int32_t *label, int32_t u, int32_t v) {
 
 // link every vertex with its r-th neighbour
 __global__ void k_cc_sample(const int32_t *rowptr, const int32_t *col, int32_t n, int32_t r,
-                            int32_t *label) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        int32_t b = rowptr[v];
-        if (rowptr[v + 1] - b > r) cc_link(label, (int32_t)v, col[b + r]);
+                            int32_t *label, unsigned long long *ctr) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + threadIdx.x;
+        bool linked = false;
+        if (v < n) {
+            int32_t b = rowptr[v];
+            if (rowptr[v + 1] - b > r) {
+                cc_link(label, (int32_t)v, col[b + r]);
+                linked = true;
+            }
+        }
+        count_arcs(ctr, linked);
     }
 }
 
@@ -101,7 +109,7 @@ __global__ void k_cc_probe(const int32_t *label, int32_t n, int32_t k, int32_t *
 // link the remaining arcs (from position `skip` on) of every vertex outside
 // the component `giant`; a warp walks one vertex so long lists are shared
 __global__ void k_cc_finish(const int32_t *rowptr, const int32_t *col, int32_t n, int32_t skip,
-                            int32_t giant, int32_t *label) {
+                            int32_t giant, int32_t *label, unsigned long long *ctr) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -115,6 +123,7 @@ __global__ void k_cc_finish(const int32_t *rowptr, const int32_t *col, int32_t n
             int32_t u = (int32_t)(base + src);
             int32_t b = rowptr[u] + skip, e = rowptr[u + 1];
             for (int32_t k = b + lane; k < e; k += 32) cc_link(label, u, col[k]);
+            if (ctr && lane == 0) atomicAdd(ctr, (unsigned long long)(e - b));
         }
     }
 }
@@ -370,9 +379,13 @@ g2_status cc_sampled(g2_graph *g, int32_t *label, cudaStream_t st, int32_t *d_er
     if (n == 0) return G2_OK;
     constexpr int kSample = 2, kProbe = 1024;
     const int grid = grid_for(g, n, kCta);
+    // arcs linked (stats mode): one per vertex and sampling round, then the
+    // remaining arcs of the vertices outside the giant component
+    unsigned long long *ctr = nullptr;
+    if (count_arcs_enabled()) G2_TRY(ws(g, B_ARCS, 2, &ctr));
     k_iota<<<grid, kCta, 0, st>>>(label, n);
     for (int r = 0; r < kSample; ++r) {
-        k_cc_sample<<<grid, kCta, 0, st>>>(t->rowptr, t->col, n, r, label);
+        k_cc_sample<<<grid, kCta, 0, st>>>(t->rowptr, t->col, n, r, label, ctr);
         k_compress<<<grid, kCta, 0, st>>>(label, n);
     }
     int32_t *probe;
@@ -393,7 +406,8 @@ g2_status cc_sampled(g2_graph *g, int32_t *label, cudaStream_t st, int32_t *d_er
         }
         i = j;
     }
-    k_cc_finish<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->rowptr, t->col, n, kSample, giant, label);
+    k_cc_finish<<<grid_for(g, n, kCta), kCta, 0, st>>>(t->rowptr, t->col, n, kSample, giant, label,
+                                                        ctr);
     k_compress<<<grid, kCta, 0, st>>>(label, n);
     stats().launches += 2 * kSample + 5;
     stats().iterations = kSample + 1;

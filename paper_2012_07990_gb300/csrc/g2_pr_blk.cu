@@ -124,11 +124,63 @@ __global__ void k_blk_order(const int32_t *rowptr, const int32_t *rank, int32_t 
     }
 }
 
-// rank of the source of every CSC arc
-__global__ void k_blk_arc_rank(const int32_t *ccol, const int32_t *rank, int32_t m, int32_t *out) {
+// per CSC arc e of row v: the rank of v, a warp per row (stores only, so a
+// long row costs its stores and nothing else)
+__global__ void k_blk_dst_ranks(const int32_t *crowptr, const int32_t *rank, int32_t n,
+                                int32_t *drank) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = gw; v < n; v += nw) {
+        const int32_t b = crowptr[v], e = crowptr[v + 1];
+        if (b == e) continue;
+        const int32_t rv = rank[v];
+        for (int32_t k = b + lane; k < e; k += 32) drank[k] = rv;
+    }
+}
+
+// per CSC arc: the rank of its source
+__global__ void k_blk_src_ranks(const int32_t *ccol, const int32_t *rank, int32_t m,
+                                int32_t *srank) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = rank[ccol[e]];
+        srank[e] = rank[ccol[e]];
+}
+
+// The position pass of the stable partition of the arcs by source block
+// (keys srank / S), placing every arc directly: its source's rank within the
+// block and its destination's rank go to its position.  A warp's stores
+// fall into one contiguous run per block present among its 32 arcs.
+__global__ void __launch_bounds__(kPartCta) k_blk_place(const int32_t *srank, const int32_t *drank,
+                                                        int32_t S, int64_t count, int32_t nkeys,
+                                                        int32_t ntiles, const int32_t *scan,
+                                                        const int32_t *shift, uint16_t *loc,
+                                                        int32_t *dst) {
+    extern __shared__ int32_t s_part[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    int32_t *c = s_part + wid * nkeys;
+    const int32_t wpc = kPartCta / 32;
+    for (int32_t tile = blockIdx.x * wpc + wid; tile < ntiles; tile += gridDim.x * wpc) {
+        for (int k = lane; k < nkeys; k += 32) c[k] = scan[(int64_t)k * ntiles + tile] + shift[k];
+        __syncwarp();
+        const int64_t base = (int64_t)tile * kPartTile;
+        for (int s = 0; s < kPartTile / 32; ++s) {
+            const int64_t i = base + s * 32 + lane;
+            const int32_t sr = i < count ? srank[i] : 0;
+            const int key = i < count ? sr / S : -1;
+            const unsigned peers = __match_any_sync(G2_FULL, key);
+            const int r = __popc(peers & lt);
+            if (key >= 0) {
+                const int32_t p = c[key] + r;
+                loc[p] = (uint16_t)(sr - key * S);
+                dst[p] = drank[i];
+            }
+            __syncwarp();
+            if (key >= 0 && r == 0) c[key] += __popc(peers);
+            __syncwarp();
+        }
+    }
 }
 
 static __global__ void k_fill_i32_blk(int32_t *p, int64_t count, int32_t v) {
@@ -137,41 +189,20 @@ static __global__ void k_fill_i32_blk(int32_t *p, int64_t count, int32_t v) {
         p[i] = v;
 }
 
-// a warp per CSC row v: every arc e of the row goes to pos[e] with its
-// source's rank within the block and v's rank
-__global__ void k_blk_scatter(const int32_t *crowptr, int32_t n, const int32_t *rank,
-                              const int32_t *srank, const int32_t *pos, int32_t S, uint16_t *loc,
-                              int32_t *dst) {
+// head bit of position p: its destination differs from position p-1's
+// (block starts are marked by k_blk_mark_starts); a warp builds a word at a
+// time from its lanes' comparisons, so the loads are coalesced
+__global__ void k_blk_heads(const int32_t *dst, int64_t total, uint32_t *head) {
+    const int64_t words = total / 32;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
-    for (int64_t v = gw; v < n; v += nw) {
-        const int32_t b = crowptr[v], e = crowptr[v + 1];
-        if (b == e) continue;
-        const int32_t rv = rank[v];
-        for (int32_t k = b + lane; k < e; k += 32) {
-            const int32_t p = pos[k];
-            loc[p] = (uint16_t)(srank[k] % S);
-            dst[p] = rv;
-        }
-    }
-}
-
-// head bit of position p: its destination differs from position p-1's
-// (block starts are marked by k_blk_mark_starts)
-__global__ void k_blk_heads(const int32_t *dst, int64_t total, uint32_t *head) {
-    const int64_t words = total / 32;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
-         w += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p0 = w * 32;
-        int32_t prev = p0 > 0 ? dst[p0 - 1] : -1;
-        uint32_t bits = 0;
-        for (int j = 0; j < 32; ++j) {
-            const int32_t d = dst[p0 + j];
-            if (d != prev) bits |= 1u << j;
-            prev = d;
-        }
-        head[w] = bits;
+    for (int64_t w = gw; w < words; w += nw) {
+        const int64_t p = w * 32 + lane;
+        const int32_t d = dst[p];
+        const int32_t prev = p > 0 ? dst[p - 1] : -1;
+        const unsigned bits = __ballot_sync(G2_FULL, d != prev);
+        if (lane == 0) head[w] = bits;
     }
 }
 
@@ -342,34 +373,58 @@ static int part_grid(const g2_graph *g, int32_t ntiles) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)g->topo->sm_count * 8));
 }
 
-// Positions of a stable partition (see k_part_count); pstart gets nkeys + 1
-// padded starts; *total the padded item count.
-static g2_status stable_partition(g2_graph *g, const int32_t *vals, int32_t div, int64_t count,
-                                  int32_t nkeys, int32_t pad, int32_t *pos, int32_t *pstart,
-                                  int64_t *total, cudaStream_t st) {
-    const int32_t ntiles = (int32_t)std::max<int64_t>(1, (count + kPartTile - 1) / kPartTile);
-    const int64_t cells = (int64_t)nkeys * ntiles;
+// The count and scan of a stable partition (see k_part_count): the scan of
+// the per-tile counts, the padded key starts (pstart, nkeys + 1 entries; the
+// padded total also in *total) and the launch shape of the position pass.
+struct PartTable {
+    int32_t *counts = nullptr, *scan = nullptr, *shift = nullptr;
+    int32_t ntiles = 0;
+    int grid = 1;
+    size_t smem = 0;
+    void release(cudaStream_t st) {
+        dfree(counts, st);
+        dfree(scan, st);
+        dfree(shift, st);
+        counts = scan = shift = nullptr;
+    }
+};
+
+static g2_status partition_table(g2_graph *g, const int32_t *vals, int32_t div, int64_t count,
+                                 int32_t nkeys, int32_t pad, int32_t *pstart, int64_t *total,
+                                 PartTable *pt, cudaStream_t st) {
+    pt->ntiles = (int32_t)std::max<int64_t>(1, (count + kPartTile - 1) / kPartTile);
+    const int64_t cells = (int64_t)nkeys * pt->ntiles;
     if (cells >= 2147483647LL) return fail(G2_EUNSUPPORTED, "partition table too large");
-    int32_t *counts = nullptr, *scan = nullptr, *shift = nullptr, *d_total;
-    G2_CK(dmalloc(&counts, (size_t)(cells + 1) * 4, st));
-    G2_CK(dmalloc(&scan, (size_t)(cells + 1) * 4, st));
-    G2_CK(dmalloc(&shift, (size_t)nkeys * 4, st));
+    int32_t *d_total;
+    G2_CK(dmalloc(&pt->counts, (size_t)(cells + 1) * 4, st));
+    G2_CK(dmalloc(&pt->scan, (size_t)(cells + 1) * 4, st));
+    G2_CK(dmalloc(&pt->shift, (size_t)nkeys * 4, st));
     G2_TRY(ws(g, B_CTR, 64, &d_total));
     d_total += 50;
-    const size_t smem = (size_t)(kPartCta / 32) * nkeys * 4;
-    const int grid = part_grid(g, ntiles);
-    k_part_count<<<grid, kPartCta, smem, st>>>(vals, div, count, nkeys, ntiles, counts);
-    G2_TRY(exclusive_scan_i32(g, counts, scan, (int32_t)cells, st));
-    k_part_starts<<<1, 1024, 0, st>>>(scan, ntiles, nkeys, pad, shift, pstart, d_total);
-    k_part_pos<<<grid, kPartCta, smem, st>>>(vals, div, count, nkeys, ntiles, scan, shift, pos);
+    pt->smem = (size_t)(kPartCta / 32) * nkeys * 4;
+    pt->grid = part_grid(g, pt->ntiles);
+    k_part_count<<<pt->grid, kPartCta, pt->smem, st>>>(vals, div, count, nkeys, pt->ntiles, pt->counts);
+    G2_TRY(exclusive_scan_i32(g, pt->counts, pt->scan, (int32_t)cells, st));
+    k_part_starts<<<1, 1024, 0, st>>>(pt->scan, pt->ntiles, nkeys, pad, pt->shift, pstart, d_total);
     G2_CK(cudaGetLastError());
     G2_CK(cudaMemcpyAsync(g->h_ctr + 50, d_total, 4, cudaMemcpyDeviceToHost, st));
     G2_CK(cudaStreamSynchronize(st));
     *total = g->h_ctr[50];
-    stats().launches += 3;
-    dfree(counts, st);
-    dfree(scan, st);
-    dfree(shift, st);
+    stats().launches += 2;
+    return G2_OK;
+}
+
+// Positions of a stable partition: pos[i] for every item.
+static g2_status stable_partition(g2_graph *g, const int32_t *vals, int32_t div, int64_t count,
+                                  int32_t nkeys, int32_t pad, int32_t *pos, int32_t *pstart,
+                                  int64_t *total, cudaStream_t st) {
+    PartTable pt;
+    G2_TRY(partition_table(g, vals, div, count, nkeys, pad, pstart, total, &pt, st));
+    k_part_pos<<<pt.grid, kPartCta, pt.smem, st>>>(vals, div, count, nkeys, pt.ntiles, pt.scan, pt.shift,
+                                                   pos);
+    G2_CK(cudaGetLastError());
+    stats().launches += 1;
+    pt.release(st);
     return G2_OK;
 }
 
@@ -426,29 +481,33 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
     int32_t *pstart = nullptr;
     G2_CK(dmalloc(&pstart, ((size_t)nb + 1) * 4, st));
     if (m > 0) {
-        // 2-3. source ranks, partition by source block
-        int32_t *srank = nullptr, *pos = nullptr, *dst = nullptr;
+        // 2-4. source and destination ranks of every arc, stable partition
+        // by source block with every arc placed in the position pass;
+        // padding keeps rank 0 in its block and points at the spare slot n
+        int32_t *srank = nullptr, *drank = nullptr, *dst = nullptr;
         G2_CK(dmalloc(&srank, (size_t)m * 4, st));
-        G2_CK(dmalloc(&pos, (size_t)m * 4, st));
-        k_blk_arc_rank<<<grid_for(g, m, kCta), kCta, 0, st>>>(t->ccol, rank, m, srank);
-        stats().launches += 1;
-        G2_TRY(stable_partition(g, srank, S, m, nb, kBlkArcs, pos, pstart, &total, st));
-        // 4. per-position block rank and destination rank; padding keeps
-        // rank 0 in its block and points at the spare slot n
+        G2_CK(dmalloc(&drank, (size_t)m * 4, st));
+        k_blk_src_ranks<<<grid_for(g, m, kCta), kCta, 0, st>>>(t->ccol, rank, m, srank);
+        k_blk_dst_ranks<<<grid_for(g, (int64_t)n * 32, kCta), kCta, 0, st>>>(t->crowptr, rank, n, drank);
+        stats().launches += 2;
+        PartTable pt;
+        G2_TRY(partition_table(g, srank, S, m, nb, kBlkArcs, pstart, &total, &pt, st));
         G2_CK(dmalloc(&t->blk_loc, ((size_t)total + kPad) * 2, st));
         G2_CK(dmalloc(&dst, (size_t)total * 4, st));
         G2_CK(cudaMemsetAsync(t->blk_loc, 0, ((size_t)total + kPad) * 2, st));
         k_fill_i32_blk<<<grid_for(g, total, kCta), kCta, 0, st>>>(dst, total, n);
-        k_blk_scatter<<<grid_for(g, (int64_t)n * 32, kCta), kCta, 0, st>>>(t->crowptr, n, rank,
-                                                                            srank, pos, S,
-                                                                            t->blk_loc, dst);
+        k_blk_place<<<pt.grid, kPartCta, pt.smem, st>>>(srank, drank, S, m, nb, pt.ntiles, pt.scan,
+                                                         pt.shift, t->blk_loc, dst);
+        stats().launches += 2;
+        G2_CK(cudaGetLastError());
+        pt.release(st);
         dfree(srank, st);
-        dfree(pos, st);
+        dfree(drank, st);
         const int64_t words = total / 32, nchunks = total / kBlkArcs;
         uint32_t *head = nullptr;
         G2_CK(dmalloc(&head, ((size_t)words + kPad) * 4, st));
         G2_CK(cudaMemsetAsync(head + words, 0, kPad * 4, st));
-        k_blk_heads<<<grid_for(g, words, kCta), kCta, 0, st>>>(dst, total, head);
+        k_blk_heads<<<grid_for(g, words * 32, kCta), kCta, 0, st>>>(dst, total, head);
         k_blk_mark_starts<<<(nb + 1 + kCta - 1) / kCta, kCta, 0, st>>>(pstart, nb, total, head,
                                                                        t->blk_bchunk);
         int32_t *ccount = nullptr;
