@@ -141,14 +141,15 @@ typedef struct g2_graph g2_graph;
  * ascending) is built on the host for the PULL direction.  Device memory
  * comes from the library's stream-ordered pool (see g2_free_graph).
  * G2_PREPARE_PAGERANK: the layouts the tuned PageRank sweep needs (the
- * hot-vertex renumbering of the column ids, the segment flags) are built
+ * source-blocked arcs and the rank order of the vertices) are built
  * after the load returns, by a host thread on a stream of its own, while the
  * caller's next calls run; g2_pagerank (and g2_free_graph) wait for them.
  * Without the flag the first g2_pagerank builds them. */
 g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *col,
                       const int32_t *w, uint32_t flags, void *stream, g2_graph **out);
 /* g2_free_graph — release a handle (a graph or a view); the topology goes
- * when its last handle does.  No call on the handle may be in progress.  The
+ * when its last handle does (the host side of the generated code frees the
+ * graph's device arrays, Sec. VI-C).  No call on the handle may be in progress.  The
  * device memory returns to the library's per-device stream-ordered pool,
  * which keeps it for later loads instead of handing it back to the driver
  * (no cudaFree, no device-wide synchronisation).  NULL is ignored. */
@@ -210,13 +211,25 @@ g2_status g2_frontier_list(g2_frontier *f, int32_t *verts, int32_t cap, int32_t 
  *  G2_OP_PR_ADD     vdata float contrib[n] (per source), vdata2 float acc[n].
  *                   acc[v] += contrib[u].  No output frontier (out must be NULL).
  *  G2_OP_BC_SIGMA   vdata int32 depth[n] (read only), vdata2 double sigma[n].
- *                   If depth[v] == depth[u] + 1: sigma[v] += sigma[u].  No output. */
+ *                   If depth[v] == depth[u] + 1: sigma[v] += sigma[u].  No output.
+ *                   (The forward path counts of Brandes' BC, Sec. VII.)
+ *  G2_OP_BC_DELTA   Brandes' dependency step of one level (Sec. VII, BC):
+ *                   the input vertexset is level d + 1 of a BFS; vdata int32
+ *                   depth[n] (read only), vdata2 double[2n] = sigma[0..n)
+ *                   (read only) followed by delta[n..2n) (accumulated).  Over
+ *                   an arc w->v with w in the input and depth[v] == depth[w] - 1:
+ *                   delta[v] += sigma[v] / sigma[w] * (1 + delta[w]).  Needs
+ *                   a symmetric graph (the arcs out of level d + 1 are the
+ *                   reverses of the shortest-path arcs into it; G2_EINVAL
+ *                   else).  No output.  Run from the deepest level up, it
+ *                   leaves delta_s(v) for every v != s. */
 typedef enum {
     G2_OP_BFS = 0,
     G2_OP_RELAX_MIN = 1,
     G2_OP_LABEL_MIN = 2,
     G2_OP_PR_ADD = 3,
-    G2_OP_BC_SIGMA = 4
+    G2_OP_BC_SIGMA = 4,
+    G2_OP_BC_DELTA = 5
 } g2_op;
 
 /* g2_edgeset_apply — one edgeset.from(in).to(filter).apply[Modified](op).
@@ -274,15 +287,22 @@ g2_status g2_sssp_delta(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
 /* PageRank, topology-driven (Sec. VII): rank float[n] device.  x0 = 1/n;
  * each round x'[v] = (1-d)/n + d*(sum_{u->v} x[u]/outdeg(u) + D/n), D = the
  * total rank of vertices without out-arcs.  `iters` rounds, no convergence
- * test.  PULL + EDGE_ONLY (and NULL): arc-balanced segmented sums over the
- * CSC; PULL + VERTEX_BASED/WM/CM: per-destination sums; PUSH (any load
+ * test.  PULL + EDGE_ONLY (and NULL): the source-blocked sweep (EdgeBlocking,
+ * Sec. VI-D, applied to the pull's sources: blocks of 49,152 sources ranked by
+ * degree, whose shares one CTA holds in shared memory, one reduction per run
+ * of a destination's arcs within a block; the layout is built on the first
+ * call, or in the background with G2_PREPARE_PAGERANK), or where that layout
+ * does not apply (more than 1,024 blocks) arc-balanced segmented sums over
+ * the CSC; PULL + VERTEX_BASED/WM/CM: per-destination sums; PUSH (any load
  * balancing, EDGE_ONLY optionally with EdgeBlocking): arc-parallel atomic
  * adds. */
 g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, float *rank,
                       const g2_hybrid *sched, void *stream);
 
-/* Betweenness centrality (Brandes) summed over the k sources srcs (host
- * int32[k]): bc double[n] device, no normalisation, no halving.  Path counts
+/* Betweenness centrality (Brandes; Sec. VII and the BC rows of Tables V-VI)
+ * summed over the k sources srcs (host int32[k]): bc double[n] device, no
+ * normalisation, no halving; per source a forward pass of path counts
+ * (G2_OP_BC_SIGMA's update) and a backward pass of dependencies (G2_OP_BC_DELTA's).  Path counts
  * are extended-range numbers (64-bit integer mantissa, int32 exponent per
  * vertex), so
  * they neither overflow nor underflow on high-diameter graphs.  Each level's
@@ -296,7 +316,8 @@ g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, float *rank,
 g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc,
                 const g2_hybrid *sched, void *stream);
 
-/* Multi-source BFS: k <= 64 sources (host int32[k]) in one traversal, one bit
+/* Multi-source BFS (not in the paper: a workload addition, the batched
+ * queries of the serving path): k <= 64 sources (host int32[k]) in one traversal, one bit
  * per source in per-vertex 64-bit visit/frontier masks.  depth int32[k][n]
  * device (row i = BFS from srcs[i]).  Schedules: PUSH with any frontier load
  * balancing but EDGE_ONLY, PULL with VERTEX_BASED or WM, or kernel fusion with
@@ -306,7 +327,9 @@ g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc,
 g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
                        const g2_hybrid *sched, void *stream);
 
-/* Multi-source SSSP: k <= 32 sources, stacked distance arrays dist
+/* Multi-source SSSP (not in the paper: a workload addition, the batched
+ * queries of the serving path; the queue is Sec. III's delta-stepping):
+ * k <= 32 sources, stacked distance arrays dist
  * int32[k][n] device, relaxed together in one frontier loop with the
  * near/far queue of g2_sssp_delta (one bit per source in per-vertex masks).
  * Schedules: PUSH with any frontier load balancing but EDGE_ONLY, or kernel
@@ -324,7 +347,10 @@ g2_status g2_sssp_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t del
  * cause.  The caller passes everything in its own memory:
  *   n, m            vertex count (1 <= n <= 1048576) and arc count (< 2^31)
  *   rowptr, col     the graph as a device CSR (int32[n+1], int32[m]); it is
- *                   read, never copied or validated
+ *                   read, never copied; a check kernel reads it first and
+ *                   returns G2_EINVAL, traversing nothing, if a row offset
+ *                   is outside [0, m] or decreasing, rowptr[0] != 0,
+ *                   rowptr[n] != m, or a column id is outside [0, n)
  *   src             source vertex
  *   depth           int32[n] device output, as g2_bfs
  *   parent          int32[n] device output or NULL, as g2_bfs
@@ -332,9 +358,14 @@ g2_status g2_sssp_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t del
  * fixed array of 8 MiB inside the library that every GPU which loads the
  * library holds until the process exits; n above its capacity returns
  * G2_EINVAL.  The first call on a device resolves that array's device address
- * (make that first call before any stream capture).  All calls share the one
+ * (make that first call before any stream capture); under CUDA's lazy module
+ * loading that first call also loads the module holding the array, which
+ * reserves its device memory and may synchronise the device, so a caller that
+ * cannot afford that makes one call at set-up time.  All calls share the one
  * array, so calls that overlap on the GPU (two streams, or two threads) race
- * and must be serialised by the caller.  Returns after completion. */
+ * and must be serialised by the caller.  The call reads 64 bytes of status
+ * back into host stack memory (a pageable copy, which can wait behind other
+ * copies in flight on the device) and returns after completion. */
 g2_status g2_bfs_csr_static(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *col,
                             int32_t src, int32_t *depth, int32_t *parent, void *stream);
 
@@ -371,20 +402,6 @@ const char *g2_last_error(void);
  * waits on a flag that nothing sets, for at most limit_ns nanoseconds, then
  * records a time-out and returns.  Returns G2_ETIMEOUT when that works. */
 g2_status g2_selftest_wait_timeout(int64_t limit_ns, void *stream);
-
-/* Diagnostic: one pass of out[t] = sum of x[idx[e]] over the elements e
- * thread t of a grid of `grid` CTAs x 256 threads strides through, with the
- * access shape of the PageRank arc sweep (16-byte loads of four consecutive
- * indices, two quads in flight per thread) (mode 0), or of the idx values
- * alone (mode 1: streams idx, no gather).  idx int32[m] (16-byte aligned),
- * x float[n] and out float[grid * 256] are device arrays; every idx must lie
- * in [0, n): a checking pass runs first and returns G2_EINVAL before any
- * gather.  *ms (host, may be NULL) receives the gather pass's device time
- * from CUDA events on `stream`.  Fed with a CSC's column ids it is the share
- * gather of a PageRank round without sums, cache or atomics: a floor for the
- * arc sweep on that index order.  Synchronises `stream` before returning. */
-g2_status g2_diag_gather(const int32_t *idx, int64_t m, const float *x, int32_t n, int32_t mode,
-                         float *out, int32_t grid, float *ms, void *stream);
 
 /* Library version string. */
 const char *g2_version(void);

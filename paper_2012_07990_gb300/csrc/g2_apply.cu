@@ -134,9 +134,9 @@ g2_status apply_round(g2_graph *g, const g2_schedule &s, const OpArgs &a, const 
     if (count_arcs_enabled()) G2_TRY(ws(g, B_ARCS, 2, &ctr));
     const DevGraph dg = t->view();
     static const char *push_names[] = {"bfs_push", "sssp_relax", "label_push", "pr_push",
-                                       "sigma_push", "cc_hook"};
+                                       "sigma_push", "cc_hook", "delta_push"};
     static const char *pull_names[] = {"bfs_pull", "relax_pull", "label_pull", "pr_pull",
-                                       "sigma_pull", "hook_pull"};
+                                       "sigma_pull", "hook_pull", "delta_pull"};
     KTime kt;
     ktime_begin(kt, s.direction == G2_PUSH ? push_names[a.kind] : pull_names[a.kind], st);
     g2_status r = G2_OK;
@@ -150,6 +150,9 @@ g2_status apply_round(g2_graph *g, const g2_schedule &s, const OpArgs &a, const 
             case K_PR: r = push_round(g, s, OpPRAdd{a.f0, a.f1}, in, out, ctr, st); break;
             case K_SIGMA: r = push_round(g, s, OpBCSigma{a.i0, a.d0}, in, out, ctr, st); break;
             case K_HOOK: r = push_round(g, s, OpHook{a.i0}, in, out, ctr, st); break;
+            case K_DELTA:
+                r = push_round(g, s, OpBCDelta{a.i0, a.d0, a.d0 + g->topo->n}, in, out, ctr, st);
+                break;
         }
     } else {
         switch (a.kind) {
@@ -159,6 +162,9 @@ g2_status apply_round(g2_graph *g, const g2_schedule &s, const OpArgs &a, const 
             case K_PR: r = pull_round(g, s, PullPRAdd{a.f0, a.f1}, in, out, ctr, st); break;
             case K_SIGMA: r = pull_round(g, s, PullBCSigma{a.i0, a.d0}, in, out, ctr, st); break;
             case K_HOOK: r = fail(G2_EUNSUPPORTED, "hooking is a PUSH update"); break;
+            case K_DELTA:
+                r = pull_round(g, s, PullBCDelta{a.i0, a.d0, a.d0 + g->topo->n}, in, out, ctr, st);
+                break;
         }
     }
     ktime_end(kt, st);
@@ -184,11 +190,15 @@ extern "C" g2_status g2_edgeset_apply(g2_graph *g, g2_op op, g2_frontier *in, vo
         case G2_OP_LABEL_MIN: kind = K_LABEL; break;
         case G2_OP_PR_ADD: kind = K_PR; break;
         case G2_OP_BC_SIGMA: kind = K_SIGMA; break;
+        case G2_OP_BC_DELTA: kind = K_DELTA; break;
         default: return fail(G2_EINVAL, "unknown op");
     }
-    if ((kind == K_PR || kind == K_SIGMA) && !vdata2) return fail(G2_EINVAL, "op needs vdata2");
-    if ((kind == K_PR || kind == K_SIGMA) && outf)
+    const bool no_out = kind == K_PR || kind == K_SIGMA || kind == K_DELTA;
+    if (no_out && !vdata2) return fail(G2_EINVAL, "op needs vdata2");
+    if (no_out && outf)
         return fail(G2_EINVAL, "this op produces no output vertexset (out must be NULL)");
+    if (kind == K_DELTA && !g->topo->symmetric)
+        return fail(G2_EINVAL, "BC_DELTA needs a symmetric graph");
     if (kind == K_RELAX && !g->topo->w) return fail(G2_EINVAL, "RELAX_MIN needs arc weights");
     Topology *t = g->topo;
     const int32_t n = t->n;
@@ -277,7 +287,7 @@ extern "C" g2_status g2_edgeset_apply(g2_graph *g, g2_op op, g2_frontier *in, vo
         case K_BFS: a.i0 = (int32_t *)vdata; a.i1 = (int32_t *)vdata2; break;
         case K_RELAX: case K_LABEL: a.i0 = (int32_t *)vdata; break;
         case K_PR: a.f0 = (const float *)vdata; a.f1 = (float *)vdata2; break;
-        case K_SIGMA: a.i0 = (int32_t *)vdata; a.d0 = (double *)vdata2; break;
+        case K_SIGMA: case K_DELTA: a.i0 = (int32_t *)vdata; a.d0 = (double *)vdata2; break;
         default: break;
     }
     G2_TRY(apply_round(g, s, a, use, o, st));

@@ -263,6 +263,24 @@ struct OpBCSigma {
     }
 };
 
+// Brandes' dependency step of one level (Sec. VII, BC): the input vertexset
+// is level d + 1; over an arc w -> u with u one level up,
+// delta[u] += sigma[u] / sigma[w] * (1 + delta[w]).  On a symmetric graph the
+// arcs w -> u out of level d + 1 are exactly the reverses of the shortest-path
+// arcs u -> w into it.
+struct OpBCDelta {
+    const int32_t *depth;
+    const double *sigma;
+    double *delta;
+    typedef int32_t S;
+    __device__ __forceinline__ S load(int32_t w) const { return depth[w]; }
+    __device__ __forceinline__ bool skip(S dw) const { return dw <= 0; }
+    __device__ __forceinline__ int relax(int32_t w, S dw, int32_t u, int32_t) const {
+        if (depth[u] == dw - 1) atomicAdd(&delta[u], sigma[u] / sigma[w] * (1.0 + delta[w]));
+        return 0;
+    }
+};
+
 // Pull-side interface: ctx(v) loads what the destination needs; filter(c)
 // selects destinations; edge(c, u, e) is the contribution of in-neighbour u
 // (already known to be in the input frontier); combine is associative;
@@ -369,6 +387,29 @@ struct PullBCSigma {
     __device__ __forceinline__ bool stop(Acc) const { return false; }
     __device__ __forceinline__ int finish(int32_t v, Ctx, Acc a) const {
         sigma[v] += a;
+        return 0;
+    }
+};
+
+// the same step pulled by the vertices one level up: u sums
+// (1 + delta[w]) / sigma[w] over its in-arcs from the input vertexset with
+// depth[w] == depth[u] + 1, then delta[u] += sigma[u] * sum
+struct PullBCDelta {
+    const int32_t *depth;
+    const double *sigma;
+    double *delta;
+    typedef int32_t Ctx;
+    typedef double Acc;
+    __device__ __forceinline__ Ctx ctx(int32_t u) const { return depth[u]; }
+    __device__ __forceinline__ bool filter(Ctx du) const { return du >= 0; }
+    __device__ __forceinline__ Acc identity() const { return 0.0; }
+    __device__ __forceinline__ Acc edge(Ctx du, int32_t w, int32_t) const {
+        return depth[w] == du + 1 ? (1.0 + delta[w]) / sigma[w] : 0.0;
+    }
+    __device__ __forceinline__ Acc combine(Acc a, Acc b) const { return a + b; }
+    __device__ __forceinline__ bool stop(Acc) const { return false; }
+    __device__ __forceinline__ int finish(int32_t u, Ctx, Acc a) const {
+        if (a != 0.0) delta[u] += sigma[u] * a;
         return 0;
     }
 };

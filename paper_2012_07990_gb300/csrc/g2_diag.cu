@@ -12,6 +12,7 @@
 // separate pass first; the pass that is timed loads without checks.
 #include <cuda_runtime.h>
 
+#include "g2_diag.h"
 #include "g2_host.h"
 
 namespace g2 {

@@ -305,7 +305,7 @@ g2_status vset_convert(g2_graph *g, const VSet &src, int rep, VSet &dst, cudaStr
 g2_status vset_count(g2_graph *g, const VSet &v, int32_t *d_out, cudaStream_t st);
 
 // ------------------------------------------------------------- apply engine
-enum OpKind { K_BFS, K_RELAX, K_LABEL, K_PR, K_SIGMA, K_HOOK };
+enum OpKind { K_BFS, K_RELAX, K_LABEL, K_PR, K_SIGMA, K_HOOK, K_DELTA };
 
 struct OpArgs {
     OpKind kind;

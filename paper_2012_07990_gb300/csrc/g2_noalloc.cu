@@ -9,6 +9,15 @@
 // only scratch the traversal needs (two frontier queues, their counters, the
 // grid-barrier words and the error word) lives in the fixed array below,
 // which every GPU that loads this library holds until the process exits.
+// (With CUDA's lazy module loading, the module that holds the array is loaded
+// on a device at this file's first use there, the first call: that call
+// reserves the array's device memory and may synchronise the device, so a
+// caller that cannot afford it makes one call at set-up time.)
+//
+// The caller's CSR is never copied, so it is checked on the device before
+// the traversal reads it (row offsets monotone within [0, m], rowptr[0] = 0,
+// rowptr[n] = m, every column id in [0, n)): a bad graph returns G2_EINVAL
+// instead of sending the traversal out of bounds.
 //
 // The traversal is the fused persistent BFS: one cooperative kernel runs the
 // whole frontier loop, warp-mapped load balancing, with a time-bounded grid
@@ -67,6 +76,22 @@ __global__ void k_static_init(int32_t *s, int32_t *depth, int32_t *parent, int32
     }
 }
 
+// The caller's CSR: on any violation the error word becomes G2_EINVAL.
+__global__ void k_static_check(const int32_t *rowptr, const int32_t *col, int32_t n, int64_t m,
+                               int32_t *err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    for (int64_t v = i0; v <= n; v += stride) {
+        const int64_t r = rowptr[v];
+        if (r < 0 || r > m || (v == 0 && r != 0) || (v == n && r != m)) bad = true;
+        else if (v < n && rowptr[v + 1] < r) bad = true;
+    }
+    for (int64_t e = i0; e < m; e += stride)
+        if ((uint32_t)col[e] >= (uint32_t)n) bad = true;
+    if (bad) atomicCAS(err, 0, (int32_t)G2_EINVAL);
+}
+
 struct StaticBfsArgs {
     DevGraph g;
     int32_t *depth;
@@ -87,6 +112,9 @@ __global__ void __launch_bounds__(kCta) k_static_bfs(StaticBfsArgs a) {
     out.dedup = DD_NONE;  // the compare-and-swap on depth admits each vertex once
     out.cap = kStaticMaxN;
     out.err = err;
+    // a graph the check rejected is not traversed (every CTA reads the word
+    // the check kernel, which ran before, left)
+    if (ld_relaxed_i32(err) != 0) return;
     int d = 0;
     for (;; ++d) {
         int32_t size = ld_relaxed_i32(cnt + d % 3);
@@ -125,6 +153,9 @@ extern "C" g2_status g2_bfs_csr_static(int32_t n, int64_t m, const int32_t *rowp
     if (per_sm < 1) return fail(G2_EUNSUPPORTED, "g2_bfs_csr_static: kernel does not fit on an SM");
     int init_grid = (int)std::min<int64_t>((n + kCta - 1) / kCta, (int64_t)sms * 8);
     k_static_init<<<init_grid, kCta, 0, st>>>(s, depth, parent, n, src);
+    const int check_grid = (int)std::min<int64_t>((std::max<int64_t>(m, n) + kCta - 1) / kCta,
+                                                  (int64_t)sms * 8);
+    k_static_check<<<check_grid, kCta, 0, st>>>(rowptr, col, n, m, s + 12);
     G2_CK(cudaGetLastError());
     StaticBfsArgs a;
     a.g.n = n;
@@ -142,9 +173,13 @@ extern "C" g2_status g2_bfs_csr_static(int32_t n, int64_t m, const int32_t *rowp
     void *params[] = {&a};
     G2_CK(cudaLaunchCooperativeKernel((const void *)k_static_bfs, dim3(per_sm * sms), dim3(kCta),
                                       params, 0, st));
+    // the header comes back to host stack memory (a pageable copy: nothing is
+    // allocated for it, pinned memory included)
     int32_t hdr[16];
     G2_CK(cudaMemcpyAsync(hdr, s, sizeof(hdr), cudaMemcpyDeviceToHost, st));
     G2_CK(cudaStreamSynchronize(st));
+    if (hdr[12] == G2_EINVAL)
+        return fail(G2_EINVAL, "g2_bfs_csr_static: invalid CSR (row offsets or a column id out of range)");
     if (hdr[12] == G2_ETIMEOUT) return fail(G2_ETIMEOUT, "g2_bfs_csr_static: grid barrier timed out");
     if (hdr[12] != 0) return fail((g2_status)hdr[12], "g2_bfs_csr_static: device error");
     return G2_OK;

@@ -34,7 +34,7 @@ G2_DEDUP_ENABLED, G2_DEDUP_DISABLED = 0, 1
 G2_DEDUP_MONOTONIC_COUNTERS, G2_DEDUP_BITMAP, G2_DEDUP_BOOLMAP = 0, 1, 2
 G2_CRITERIA_NONE, G2_INPUT_VERTEXSET_SIZE = 0, 1
 G2_FRONTIER_SPARSE, G2_FRONTIER_BITMAP, G2_FRONTIER_BOOLMAP = 0, 1, 2
-G2_OP_BFS, G2_OP_RELAX_MIN, G2_OP_LABEL_MIN, G2_OP_PR_ADD, G2_OP_BC_SIGMA = range(5)
+G2_OP_BFS, G2_OP_RELAX_MIN, G2_OP_LABEL_MIN, G2_OP_PR_ADD, G2_OP_BC_SIGMA, G2_OP_BC_DELTA = range(6)
 
 
 class g2_schedule(ctypes.Structure):

@@ -1,7 +1,9 @@
 """CPU checks of the C ABI: the library loads without a GPU, exports every
-entry point include/g2.h declares, and the binding's constants and struct
-layouts agree with the header."""
+entry point include/*.h declares (g2.h, the library; g2_diag.h, its
+measurement probes), and the binding's constants and struct layouts agree
+with the header."""
 import ctypes
+import glob
 import os
 import re
 
@@ -9,6 +11,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "g2.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 @pytest.fixture(scope="module")
@@ -20,9 +23,11 @@ def g2mod():
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(g2_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(g2_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def header_defines():

@@ -583,6 +583,56 @@ def test_apply_pr_add_covers_each_arc_once(g2, rmat14):
             assert np.array_equal(host(acc), want.astype(np.float32)), ("pull", lb, rep)
 
 
+def _brandes_by_levels(g2, g, src, sched_sigma, sched_delta, fmt):
+    """Single-source BC through the operator alone: path counts by
+    G2_OP_BC_SIGMA from the source's level down, then dependencies by
+    G2_OP_BC_DELTA from the deepest level up (depths from the oracle's BFS)."""
+    depth, _ = oracle.bfs_graph(g, src, want_parent=False)
+    dg = g2.load_graph(g)
+    d = torch.from_numpy(depth.astype(np.int32)).cuda()
+    sd = torch.zeros(2 * g.n, dtype=torch.float64, device="cuda")  # sigma, then delta
+    sd[src] = 1.0
+    levels = [np.nonzero(depth == k)[0].astype(np.int32) for k in range(int(depth.max()) + 1)]
+    for lv in levels[:-1]:
+        f = g2.Frontier(dg, fmt)
+        f.set(lv)
+        g2.g2_edgeset_apply(dg, g2.G2_OP_BC_SIGMA, f, d, sd[: g.n], sched_sigma)
+    for lv in reversed(levels[1:]):
+        f = g2.Frontier(dg, fmt)
+        f.set(lv)
+        g2.g2_edgeset_apply(dg, g2.G2_OP_BC_DELTA, f, d, sd, sched_delta)
+    delta = host(sd)[g.n:].copy()
+    delta[src] = 0.0  # delta_s(s) is excluded from BC
+    return delta
+
+
+def test_apply_bc_delta_gives_brandes_dependencies(g2, rmat14, grid):
+    """G2_OP_BC_DELTA, Brandes' backward step of one level: run level by level
+    after G2_OP_BC_SIGMA's forward path counts, the dependencies of every
+    vertex equal the oracle's single-source BC, PUSH (every frontier load
+    balancing) and PULL (bitmap and boolmap input)."""
+    g12 = gg.rmat(12, seed=3)
+    cases = [(g12, g12.max_degree_vertex()), (grid, 0), (rmat14, 5), (gg.star(200), 7), (gg.path(50), 0)]
+    for g, src in cases:
+        want = oracle.bc_graph(g, np.array([src], np.int32))
+        scheds = [(g2.schedule(lb), g2.schedule(lb), g2.G2_FRONTIER_SPARSE) for lb in LBS]
+        scheds += [(pull_sched(g2, lb, rep), pull_sched(g2, lb, rep), fmt)
+                   for lb in ("VERTEX_BASED", "WM", "CM")
+                   for rep, fmt in ((g2.G2_BITMAP, g2.G2_FRONTIER_BITMAP),
+                                    (g2.G2_BOOLMAP, g2.G2_FRONTIER_BOOLMAP))]
+        for s_sigma, s_delta, fmt in scheds:
+            got = _brandes_by_levels(g2, g, src, s_sigma, s_delta, fmt)
+            assert bc_close(got, want), (g.name, src, s_delta.load_balance, s_delta.direction)
+    # a directed graph is rejected before any launch
+    gd = gg.gnp(50, 0.1, 2, symmetric=False)
+    dg = g2.load_graph(gd)
+    f = g2.Frontier(dg, g2.G2_FRONTIER_SPARSE)
+    f.set(np.array([0], np.int32))
+    with pytest.raises(Exception):
+        g2.g2_edgeset_apply(dg, g2.G2_OP_BC_DELTA, f, dev(gd.n), torch.zeros(2 * gd.n, dtype=torch.float64,
+                                                                              device="cuda"))
+
+
 def test_apply_bfs_round_and_frontier_formats(g2, rmat14):
     """One applyModified round of the Fig. 2 program from a frontier: the
     output vertexset is exactly the unvisited out-neighbours."""
