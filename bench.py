@@ -973,32 +973,66 @@ def run_serve_workload(args):
 
 
 def run_profile_case(args):
-    """A short run of one algorithm for profilers: load RMAT at --scale, run
-    the algorithm --steps times with the tuned schedule, print a checksum."""
+    """A short run of one piece of the library for profilers (one launch of
+    each kernel of interest, a few hundred MB on the device at most), so that a
+    capture names a committed command:
+
+    * pr / bfs / cc: RMAT at --scale, the algorithm --steps times with the
+      tuned schedule;
+    * road_fused: the --grid x --grid road grid (weights U[1, 1000]), one fused
+      WM BFS from vertex 0 (no parent array) and one fused WM delta-stepping
+      SSSP from vertex 0 with delta 1024 -- the one-cluster loops;
+    * bc_rmat: RMAT at --scale, BC from its two highest-degree vertices with
+      the NULL schedule -- the level passes on a power-law graph."""
     import torch
     from paper_2012_07990_gb300 import build_native
     build_native.build()
     from paper_2012_07990_gb300 import g2
+    from paper_2012_07990_gb300 import graphgen as gg
+    case = args.profile_case
+    if case == "road_fused":
+        G = gg.road_grid(args.grid, seed=1)
+        w = gg.pair_weights(G, 1000, seed=1)
+        dg = g2.load_graph(G, w)
+        out = torch.empty(G.n, dtype=torch.int32, device="cuda")
+        s = g2.schedule("WM", kernel_fusion=True)
+        g2.g2_bfs(dg, 0, out, None, s)
+        bfs = g2.g2_last_stats()
+        g2.g2_sssp_delta(dg, 0, 1024, out, s)
+        sssp = g2.g2_last_stats()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": case, "grid": args.grid, "bfs_levels": bfs["iterations"],
+                          "bfs_launches": bfs["launches"], "sssp_rounds": sssp["iterations"],
+                          "sssp_launches": sssp["launches"]}))
+        return
     G = make_graph(args.scale)
     dg = g2.load_graph(G)
+    if case == "bc_rmat":
+        srcs = np.argsort(-G.degrees(), kind="stable")[:2].astype(np.int32)
+        bc = torch.empty(G.n, dtype=torch.float64, device="cuda")
+        g2.g2_bc(dg, srcs, bc, None)
+        st = g2.g2_last_stats()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": case, "scale": args.scale, "levels": st["iterations"],
+                          "launches": st["launches"]}))
+        return
     src = G.max_degree_vertex()
-    out = torch.empty(G.n, dtype=torch.float32 if args.profile_case == "pr" else torch.int32,
-                      device="cuda")
+    out = torch.empty(G.n, dtype=torch.float32 if case == "pr" else torch.int32, device="cuda")
     for _ in range(args.steps):
-        if args.profile_case == "pr":
+        if case == "pr":
             g2.g2_pagerank(dg, DAMPING, PR_ITERS, out)
-        elif args.profile_case == "bfs":
+        elif case == "bfs":
             g2.g2_bfs(dg, src, out, None, None)
         else:
             g2.g2_cc(dg, out, None)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": args.profile_case, "scale": args.scale, "n": G.n, "m": G.m,
+    print(json.dumps({"profile_case": case, "scale": args.scale, "n": G.n, "m": G.m,
                       "checksum": float(out.double().sum().item())}))
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["pr", "bfs", "cc"], default=None)
+    ap.add_argument("--profile-case", choices=["pr", "bfs", "cc", "road_fused", "bc_rmat"], default=None)
     ap.add_argument("--serve-pool", choices=["full", "small"], default="full")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=1.0)
