@@ -426,7 +426,8 @@ def run_extras(g2, G22, dg22, src22, sb, sc):
       measured HBM peak;
     * RMAT-14 BFS, the plain single-query path;
     * the 4096 x 4096 road grid: BFS and delta-stepping SSSP (delta 1024 and
-      16384), fused persistent loop against plain per-round launches;
+      16384), fused persistent loop against plain per-round launches, and the
+      asynchronous variants (no barrier inside a bucket);
     * RMAT-21 batched: 64-source BFS in one traversal against 64 single-source
       calls (tuned schedule and the fixed TWC PUSH schedule), 32-source SSSP
       against 32 single calls, BC from 16 sources;
@@ -502,6 +503,14 @@ def run_extras(g2, G22, dg22, src22, sb, sc):
             grid[f"sssp_d{delta}_{name}"] = {
                 "ms": round(ms, 3), "rounds": st["iterations"], "launches": st["launches"],
                 "gteps": round(reached_arcs(Gg, dist, 2**31 - 1) / ms / 1e6, 3)}
+    for name, fn in (("sssp_d8192_async", lambda: g2.g2_sssp_async(dgg, 0, 8192, dist)),
+                     ("bfs_async_d64", lambda: g2.g2_bfs_async(dgg, 0, 64, depth, None))):
+        ms = _timed(fn, reps=2)
+        st = g2.g2_last_stats()
+        out_arr = dist if name.startswith("sssp") else depth
+        grid[name] = {"ms": round(ms, 3), "items": st["iterations"], "barriers": st["barriers"],
+                      "gteps": round(reached_arcs(Gg, out_arr, 2**31 - 1 if name.startswith("sssp") else -1)
+                                     / ms / 1e6, 3)}
     grid["fused_vs_plain"] = {"bfs": round(grid["bfs_plain"]["ms"] / grid["bfs_fused"]["ms"], 2),
                               "sssp_d1024": round(grid["sssp_d1024_plain"]["ms"] / grid["sssp_d1024_fused"]["ms"], 2)}
     out["grid4096"] = grid
@@ -718,6 +727,19 @@ def run_grid_workload(args):
         reached = int(deg[dist.cpu().numpy() < 2**31 - 1].sum())
         row["gteps_best"] = round(reached / min(v for k, v in row.items() if k.endswith("_ms")) / 1e6, 3)
         res["sssp"].append(row)
+    # asynchronous delta-stepping (no barrier inside a bucket) beside them
+    res["sssp_async"] = []
+    for delta in (0, 1024, 4096, 8192, 16384, 65536):
+        ms = _timed(lambda: g2.g2_sssp_async(dg, 0, delta, dist), reps=2)
+        st = g2.g2_last_stats()
+        res["sssp_async"].append({"delta": delta, "ms": round(ms, 3), "items": st["iterations"],
+                                  "barriers": st["barriers"]})
+    res["bfs_async"] = []
+    for delta in (1, 16, 64, 256):
+        ms = _timed(lambda: g2.g2_bfs_async(dg, 0, delta, depth, None), reps=2)
+        st = g2.g2_last_stats()
+        res["bfs_async"].append({"delta": delta, "ms": round(ms, 3), "items": st["iterations"],
+                                 "barriers": st["barriers"]})
     for name, s in (("null_schedule", None), ("plain_strict", g2.schedule("STRICT")),
                     ("fused_vertex", g2.schedule("VERTEX_BASED", kernel_fusion=True)),
                     ("fused_wm", wm), ("fused_wm_grid_only", wm)):

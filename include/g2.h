@@ -339,6 +339,31 @@ g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *dep
 g2_status g2_sssp_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t delta,
                         int32_t *dist, const g2_hybrid *sched, void *stream);
 
+/* Asynchronous SSSP and BFS (not the paper's method: Sec. VII-A and Table VII
+ * show its delta-stepping losing to a 24-core CPU on road graphs, where every
+ * bucket and every near round inside it ends at a barrier while the frontier
+ * holds a few thousand vertices).  One persistent cooperative kernel relaxes
+ * the out-arcs of the vertices in a shared worklist (a vertex queued at most
+ * once at a time) with no barrier inside a bucket of width `delta`: a bucket
+ * ends when a device-side count of pending items reaches zero, and only the
+ * step to the next bucket (the smallest far distance, the split of the far
+ * pile) synchronises the grid.  delta <= 0: one bucket, fully asynchronous.
+ * Every wait is bounded (G2_ETIMEOUT).  If the worklist (4 n appends) runs
+ * out the kernel is run again with four times the room.  Results equal
+ * g2_sssp_delta's / g2_bfs's:
+ *   g2_sssp_async  dist int32[n] device (INT32_MAX unreachable); needs
+ *                  weights >= 1; G2_EOVERFLOW if a distance would reach
+ *                  INT32_MAX.
+ *   g2_bfs_async   depth int32[n] device (-1 unreachable), parent int32[n]
+ *                  device or NULL (the smallest-id in-neighbour one level up,
+ *                  taken by a pull pass over the final depths); delta counts
+ *                  levels per bucket.
+ * g2_last_stats: `iterations` = worklist items processed, `barriers` = grid
+ * barriers (three per bucket). */
+g2_status g2_sssp_async(g2_graph *g, int32_t src, int32_t delta, int32_t *dist, void *stream);
+g2_status g2_bfs_async(g2_graph *g, int32_t src, int32_t delta, int32_t *depth, int32_t *parent,
+                       void *stream);
+
 /* g2_bfs_csr_static — BFS that allocates no device memory (the paper has no
  * counterpart: this entry point exists for callers that cannot allocate).
  * For callers that cannot call cudaMalloc, e.g. code running inside another

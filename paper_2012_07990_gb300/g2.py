@@ -94,6 +94,8 @@ _SIGS = {
     "g2_selftest_wait_timeout": [I64, P],
     "g2_diag_gather": [P, I64, P, I32, I32, P, I32, ctypes.POINTER(F32), P],
     "g2_bfs_csr_static": [I32, I64, P, P, I32, P, P, P],
+    "g2_sssp_async": [P, I32, I32, P, P],
+    "g2_bfs_async": [P, I32, I32, P, P, P],
     "g2_set_kernel_timing": [I32],
     "g2_kernel_time": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I32],
     "g2_version": [],
@@ -289,6 +291,16 @@ def g2_cc(g: Graph, label, sched=None, stream=None):
 def g2_sssp_delta(g: Graph, src: int, delta: int, dist, sched=None, stream=None):
     _check(_lib.g2_sssp_delta(g.handle, int(src), int(delta), _ptr(dist), _sched(sched),
                               _stream(stream)), "g2_sssp_delta")
+
+
+def g2_sssp_async(g: Graph, src: int, delta: int, dist, stream=None):
+    _check(_lib.g2_sssp_async(g.handle, int(src), int(delta), _ptr(dist), _stream(stream)),
+           "g2_sssp_async")
+
+
+def g2_bfs_async(g: Graph, src: int, delta: int, depth, parent=None, stream=None):
+    _check(_lib.g2_bfs_async(g.handle, int(src), int(delta), _ptr(depth), _ptr(parent),
+                             _stream(stream)), "g2_bfs_async")
 
 
 def g2_pagerank(g: Graph, damping: float, iters: int, rank, sched=None, stream=None):

@@ -1036,3 +1036,41 @@ def test_background_pagerank_preparation(g2, rmat14):
     g2.g2_pagerank(dg, 0.85, 3, r)
     assert np.allclose(host(r), 0.2)
 
+
+
+# ------------------------------------------------------------ asynchronous
+@pytest.mark.parametrize("cap", [None, "1"])
+def test_async_sssp_and_bfs(g2, rmat14, grid, monkeypatch, cap):
+    """The asynchronous SSSP and BFS (no barrier inside a bucket; buckets of
+    width delta, or one bucket for delta <= 0) against the oracle, bit-exact:
+    road grids 128^2 and 300^2 from a corner and the centre, a star from a
+    leaf and from the centre, RMAT-14, a path, directed G(n, p) and a graph
+    with unreachable parts.  cap=1 gives the worklist room for n appends only,
+    so runs that need more go through the overflow-and-retry path."""
+    if cap:
+        monkeypatch.setenv("G2_ASYNC_CAP", cap)
+    g300 = gg.road_grid(300, seed=4)
+    star = gg.star(30001)
+    cases = [(grid, 0), (grid, grid.n // 2 + 64), (g300, 0), (g300, g300.n - 1), (star, 17), (star, 0),
+             (rmat14, rmat14.max_degree_vertex()), (gg.path(3000), 0),
+             (gg.gnp(400, 0.01, 5, symmetric=False), 3),
+             (gg.disjoint_union(gg.road_grid(40, seed=2), gg.star(50)), 5)]
+    for g, src in cases:
+        w = gg.pair_weights(g, 1000, seed=3) if g.symmetric else \
+            np.random.default_rng(7).integers(1, 1000, g.m).astype(np.int32)
+        dg = g2.load_graph(g, w)
+        want = oracle.sssp_graph(g, w, src)
+        od, op = oracle.bfs_graph(g, src)
+        for delta in (0, 1, 700, 5000):
+            dist = dev(g.n)
+            g2.g2_sssp_async(dg, src, delta, dist)
+            assert np.array_equal(host(dist), want), (g.name, src, delta)
+            st = g2.g2_last_stats()
+            assert st["iterations"] >= int((want < 2**31 - 1).sum())  # each reached vertex at least once
+        for delta in (0, 1, 3):
+            d, p = dev(g.n), dev(g.n)
+            g2.g2_bfs_async(dg, src, delta, d, p)
+            assert np.array_equal(host(d), od) and np.array_equal(host(p), op), (g.name, src, delta)
+            d2 = dev(g.n)
+            g2.g2_bfs_async(dg, src, delta, d2)
+            assert np.array_equal(host(d2), od), (g.name, src, delta)
