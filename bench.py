@@ -960,6 +960,55 @@ def run_batched_workload(args):
     print(json.dumps({"workload": f"rmat{args.batch_scale}_batched", "n": G.n, "m": G.m, **out}))
 
 
+def run_lb_workload(args):
+    """The load-balancing comparison of the paper's Table VIII: BFS PUSH-only
+    (kernel fusion off) with ETWC, TWC and CM (and STRICT, WM and
+    VERTEX_BASED beside them) on RMAT-22 from its hub and on the 4096 x 4096
+    road grid from vertex 0; plus one PUSH round from RMAT-22's hub alone
+    (163K arcs in one vertex), the case where a load balancer that keeps a
+    vertex on one CTA serialises."""
+    import torch
+    from paper_2012_07990_gb300 import build_native
+    build_native.build()
+    from paper_2012_07990_gb300 import g2
+    from paper_2012_07990_gb300 import graphgen as gg
+    lbs = ("ETWC", "TWC", "CM", "STRICT", "WM", "VERTEX_BASED")
+    out = {"workload": "lb_push_bfs"}
+    G = make_graph(22)
+    Gg = gg.road_grid(4096, seed=1)
+    for name, graph, src in (("rmat22", G, G.max_degree_vertex()), ("grid4096", Gg, 0)):
+        dg = g2.load_graph(graph)
+        depth = torch.empty(graph.n, dtype=torch.int32, device="cuda")
+        row = {}
+        for lb in lbs:
+            ms = _timed(lambda: g2.g2_bfs(dg, src, depth, None, g2.schedule(lb)), reps=3 if name == "rmat22" else 1)
+            row[lb] = {"ms": round(ms, 3), "levels": g2.g2_last_stats()["iterations"]}
+        if name == "rmat22":
+            hub = np.array([src], np.int32)
+            fin = g2.Frontier(dg, g2.G2_FRONTIER_SPARSE)
+            fin.set(hub)
+            first = {}
+            for lb in lbs:
+                ts = []
+                for rep in range(6):
+                    depth.fill_(-1)
+                    depth[src] = 0
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    g2.g2_edgeset_apply(dg, g2.G2_OP_BFS, fin, depth, None, g2.schedule(lb))
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if rep:
+                        ts.append(e0.elapsed_time(e1))
+                first[lb] = round(float(np.median(ts)), 4)
+            row["first_round_from_hub_ms"] = first
+        out[name] = row
+        dg.free()
+    print(json.dumps(out))
+
+
 def run_serve_workload(args):
     """Serving: Poisson stream (BFS 60% / SSSP 30% / single-source BC 10%) over
     a resident pool (full: RMAT 16/18/20/22 + grids 512^2..4096^2; small: RMAT
@@ -977,14 +1026,29 @@ def run_serve_workload(args):
     t = time.time()
     pool = serve.GraphPool(g2, specs)
     load_s = time.time() - t
-    trace = serve.make_trace(pool, rate=args.serve_rate, duration=args.serve_duration, seed=1)
     ex = serve.GpuExecutor(g2, pool, slots=4)
+    ex1 = serve.GpuExecutor(g2, pool, slots=1)
+    if args.serve_rates:
+        # latency against offered load: the same number of requests at each
+        # rate, continuous batching (response ratio) against serial launches
+        curve = []
+        for rate in (float(r) for r in args.serve_rates.split(",")):
+            trace = serve.make_trace(pool, rate=rate, duration=args.serve_requests / rate, seed=1)
+            srv = serve.Server(ex, pool, policy="hrrn")
+            srv.run(trace[: min(128, len(trace))])  # warm views, workspaces and the cost model
+            cb = srv.run(trace).summary()
+            serial = serve.Server(ex1, pool, max_batch=dict(bfs=1, sssp=1, bc=1), policy="fifo").run(trace)
+            curve.append({"rate_per_s": rate, "requests": len(trace), "continuous_batching": cb,
+                          "serial_plain": serial.summary()})
+        print(json.dumps({"workload": f"serve_curve_{args.serve_pool}", "graphs": [s.name for s in specs],
+                          "pool_load_s": round(load_s, 2), "curve": curve}))
+        return
+    trace = serve.make_trace(pool, rate=args.serve_rate, duration=args.serve_duration, seed=1)
     res = {}
     for policy in ("hrrn", "fifo"):
         srv = serve.Server(ex, pool, policy=policy)
         srv.run(trace[: min(256, len(trace))])  # warm views, workspaces and the cost model
         res[policy] = srv.run(trace).summary()
-    ex1 = serve.GpuExecutor(g2, pool, slots=1)
     serial = serve.Server(ex1, pool, max_batch=dict(bfs=1, sssp=1, bc=1), policy="fifo").run(trace)
     print(json.dumps({"workload": f"serve_{args.serve_pool}", "graphs": [s.name for s in specs],
                       "pool_load_s": round(load_s, 2), "rate_per_s": args.serve_rate,
@@ -1058,7 +1122,11 @@ def main():
     ap.add_argument("--serve-pool", choices=["full", "small"], default="full")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=1.0)
-    ap.add_argument("--workload", choices=["rmat22", "grid", "batched", "serve", "tune", "gather"],
+    ap.add_argument("--serve-rates", default=None,
+                    help="comma-separated request rates: a latency-against-load curve")
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests per rate of the curve (--serve-rates)")
+    ap.add_argument("--workload", choices=["rmat22", "grid", "batched", "serve", "tune", "gather", "lb"],
                     default="rmat22",
                     help="rmat22: the default step (the JSON line the driver reads); grid and "
                          "batched: the road-grid and multi-source configurations")
@@ -1092,6 +1160,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve_workload(args)
+        return
+    if args.workload == "lb":
+        run_lb_workload(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -230,9 +230,23 @@ struct EtwcEntry {
     S s;
 };
 
+// Frontier-wide hand-off of ETWC's largest CTA-stage entries: a vertex whose
+// CTA-granularity part reaches kEtwcSpill arcs would otherwise keep one CTA
+// busy while the others idle (a hub on a power-law graph: RMAT-22's first
+// round is one 163K-arc vertex); such entries go to a list that a second
+// pass spreads over every CTA (k_push_etwc_spill).  q == null: no hand-off,
+// every entry stays with its CTA, as in Algorithm 3.
+constexpr int32_t kEtwcSpill = 4096;
+template <class S>
+struct EtwcSpill {
+    EtwcEntry<S> *q;
+    int32_t *cnt;
+};
+
 template <class Op>
 __device__ void lb_etwc(const DevGraph &g, const FrontierIn &fin, int32_t fsize, const Op &op,
-                        const OutCtx &out, int bid, int nb, unsigned long long *ctr) {
+                        const OutCtx &out, int bid, int nb, unsigned long long *ctr,
+                        EtwcSpill<typename Op::S> spill = {nullptr, nullptr}) {
     typedef typename Op::S S;
     __shared__ EtwcEntry<S> q0[kCta], q1[kCta], q2[kCta];
     __shared__ int n0, n1, n2;
@@ -251,8 +265,12 @@ __device__ void lb_etwc(const DevGraph &g, const FrontierIn &fin, int32_t fsize,
                 len0 = size;
                 int32_t c = (size / kCta) * kCta;  // CTA-granularity part
                 if (c > 0) {
-                    int p = atomicAdd(&n2, 1);
-                    q2[p] = EtwcEntry<S>{beg, beg + c, u, s};
+                    if (spill.q && c >= kEtwcSpill) {
+                        spill.q[atomicAdd(spill.cnt, 1)] = EtwcEntry<S>{beg, beg + c, u, s};
+                    } else {
+                        int p = atomicAdd(&n2, 1);
+                        q2[p] = EtwcEntry<S>{beg, beg + c, u, s};
+                    }
                     beg += c;
                     size -= c;
                 }
@@ -309,6 +327,23 @@ __device__ void lb_etwc(const DevGraph &g, const FrontierIn &fin, int32_t fsize,
             }
         }
         __syncthreads();
+    }
+}
+
+// The handed-off entries, spread over the grid: entry j's arcs in chunks of
+// kCta arcs, chunk c of every entry taken by CTA c mod gridDim.x.
+template <class Op>
+__device__ void lb_etwc_spill(const DevGraph &g, const EtwcEntry<typename Op::S> *q,
+                              const int32_t *cnt, const Op &op, const OutCtx &out, int bid,
+                              int nb) {
+    const int32_t k = *cnt;
+    for (int32_t j = 0; j < k; ++j) {
+        const EtwcEntry<typename Op::S> en = q[j];
+        for (int64_t e = en.beg + (int64_t)bid * kCta + threadIdx.x; e < en.end;
+             e += (int64_t)nb * kCta) {
+            const int32_t v = g.col[e];
+            emit(out, v, op.relax(en.u, en.s, v, (int32_t)e));
+        }
     }
 }
 

@@ -26,8 +26,15 @@ __global__ void __launch_bounds__(kCta) k_push_cta(DevGraph g, FrontierIn fin, i
 }
 template <class Op>
 __global__ void __launch_bounds__(kCta) k_push_etwc(DevGraph g, FrontierIn fin, int32_t fsize,
-                                                    Op op, OutCtx out, unsigned long long *ctr) {
-    lb_etwc(g, fin, fsize, op, out, blockIdx.x, gridDim.x, ctr);
+                                                    Op op, OutCtx out, unsigned long long *ctr,
+                                                    EtwcSpill<typename Op::S> spill) {
+    lb_etwc(g, fin, fsize, op, out, blockIdx.x, gridDim.x, ctr, spill);
+}
+template <class Op>
+__global__ void __launch_bounds__(kCta) k_push_etwc_spill(DevGraph g,
+                                                          const EtwcEntry<typename Op::S> *q,
+                                                          const int32_t *cnt, Op op, OutCtx out) {
+    lb_etwc_spill(g, q, cnt, op, out, blockIdx.x, gridDim.x);
 }
 template <class Op>
 __global__ void __launch_bounds__(kCta) k_push_strict(DevGraph g, FrontierIn fin, int32_t fsize,
@@ -84,9 +91,26 @@ inline g2_status push_round(g2_graph *g, const g2_schedule &s, const Op &op, con
         case G2_LB_CM:
             k_push_cta<<<grid_for(g, fsize, kCta), kCta, 0, st>>>(dg, fin, fsize, op, out, ctr);
             break;
-        case G2_LB_ETWC:
-            k_push_etwc<<<grid_for(g, fsize, kCta), kCta, 0, st>>>(dg, fin, fsize, op, out, ctr);
+        case G2_LB_ETWC: {
+            // entries of kEtwcSpill arcs or more are handed to a second pass
+            // over the whole grid, where the graph has such vertices
+            int32_t maxdeg = 0;
+            G2_TRY(max_out_degree(g, st, &maxdeg));
+            EtwcSpill<typename Op::S> spill{nullptr, nullptr};
+            if (maxdeg >= kEtwcSpill) {
+                int32_t *ctrs;
+                G2_TRY(ws(g, B_CTR, 64, &ctrs));
+                spill.cnt = ctrs + 45;
+                G2_TRY(ws(g, B_TWC_L, (size_t)fsize, &spill.q));
+                G2_CK(cudaMemsetAsync(spill.cnt, 0, sizeof(int32_t), st));
+            }
+            k_push_etwc<<<grid_for(g, fsize, kCta), kCta, 0, st>>>(dg, fin, fsize, op, out, ctr, spill);
+            if (spill.q) {
+                k_push_etwc_spill<<<t->sm_count * 8, kCta, 0, st>>>(dg, spill.q, spill.cnt, op, out);
+                stats().launches += 1;
+            }
             break;
+        }
         case G2_LB_STRICT: {
             int32_t *deg, *scan;
             G2_TRY(ws(g, B_I1, (size_t)fsize + 1, &deg));

@@ -1074,3 +1074,28 @@ def test_async_sssp_and_bfs(g2, rmat14, grid, monkeypatch, cap):
             d2 = dev(g.n)
             g2.g2_bfs_async(dg, src, delta, d2)
             assert np.array_equal(host(d2), od), (g.name, src, delta)
+
+
+def test_etwc_hands_large_entries_to_the_grid(g2):
+    """ETWC PUSH where vertices have 4,096 arcs or more at CTA granularity:
+    their CTA-stage entries go to a frontier-wide list that a second pass
+    spreads over every CTA.  BFS from a hub equals the oracle, and an
+    accumulate over a frontier holding several hubs visits each arc exactly
+    once."""
+    g = gg.disjoint_union(gg.star(9000), gg.star(20000), gg.rmat(12, seed=5), gg.complete(70))
+    for src in (0, 9000, 9001, g.n - 1):
+        od, op = oracle.bfs_graph(g, src)
+        d, p = run_bfs(g2, g, src, g2.schedule("ETWC"))
+        assert np.array_equal(d, od) and np.array_equal(p, op), src
+    rng = np.random.default_rng(3)
+    contrib = rng.integers(1, 64, g.n).astype(np.float32)  # small integers: exact float sums
+    active = np.unique(np.concatenate([[0, 9000], rng.choice(g.n, 2000, replace=False)])).astype(np.int32)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    mask = np.isin(src, active)
+    want = np.bincount(g.col[mask], weights=contrib[src[mask]], minlength=g.n)
+    dg = g2.load_graph(g)
+    fin = g2.Frontier(dg, g2.G2_FRONTIER_SPARSE)
+    fin.set(active)
+    acc = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+    g2.g2_edgeset_apply(dg, g2.G2_OP_PR_ADD, fin, torch.from_numpy(contrib).cuda(), acc, g2.schedule("ETWC"))
+    assert np.array_equal(host(acc), want.astype(np.float32))
