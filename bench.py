@@ -769,7 +769,9 @@ def run_tune_workload(args):
     paper's default schedule (all Table II fields at their defaults).  Then
     a sibling graph of each family (RMAT-19 seed 2, grid 1200^2 seed 2) is
     tuned once from cold and once warm-started from the first graph's cache
-    entry with a sixth of the random samples."""
+    entry with a sixth of the random samples.  For BFS the whole space is
+    also searched exhaustively (every simple schedule of both directions,
+    then hybrids of the fastest), on both graphs."""
     import tempfile
     import torch
     from paper_2012_07990_gb300 import build_native
@@ -836,7 +838,27 @@ def run_tune_workload(args):
                               "cold_evaluations": cold.evaluated,
                               "warm_ms": round(min(cost2(warm.best) for _ in range(3)), 3),
                               "warm_evaluations": warm.evaluated}
+            if algo == "bfs":
+                # the whole space (Table I): every simple schedule of both
+                # directions, then hybrids of the fastest ones; how far the
+                # random + halving search and the warm start land from it
+                ex2 = at.exhaustive(cost2, reps=2)
+                row["sibling"]["exhaustive_ms"] = round(min(cost2(ex2.best) for _ in range(3)), 3)
+                row["sibling"]["exhaustive_evaluations"] = ex2.evaluated
+                row["sibling"]["exhaustive_rejected"] = ex2.rejected
             dg2.free()
+            if algo == "bfs":
+                dg, cost = evaluate(G1, w1, algo)
+                t0 = time.perf_counter()
+                ex = at.exhaustive(cost, reps=2)
+                row["exhaustive"] = {
+                    "ms": round(min(cost(ex.best) for _ in range(3)), 3), "best": ex.best,
+                    "evaluations": ex.evaluated, "rejected": ex.rejected,
+                    "seconds": round(time.perf_counter() - t0, 1),
+                    "push_only_ms": round(ex.per_direction[0]["ms"], 3),
+                    "pull_only_ms": round(ex.per_direction[1]["ms"], 3),
+                    "tuned_over_exhaustive": round(best / min(cost(ex.best) for _ in range(3)), 3)}
+                dg.free()
             rows[algo] = row
         out["graphs"][f"{fam}:{G1.name}"] = rows
     print(json.dumps(out))

@@ -110,6 +110,94 @@ def key_of(d: dict) -> str:
     return json.dumps(d, sort_keys=True)
 
 
+# ---------------------------------------------------------- exhaustive search
+HYBRID_THRESHOLDS = (0.0, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1)
+
+
+def enumerate_direction(direction: int) -> list[dict]:
+    """Every simple schedule of one traversal direction: the cartesian
+    product of the Table II fields (Sec. V, Table I counts 288 per direction
+    for the paper's compiler): load balancing (7) x EdgeBlocking (2) x output
+    frontier creation (3) x kernel fusion (2) x deduplication (PUSH: disabled,
+    or enabled with one of the 3 dedup types -- 4; PULL: disabled or enabled
+    -- 2, times the 2 representations of the PULL input frontier) = 336 points
+    per direction.  Points an algorithm cannot run (EdgeBlocking outside
+    EDGE_ONLY sweeps, EDGE_ONLY without the all-vertices frontier, PULL with
+    a load balancing it has no pull form for, ...) are part of the space; the
+    library rejects them and the search drops them."""
+    out = []
+    for lb in LBS:
+        for eb in (False, True):
+            for fc in (0, 1, 2):
+                for kf in (False, True):
+                    if direction == 0:
+                        for dd in ((False, 0), (True, 0), (True, 1), (True, 2)):
+                            out.append(_simple(lb=lb, edge_blocking=eb, frontier_creation=fc,
+                                               kernel_fusion=kf, dedup=dd[0], dedup_type=dd[1]))
+                    else:
+                        for dedup in (False, True):
+                            for pf in (0, 1):
+                                out.append(_simple(lb=lb, direction=1, edge_blocking=eb,
+                                                   frontier_creation=fc, kernel_fusion=kf,
+                                                   dedup=dedup, pull_frontier=pf))
+    return out
+
+
+@dataclass
+class ExhaustiveResult:
+    best: dict
+    best_ms: float
+    evaluated: int          # points timed (rejected ones included)
+    rejected: int           # points the library refused
+    per_direction: dict     # direction -> (best schedule, ms, points, rejected)
+
+
+def exhaustive(cost, reps: int = 2, top: int = 4,
+               thresholds=HYBRID_THRESHOLDS) -> ExhaustiveResult:
+    """Time every simple schedule of both directions (each alone, criteria
+    NONE), then every hybrid of the `top` fastest PUSH and PULL schedules at
+    each threshold; the fastest of all is the optimum of the space."""
+    timed = []
+    evaluated = rejected = 0
+    per_dir = {}
+    for direction in (0, 1):
+        ok = []
+        pts = enumerate_direction(direction)
+        for s in pts:
+            d = {"criteria": 0, "threshold": 0.0, "s1": s, "s2": s}
+            evaluated += 1
+            try:
+                t = min(cost(d) for _ in range(reps))
+            except Exception:
+                rejected += 1
+                continue
+            ok.append((t, s))
+            timed.append((t, d))
+        ok.sort(key=lambda x: x[0])
+        per_dir[direction] = {"best": ok[0][1] if ok else None, "ms": ok[0][0] if ok else None,
+                              "points": len(pts), "rejected": len(pts) - len(ok)}
+        per_dir[direction]["top"] = [s for _, s in ok[:top]]
+    for s1 in per_dir[0]["top"]:
+        for s2 in per_dir[1]["top"]:
+            if s1["kernel_fusion"] or s2["kernel_fusion"]:
+                continue  # a fused loop runs s1 throughout: no hybrid
+            for tau in thresholds:
+                d = {"criteria": 1, "threshold": tau, "s1": s1, "s2": s2}
+                evaluated += 1
+                try:
+                    t = min(cost(d) for _ in range(reps))
+                except Exception:
+                    rejected += 1
+                    continue
+                timed.append((t, d))
+    timed.sort(key=lambda x: x[0])
+    if not timed:
+        raise RuntimeError("no schedule could be evaluated")
+    for v in per_dir.values():
+        v.pop("top", None)
+    return ExhaustiveResult(timed[0][1], timed[0][0], evaluated, rejected, per_dir)
+
+
 # ------------------------------------------------------------ the search
 @dataclass
 class TuneResult:

@@ -683,6 +683,8 @@ __global__ void k_sssp_rebuild(const int32_t *dist, int32_t n, int32_t T, int32_
 static g2_status check_fused_lb(const g2_schedule &s) {
     if (s.direction != G2_PUSH)
         return fail(G2_EUNSUPPORTED, "fused loops run PUSH rounds");
+    if (s.edge_blocking)
+        return fail(G2_EUNSUPPORTED, "EdgeBlocking applies to EDGE_ONLY full sweeps only");
     switch (s.load_balance) {
         case G2_LB_VERTEX_BASED: case G2_LB_WM: case G2_LB_CM: case G2_LB_ETWC: return G2_OK;
         default:

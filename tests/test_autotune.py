@@ -29,6 +29,52 @@ def test_samples_are_valid_points():
                 assert d["s1"]["delta"] >= 1
 
 
+def test_exhaustive_space_enumerates_every_table_ii_point_once():
+    """Per direction the space is the cartesian product of the Table II
+    fields: 7 load balancers x EdgeBlocking (2) x frontier creation (3) x
+    kernel fusion (2) x deduplication (PUSH 4: off or one of 3 types; PULL 2,
+    times the 2 PULL input representations) = 336 distinct points, each with
+    the direction's value."""
+    for direction in (0, 1):
+        pts = at.enumerate_direction(direction)
+        assert len(pts) == 7 * 2 * 3 * 2 * 4 == 336
+        assert len({at.key_of(p) for p in pts}) == len(pts)
+        assert all(p["direction"] == direction for p in pts)
+        assert {p["lb"] for p in pts} == set(at.LBS)
+        assert sum(p["edge_blocking"] for p in pts) == 168
+        assert sum(p["kernel_fusion"] for p in pts) == 168
+    push = at.enumerate_direction(0)
+    assert {(p["dedup"], p["dedup_type"]) for p in push} == {(False, 0), (True, 0), (True, 1), (True, 2)}
+    pull = at.enumerate_direction(1)
+    assert {(p["dedup"], p["pull_frontier"]) for p in pull} == {(a, b) for a in (False, True) for b in (0, 1)}
+
+
+def test_exhaustive_search_finds_the_optimum_and_drops_rejected_points():
+    """On a synthetic cost (refusing EdgeBlocking and fused PULL as the
+    library does) the exhaustive search returns the true minimum over simple
+    and hybrid schedules, counts every point, and reports each direction's
+    best."""
+    def base(s):
+        if s["edge_blocking"] or (s["direction"] == 1 and s["kernel_fusion"]):
+            raise RuntimeError("unsupported")
+        return (5.0 + at.LBS.index(s["lb"]) + s["frontier_creation"] + (0.5 if s["dedup"] else 0.0)
+                + (1.7 if s["kernel_fusion"] else 0.0))
+
+    def cost(d):
+        if d["criteria"] == 0:
+            return base(d["s1"])
+        return 0.6 * base(d["s1"]) + 0.3 * base(d["s2"]) + (0.0 if d["threshold"] == 0.02 else 0.1)
+
+    res = at.exhaustive(cost, reps=1)
+    assert res.per_direction[0]["ms"] == 5.0 and res.per_direction[1]["ms"] == 5.0
+    assert res.best["criteria"] == 1 and res.best["threshold"] == 0.02
+    assert abs(res.best_ms - 4.5) < 1e-9
+    assert res.rejected >= 336  # every EdgeBlocking point of both directions, fused PULL
+    # every simple point of both directions, then the hybrids of the 4
+    # fastest PUSH x the 4 fastest PULL schedules (none fused here) at each threshold
+    assert res.evaluated == 2 * 336 + 4 * 4 * len(at.HYBRID_THRESHOLDS)
+
+
 def test_successive_halving_finds_the_minimum_under_noise():
     rng = random.Random(3)
     cands = [{"x": i} for i in range(40)]
