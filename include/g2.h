@@ -323,7 +323,12 @@ g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc,
  * balancing but EDGE_ONLY, PULL with VERTEX_BASED or WM, or kernel fusion with
  * WM PUSH (the whole loop in one cooperative kernel).  NULL schedule: the
  * direction-optimising hybrid (STRICT PUSH below 2% of n, VERTEX_BASED PULL);
- * fused WM PUSH on a bounded-degree graph (largest out-degree <= 32). */
+ * on a bounded-degree graph (largest out-degree <= 32) the sources run as
+ * single-source fused WM queries, about one per 12 SMs at a time, each on an
+ * internal view of the graph and a stream of its own driven by a library
+ * thread (their one-cluster loops share the GPU; the caller's stream is
+ * synchronised first; G2_BATCH_SPLIT_WORKERS sets the count, 0 runs the
+ * fused multi-source loop instead). */
 g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
                        const g2_hybrid *sched, void *stream);
 
@@ -334,8 +339,10 @@ g2_status g2_bfs_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t *dep
  * near/far queue of g2_sssp_delta (one bit per source in per-vertex masks).
  * Schedules: PUSH with any frontier load balancing but EDGE_ONLY, or kernel
  * fusion with WM PUSH (the whole loop in one cooperative kernel).  NULL
- * schedule: STRICT PUSH; fused WM PUSH on a bounded-degree graph (largest
- * out-degree <= 32). */
+ * schedule: STRICT PUSH; on a bounded-degree graph (largest out-degree <= 32)
+ * the sources run as single-source fused WM queries, about one per 19 SMs at
+ * a time, as g2_bfs_batch does (G2_BATCH_SPLIT_WORKERS = 0: the fused
+ * multi-source loop). */
 g2_status g2_sssp_batch(g2_graph *g, const int32_t *srcs, int32_t k, int32_t delta,
                         int32_t *dist, const g2_hybrid *sched, void *stream);
 

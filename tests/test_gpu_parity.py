@@ -731,12 +731,19 @@ def test_bfs_batch(g2):
             assert np.array_equal(host(depth).reshape(k, g.n), want[:k]), k
 
 
-def test_bfs_batch_fused_on_a_road_grid(g2, grid):
-    """Bounded-degree graph: the NULL schedule runs the fused multi-source
-    loop (one launch), with repeated sources and a ragged k."""
+def test_bfs_batch_fused_on_a_road_grid(g2, grid, monkeypatch):
+    """Bounded-degree graph, with repeated sources and a ragged k.  The NULL
+    schedule splits the batch into single-source fused queries on worker
+    streams (k = 1 runs one); with the split switched off it, like the
+    explicit fused schedule, runs the fused multi-source loop in one launch."""
     srcs = np.concatenate([gg.random_sources(grid, 40, seed=3), [7, 7, 0]]).astype(np.int32)
     want = np.stack([oracle.bfs_graph(grid, s, want_parent=False)[0] for s in srcs])
     dg = g2.load_graph(grid)
+    for k in (len(srcs), 2, 1):
+        depth = dev(k * grid.n)
+        g2.g2_bfs_batch(dg, srcs[:k], depth, None)
+        assert np.array_equal(host(depth).reshape(k, grid.n), want[:k]), k
+    monkeypatch.setenv("G2_BATCH_SPLIT_WORKERS", "0")
     for s in (None, g2.schedule("WM", kernel_fusion=True)):
         depth = dev(len(srcs) * grid.n)
         g2.g2_bfs_batch(dg, srcs, depth, s)
@@ -763,19 +770,24 @@ def test_sssp_batch(g2):
                 assert np.array_equal(host(dist).reshape(k, g.n), want[:k]), (delta, k)
 
 
-def test_sssp_batch_fused_on_a_road_grid(g2, grid):
-    """Bounded-degree graph: the NULL schedule runs the fused multi-source
-    near/far loop (one launch after seeding) for every delta, with repeated
-    sources and a ragged k."""
+def test_sssp_batch_fused_on_a_road_grid(g2, grid, monkeypatch):
+    """Bounded-degree graph, every delta, with repeated sources and a ragged
+    k.  The NULL schedule splits the batch into single-source fused queries on
+    worker streams; with the split switched off it runs the fused multi-source
+    near/far loop (one launch after seeding)."""
     w = gg.pair_weights(grid, 1000, seed=4)
     srcs = np.concatenate([gg.random_sources(grid, 27, seed=4), [9, 9]]).astype(np.int32)
     want = np.stack([oracle.sssp_graph(grid, w, s) for s in srcs])
     dg = g2.load_graph(grid, w)
-    for delta in (0, 1, 300, 5000, 1 << 30):
-        dist = dev(len(srcs) * grid.n)
-        g2.g2_sssp_batch(dg, srcs, delta, dist, None)
-        assert np.array_equal(host(dist).reshape(len(srcs), grid.n), want), delta
-        assert g2.g2_last_stats()["launches"] == 3
+    for split in ("", "0"):
+        if split:
+            monkeypatch.setenv("G2_BATCH_SPLIT_WORKERS", split)
+        for delta in (0, 1, 300, 5000, 1 << 30):
+            dist = dev(len(srcs) * grid.n)
+            g2.g2_sssp_batch(dg, srcs, delta, dist, None)
+            assert np.array_equal(host(dist).reshape(len(srcs), grid.n), want), (delta, split)
+            if split:
+                assert g2.g2_last_stats()["launches"] == 3
     with pytest.raises(g2.G2Error) as e:
         g2.g2_sssp_batch(dg, srcs[:3], 64, dev(3 * grid.n), g2.schedule("ETWC", kernel_fusion=True))
     assert e.value.status == g2.G2_EUNSUPPORTED
