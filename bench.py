@@ -1091,7 +1091,10 @@ def run_profile_case(args):
       WM BFS from vertex 0 (no parent array) and one fused WM delta-stepping
       SSSP from vertex 0 with delta 1024 -- the one-cluster loops;
     * bc_rmat: RMAT at --scale, BC from its two highest-degree vertices with
-      the NULL schedule -- the level passes on a power-law graph."""
+      the NULL schedule -- the level passes on a power-law graph;
+    * batch_grid: the --grid x --grid road grid, the fused multi-source loops
+      (64-source BFS, 32-source SSSP with delta 4096), the split into
+      single-source queries switched off."""
     import torch
     from paper_2012_07990_gb300 import build_native
     build_native.build()
@@ -1107,6 +1110,25 @@ def run_profile_case(args):
         g2.g2_bfs(dg, 0, out, None, s)
         bfs = g2.g2_last_stats()
         g2.g2_sssp_delta(dg, 0, 1024, out, s)
+        sssp = g2.g2_last_stats()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": case, "grid": args.grid, "bfs_levels": bfs["iterations"],
+                          "bfs_launches": bfs["launches"], "sssp_rounds": sssp["iterations"],
+                          "sssp_launches": sssp["launches"]}))
+        return
+    if case == "batch_grid":
+        # the fused multi-source loops on a road grid (the split into
+        # single-source queries switched off): 64-source BFS, then 32-source
+        # delta-stepping SSSP with delta 4096
+        os.environ["G2_BATCH_SPLIT_WORKERS"] = "0"
+        G = gg.road_grid(args.grid, seed=1)
+        w = gg.pair_weights(G, 1000, seed=1)
+        dg = g2.load_graph(G, w)
+        srcs = gg.random_sources(G, 64, seed=1)
+        out = torch.empty(64 * G.n, dtype=torch.int32, device="cuda")
+        g2.g2_bfs_batch(dg, srcs, out, None)
+        bfs = g2.g2_last_stats()
+        g2.g2_sssp_batch(dg, srcs[:32], 4096, out, None)
         sssp = g2.g2_last_stats()
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": case, "grid": args.grid, "bfs_levels": bfs["iterations"],
@@ -1140,7 +1162,8 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["pr", "bfs", "cc", "road_fused", "bc_rmat"], default=None)
+    ap.add_argument("--profile-case", choices=["pr", "bfs", "cc", "road_fused", "bc_rmat", "batch_grid"],
+                    default=None)
     ap.add_argument("--serve-pool", choices=["full", "small"], default="full")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=1.0)
