@@ -38,6 +38,15 @@ constexpr int kPartTile = 2048;
 constexpr int kPartMaxKeys = 1024;
 constexpr int kPartCta = 256;
 
+// floor(x / d) for 0 <= x < 2^31 and 1 <= d < 2^24: a float estimate from the
+// reciprocal, then the exact correction (the estimate is off by at most one)
+__device__ __forceinline__ int32_t div_floor(int32_t x, int32_t d, float inv) {
+    int32_t q = __float2int_rz((float)x * inv);
+    if (q * d > x) --q;
+    else if ((q + 1) * d <= x) ++q;
+    return q;
+}
+
 __global__ void __launch_bounds__(kPartCta) k_part_count(const int32_t *vals, int32_t div,
                                                          int64_t count, int32_t nkeys,
                                                          int32_t ntiles, int32_t *counts) {
@@ -49,9 +58,11 @@ __global__ void __launch_bounds__(kPartCta) k_part_count(const int32_t *vals, in
         for (int k = lane; k < nkeys; k += 32) c[k] = 0;
         __syncwarp();
         const int64_t base = (int64_t)tile * kPartTile;
+        const float inv = 1.0f / (float)div;
+#pragma unroll 8
         for (int s = 0; s < kPartTile / 32; ++s) {
             const int64_t i = base + s * 32 + lane;
-            if (i < count) atomicAdd(&c[vals[i] / div], 1);
+            if (i < count) atomicAdd(&c[div_floor(vals[i], div, inv)], 1);
         }
         __syncwarp();
         for (int k = lane; k < nkeys; k += 32) counts[(int64_t)k * ntiles + tile] = c[k];
@@ -165,20 +176,32 @@ __global__ void __launch_bounds__(kPartCta) k_blk_place(const int32_t *srank, co
         for (int k = lane; k < nkeys; k += 32) c[k] = scan[(int64_t)k * ntiles + tile] + shift[k];
         __syncwarp();
         const int64_t base = (int64_t)tile * kPartTile;
-        for (int s = 0; s < kPartTile / 32; ++s) {
-            const int64_t i = base + s * 32 + lane;
-            const int32_t sr = i < count ? srank[i] : 0;
-            const int key = i < count ? sr / S : -1;
-            const unsigned peers = __match_any_sync(G2_FULL, key);
-            const int r = __popc(peers & lt);
-            if (key >= 0) {
-                const int32_t p = c[key] + r;
-                loc[p] = (uint16_t)(sr - key * S);
-                dst[p] = drank[i];
+        const float inv = 1.0f / (float)S;
+        // eight steps' ranks are loaded at once, so the placement's chain
+        // (match, counter, store) does not wait on a load every step
+        constexpr int kB = 8;
+        for (int s0 = 0; s0 < kPartTile / 32; s0 += kB) {
+            int32_t sr[kB], dr[kB];
+#pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                const int64_t i = base + (s0 + j) * 32 + lane;
+                sr[j] = i < count ? srank[i] : -1;
+                dr[j] = i < count ? drank[i] : 0;
             }
-            __syncwarp();
-            if (key >= 0 && r == 0) c[key] += __popc(peers);
-            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                const int key = sr[j] >= 0 ? div_floor(sr[j], S, inv) : -1;
+                const unsigned peers = __match_any_sync(G2_FULL, key);
+                const int r = __popc(peers & lt);
+                if (key >= 0) {
+                    const int32_t p = c[key] + r;
+                    loc[p] = (uint16_t)(sr[j] - key * S);
+                    dst[p] = dr[j];
+                }
+                __syncwarp();
+                if (key >= 0 && r == 0) c[key] += __popc(peers);
+                __syncwarp();
+            }
         }
     }
 }
