@@ -960,13 +960,16 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     auto bail = [&](g2_status s) { g2_free_graph(g); return s; };
     cudaError_t e;
     if ((e = cudaGetDevice(&t->device)) != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
-    // two attribute queries (the full property query costs milliseconds)
-    int sms = 0, l2 = 0;
+    // three attribute queries (the full property query costs milliseconds)
+    int sms = 0, l2 = 0, optin = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, t->device)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, t->device)) != cudaSuccess)
+        (e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, t->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, t->device)) !=
+            cudaSuccess)
         return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
     t->sm_count = sms;
     t->l2_bytes = l2;
+    t->smem_optin = optin;
     t->max_coop_blocks = 0;
     if (finish_handle(g) != G2_OK) return bail(G2_ENOMEM);
     // every array carries kPad spare elements (zeroed) so that a 16-byte

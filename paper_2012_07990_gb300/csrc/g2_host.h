@@ -108,6 +108,7 @@ struct Topology {
     int device;
     int sm_count;
     int64_t l2_bytes;
+    int32_t smem_optin;   // largest dynamic shared memory a CTA may opt into
     int max_coop_blocks;  // resident CTAs of kCta threads for the fused kernels
     int32_t *rowptr, *col, *w;     // CSR
     int32_t *crowptr, *ccol, *cw;  // CSC (== CSR pointers when symmetric)

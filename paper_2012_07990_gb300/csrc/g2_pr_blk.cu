@@ -260,9 +260,9 @@ __global__ void k_blk_lane_heads(const uint32_t *head, int64_t lanes, uint16_t *
     }
 }
 
-// nzrow[k] = destination rank of the k-th run
+// nzrow1[k + 1] = destination rank of the k-th run
 __global__ void k_blk_nzrow(const uint32_t *head, const int32_t *chunk_rank, const int32_t *dst,
-                            int64_t words, int32_t *nzrow) {
+                            int64_t words, int32_t *nzrow1) {
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
          w += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = w / kBlkHeadWords;
@@ -272,7 +272,7 @@ __global__ void k_blk_nzrow(const uint32_t *head, const int32_t *chunk_rank, con
         while (bits) {
             const int j = __ffs(bits) - 1;
             bits &= bits - 1;
-            nzrow[r++] = dst[w * 32 + j];
+            nzrow1[++r] = dst[w * 32 + j];
         }
     }
 }
@@ -388,8 +388,6 @@ __global__ void __launch_bounds__(kCta, 6) k_pr_blk_vertex(const int32_t *deg, c
 }
 
 // ------------------------------------------------------------ host side
-constexpr int kBlkCta = 1024;
-
 static int part_grid(const g2_graph *g, int32_t ntiles) {
     const int wpc = kPartCta / 32;
     int64_t b = ((int64_t)ntiles + wpc - 1) / wpc;
@@ -465,6 +463,7 @@ static void free_blk(Topology *t, cudaStream_t st) {
 // Whether the source-blocked layout applies to t with blocks of S sources.
 bool pr_blk_applies(const Topology *t, int32_t S) {
     if (S < 256 || S > kBlkMaxS || (S & 3)) return false;
+    if (blk_smem_bytes(S) > (size_t)t->smem_optin) return false;
     const int64_t nb = ((int64_t)t->n + S - 1) / S;
     if (t->n == 0 || nb > kPartMaxKeys) return false;
     // padded arcs must stay int32-addressable
@@ -542,7 +541,11 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
                               st));
         G2_CK(cudaStreamSynchronize(st));
         const int32_t nruns = g->h_ctr[51];
-        G2_CK(dmalloc(&t->blk_nzrow, ((size_t)nruns + 1) * 4, st));
+        // run r's row at r + 1; entry 0 and the kPad entries past the last
+        // run point at the spare slot n
+        G2_CK(dmalloc(&t->blk_nzrow, ((size_t)nruns + 1 + kPad) * 4, st));
+        k_fill_i32_blk<<<1, 32, 0, st>>>(t->blk_nzrow, 1, n);
+        k_fill_i32_blk<<<1, kPad, 0, st>>>(t->blk_nzrow + (size_t)nruns + 1, kPad, n);
         k_blk_nzrow<<<grid_for(g, words, kCta), kCta, 0, st>>>(head, t->blk_chunk_rank, dst, words,
                                                                t->blk_nzrow);
         const int64_t lanes = nchunks * 32;
@@ -552,7 +555,7 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
         if (const char *e = getenv("G2_PR_BLK_RUNCOST")) runcost = std::max(0, atoi(e));
         k_blk_cta_split<<<(G + 1 + kCta - 1) / kCta, kCta, 0, st>>>(t->blk_chunk_rank, nchunks, G,
                                                                     runcost, t->blk_cta);
-        stats().launches += 9;
+        stats().launches += 11;
         dfree(ccount, st);
         dfree(dst, st);
         dfree(head, st);
@@ -610,10 +613,21 @@ g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *ran
         double *dprev = dd + 2 + (it & 1);
         KTime kt;
         ktime_begin(kt, "pr_round", st);
-        kern<<<grid, kBlkCta, smem, st>>>(reinterpret_cast<const uint4 *>(t->blk_loc), t->blk_lane_heads,
-                                          t->blk_chunk_rank, t->blk_nzrow, t->blk_bchunk,
-                                          t->blk_nb, t->blk_cta, S, nshare, cbuf[it & 1], y,
-                                          dd + 8, dprev);
+        BlkSweepArgs a;
+        a.loc4 = reinterpret_cast<const uint4 *>(t->blk_loc);
+        a.lane_heads = t->blk_lane_heads;
+        a.chunk_rank = t->blk_chunk_rank;
+        a.nzrow1 = t->blk_nzrow;
+        a.bchunk = t->blk_bchunk;
+        a.nb = t->blk_nb;
+        a.cta_chunk = t->blk_cta;
+        a.S = S;
+        a.nshare = nshare;
+        a.share = cbuf[it & 1];
+        a.y = y;
+        a.dslots = dd + 8;
+        a.dfin = dprev;
+        kern<<<grid, kBlkCta, smem, st>>>(a);
         ktime_end(kt, st);
         KTime kv;
         ktime_begin(kv, "pr_vertex", st);
