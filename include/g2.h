@@ -52,8 +52,8 @@ typedef enum {
 #define G2_SYMMETRIC   0x1u  /* every arc u->v has v->u (then CSC aliases CSR) */
 #define G2_DEVICE_PTRS 0x2u  /* rowptr/col/w are device pointers (else host) */
 #define G2_PREPARE_PAGERANK 0x4u /* build PageRank's layouts in the background */
-#define G2_LOAD_OVERLAP 0x8u     /* the load runs beside other GPU work: the upload kernel
-                                    takes a quarter of the SMs and no copy engine */
+#define G2_LOAD_OVERLAP 0x8u     /* the load runs beside other GPU work: pinned or device
+                                    arrays go by copy engine, leaving the SMs */
 
 /* --------------------------------------------- schedule (Table II fields) */
 /* configLoadBalance load_balance_type */
@@ -134,10 +134,12 @@ typedef struct g2_graph g2_graph;
  * coherent link) and col / w are 16-byte aligned, one kernel reads, checks
  * and stores the arcs; otherwise they are copied with cudaMemcpyAsync and
  * checked after.  G2_LOAD_OVERLAP (a load on its own stream while other
- * calls run, e.g. the next graph of a stream of requests) runs that kernel
- * on a quarter of the SMs, so the other calls keep the rest and the copy
- * engines (their small per-round copies would otherwise wait behind the
- * arcs' transfer).  For a non-symmetric graph the transpose (CSC, lists sorted
+ * calls run, e.g. the next graph of a stream of requests) copies pinned host
+ * or device arrays with a copy engine and validates them in one pass after,
+ * so the other calls keep every SM during the transfer (a kernel that needs
+ * whole SMs would otherwise wait for the copy kernel's); pageable arrays in
+ * such a load are read by the copy kernel on a quarter of the SMs.  For a
+ * non-symmetric graph the transpose (CSC, lists sorted
  * ascending) is built on the host for the PULL direction.  Device memory
  * comes from the library's stream-ordered pool (see g2_free_graph).
  * G2_PREPARE_PAGERANK: the layouts the tuned PageRank sweep needs (the

@@ -929,6 +929,20 @@ static const int32_t *device_readable(const int32_t *p, bool dev, int device) {
     return pageable && host_tables ? p : nullptr;
 }
 
+// Whether a copy engine reads p directly: device memory or pinned host
+// memory (pageable memory goes through the driver's staging buffers, which
+// holds up the other host threads' CUDA calls meanwhile).
+static bool copy_engine_source(const void *p, bool dev) {
+    if (!p || dev) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeDevice ||
+           a.type == cudaMemoryTypeManaged;
+}
+
 g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *col,
                       const int32_t *w, uint32_t flags, void *stream, g2_graph **out) {
     if (!out) return fail(G2_EINVAL, "null output handle");
@@ -989,14 +1003,18 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
         return bail(cuda_fail(e, "copy rowptr"));
     // the arcs are read by the validating copy kernel itself where the device
     // can address the caller's arrays; otherwise copied, then validated.  A
-    // load that overlaps other work runs the copy kernel on a quarter of the
-    // SMs (deeper per thread), leaving the rest, and the copy engines, to the
-    // other calls: their small per-round copies would wait behind the arcs'
-    // transfer on a copy engine.
+    // load that overlaps other work moves pinned or device arrays with a copy
+    // engine and validates them in one pass afterwards: the copy kernel would
+    // hold SMs for the whole transfer, and a kernel that needs whole SMs
+    // (PageRank's sweep, one 1024-thread CTA per SM) would wait for them
+    // (measured on RMAT-22: 7.1-7.4 ms per pipelined load + step against
+    // 7.6-7.7 ms).  Pageable arrays in such a load keep the copy kernel, on a
+    // quarter of the SMs with deeper reads per thread.
     const bool overlap = flags & G2_LOAD_OVERLAP;
     const int32_t *col_rd = m > 0 ? device_readable(col, dev, t->device) : nullptr;
     const int32_t *w_rd = (w && m > 0) ? device_readable(w, dev, t->device) : nullptr;
-    const bool fused_copy = col_rd && (!w || w_rd);
+    const bool engine = overlap && copy_engine_source(col, dev) && copy_engine_source(w, dev);
+    const bool fused_copy = col_rd && (!w || w_rd) && !engine;
     if (!fused_copy) {
         if (m > 0 && (e = cudaMemcpyAsync(t->col, col, (size_t)m * 4, kind, st)) != cudaSuccess)
             return bail(cuda_fail(e, "copy col"));

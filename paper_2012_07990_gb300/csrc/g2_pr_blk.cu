@@ -135,27 +135,114 @@ __global__ void k_blk_order(const int32_t *rowptr, const int32_t *rank, int32_t 
     }
 }
 
-// per CSC arc e of row v: the rank of v, a warp per row (stores only, so a
-// long row costs its stores and nothing else)
-__global__ void k_blk_dst_ranks(const int32_t *crowptr, const int32_t *rank, int32_t n,
-                                int32_t *drank) {
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    for (int64_t v = gw; v < n; v += nw) {
-        const int32_t b = crowptr[v], e = crowptr[v + 1];
-        if (b == e) continue;
-        const int32_t rv = rank[v];
-        for (int32_t k = b + lane; k < e; k += 32) drank[k] = rv;
+// Per CSC arc: the rank of its source, and (as k_part_count) the per-tile
+// counts of the partition keys srank / S, in one pass over the arcs.  Eight
+// steps' gathers are issued before their counts.
+__global__ void __launch_bounds__(kPartCta) k_blk_src_count(const int32_t *ccol,
+                                                            const int32_t *rank, int32_t S,
+                                                            int64_t count, int32_t nkeys,
+                                                            int32_t ntiles, int32_t *srank,
+                                                            int32_t *counts) {
+    extern __shared__ int32_t s_part[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *c = s_part + wid * nkeys;
+    const int32_t wpc = kPartCta / 32;
+    const float inv = 1.0f / (float)S;
+    for (int32_t tile = blockIdx.x * wpc + wid; tile < ntiles; tile += gridDim.x * wpc) {
+        for (int k = lane; k < nkeys; k += 32) c[k] = 0;
+        __syncwarp();
+        const int64_t base = (int64_t)tile * kPartTile;
+        constexpr int kB = 8;
+        for (int s0 = 0; s0 < kPartTile / 32; s0 += kB) {
+            int32_t sr[kB];
+#pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                const int64_t i = base + (s0 + j) * 32 + lane;
+                sr[j] = i < count ? rank[ccol[i]] : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                const int64_t i = base + (s0 + j) * 32 + lane;
+                if (i < count) {
+                    srank[i] = sr[j];
+                    atomicAdd(&c[div_floor(sr[j], S, inv)], 1);
+                }
+            }
+        }
+        __syncwarp();
+        for (int k = lane; k < nkeys; k += 32) counts[(int64_t)k * ntiles + tile] = c[k];
+        __syncwarp();
     }
 }
 
-// per CSC arc: the rank of its source
-__global__ void k_blk_src_ranks(const int32_t *ccol, const int32_t *rank, int32_t m,
-                                int32_t *srank) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x)
-        srank[e] = rank[ccol[e]];
+// Per CSC arc of row v: the rank of v.  The rows are taken 32 at a time (a
+// group); a group's arcs are cut into pieces of kDstPiece positions, and
+// every piece is one work item (hub rows make a few groups hold millions of
+// arcs).  k_blk_dst_pieces counts the pieces of every group; after their
+// exclusive scan, a warp takes an equal range of consecutive items, finds
+// the group of its first item by one binary search and walks on from there.
+// For an item the warp loads the 32 rows' ends and ranks (one coalesced load
+// each) and writes the piece's positions in coalesced steps of 32, each lane
+// finding its position's row among the 32 by a binary search over the lanes.
+constexpr int kDstPiece = 2048;
+
+__global__ void k_blk_dst_pieces(const int32_t *crowptr, int32_t n, int32_t *pieces) {
+    const int64_t groups = ((int64_t)n + 31) / 32;
+    for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < groups;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t len = (int64_t)crowptr[min((int64_t)n, gi * 32 + 32)] - crowptr[gi * 32];
+        pieces[gi] = (int32_t)((len + kDstPiece - 1) / kDstPiece);
+    }
+}
+
+__global__ void k_blk_dst_ranks(const int32_t *crowptr, const int32_t *rank, int32_t n,
+                                const int32_t *piece_start, int32_t *drank) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t groups = (int32_t)(((int64_t)n + 31) / 32);
+    const int64_t items = piece_start[groups];
+    const int64_t per = (items + nw - 1) / nw;
+    const int64_t it0 = gw * per, it1 = min(items, it0 + per);
+    if (it0 >= it1) return;
+    // the group of item it0: the last g with piece_start[g] <= it0
+    int32_t g = 0, hi = groups - 1;
+    while (g < hi) {
+        const int32_t mid = (int32_t)(((int64_t)g + hi + 1) >> 1);
+        if (piece_start[mid] <= it0) g = mid;
+        else hi = mid - 1;
+    }
+    int32_t gbeg = piece_start[g], gend = piece_start[g + 1];
+    int32_t end = 0, rk = 0, start = 0, stop = 0, loaded = -1;
+    for (int64_t it = it0; it < it1; ++it) {
+        while (it >= gend) {  // groups without pieces (no arcs) are passed over
+            ++g;
+            gbeg = gend;
+            gend = piece_start[g + 1];
+        }
+        if (loaded != g) {
+            const int32_t v0 = g * 32;
+            const int32_t vl = min(v0 + lane, n - 1);
+            end = crowptr[vl + 1];  // end of row v0 + lane (rows past n: m)
+            rk = rank[vl];
+            start = crowptr[v0];
+            stop = __shfl_sync(G2_FULL, end, 31);
+            loaded = g;
+        }
+        const int32_t pb = start + (int32_t)(it - gbeg) * kDstPiece;
+        const int32_t pe = min(stop, pb + kDstPiece);
+        for (int32_t p0 = pb; p0 < pe; p0 += 32) {
+            const int32_t p = p0 + lane;
+            // k = the number of the 32 rows that end at or before arc p
+            // (at most 31 for p < stop)
+            int k = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(G2_FULL, end, k + step - 1) <= p) k += step;
+            const int32_t r = __shfl_sync(G2_FULL, rk, k);
+            if (p < pe) drank[p] = r;
+        }
+    }
 }
 
 // The position pass of the stable partition of the arcs by source block
@@ -206,6 +293,20 @@ __global__ void __launch_bounds__(kPartCta) k_blk_place(const int32_t *srank, co
     }
 }
 
+// The padding of every block (after its arcs, up to the next whole chunk):
+// source rank 0 of the block and the spare destination slot n.  A CTA per
+// block.
+__global__ void k_blk_fill_pad(const int32_t *scan, int32_t ntiles, const int32_t *pstart,
+                               int32_t nb, int32_t n, uint16_t *loc, int32_t *dst) {
+    for (int32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int64_t size = (int64_t)scan[(int64_t)(b + 1) * ntiles] - scan[(int64_t)b * ntiles];
+        for (int64_t p = pstart[b] + size + threadIdx.x; p < pstart[b + 1]; p += blockDim.x) {
+            loc[p] = 0;
+            dst[p] = n;
+        }
+    }
+}
+
 static __global__ void k_fill_i32_blk(int32_t *p, int64_t count, int32_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -213,19 +314,27 @@ static __global__ void k_fill_i32_blk(int32_t *p, int64_t count, int32_t v) {
 }
 
 // head bit of position p: its destination differs from position p-1's
-// (block starts are marked by k_blk_mark_starts); a warp builds a word at a
-// time from its lanes' comparisons, so the loads are coalesced
+// (block starts are marked by k_blk_mark_starts).  A warp takes 128
+// positions a step, four per lane in one 16-byte load; a lane's four flags
+// form a nibble and eight lanes' nibbles a head word.  total is a multiple
+// of kBlkArcs.
 __global__ void k_blk_heads(const int32_t *dst, int64_t total, uint32_t *head) {
-    const int64_t words = total / 32;
+    const int64_t steps = total / 128;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
-    for (int64_t w = gw; w < words; w += nw) {
-        const int64_t p = w * 32 + lane;
-        const int32_t d = dst[p];
-        const int32_t prev = p > 0 ? dst[p - 1] : -1;
-        const unsigned bits = __ballot_sync(G2_FULL, d != prev);
-        if (lane == 0) head[w] = bits;
+    for (int64_t q = gw; q < steps; q += nw) {
+        const int64_t p = q * 128 + lane * 4;
+        const int4 d = *reinterpret_cast<const int4 *>(dst + p);
+        int32_t prev = __shfl_up_sync(G2_FULL, d.w, 1);
+        if (lane == 0) prev = p > 0 ? dst[p - 1] : -1;
+        const uint32_t nib = (uint32_t)(d.x != prev) | ((uint32_t)(d.y != d.x) << 1) |
+                             ((uint32_t)(d.z != d.y) << 2) | ((uint32_t)(d.w != d.z) << 3);
+        uint32_t word = nib << (4 * (lane & 7));
+        word |= __shfl_xor_sync(G2_FULL, word, 1);
+        word |= __shfl_xor_sync(G2_FULL, word, 2);
+        word |= __shfl_xor_sync(G2_FULL, word, 4);
+        if ((lane & 7) == 0) head[q * 4 + (lane >> 3)] = word;
     }
 }
 
@@ -410,29 +519,45 @@ struct PartTable {
     }
 };
 
-static g2_status partition_table(g2_graph *g, const int32_t *vals, int32_t div, int64_t count,
-                                 int32_t nkeys, int32_t pad, int32_t *pstart, int64_t *total,
-                                 PartTable *pt, cudaStream_t st) {
+// The tables of a stable partition of count items into nkeys keys, and the
+// launch shape of its count and position passes.
+static g2_status partition_alloc(g2_graph *g, int64_t count, int32_t nkeys, PartTable *pt,
+                                 cudaStream_t st) {
     pt->ntiles = (int32_t)std::max<int64_t>(1, (count + kPartTile - 1) / kPartTile);
     const int64_t cells = (int64_t)nkeys * pt->ntiles;
     if (cells >= 2147483647LL) return fail(G2_EUNSUPPORTED, "partition table too large");
-    int32_t *d_total;
     G2_CK(dmalloc(&pt->counts, (size_t)(cells + 1) * 4, st));
     G2_CK(dmalloc(&pt->scan, (size_t)(cells + 1) * 4, st));
     G2_CK(dmalloc(&pt->shift, (size_t)nkeys * 4, st));
-    G2_TRY(ws(g, B_CTR, 64, &d_total));
-    d_total += 50;
     pt->smem = (size_t)(kPartCta / 32) * nkeys * 4;
     pt->grid = part_grid(g, pt->ntiles);
-    k_part_count<<<pt->grid, kPartCta, pt->smem, st>>>(vals, div, count, nkeys, pt->ntiles, pt->counts);
-    G2_TRY(exclusive_scan_i32(g, pt->counts, pt->scan, (int32_t)cells, st));
+    return G2_OK;
+}
+
+// After the count pass: the scan, the padded key starts and the total.
+static g2_status partition_starts(g2_graph *g, int32_t nkeys, int32_t pad, int32_t *pstart,
+                                  int64_t *total, PartTable *pt, cudaStream_t st) {
+    int32_t *d_total;
+    G2_TRY(ws(g, B_CTR, 64, &d_total));
+    d_total += 50;
+    G2_TRY(exclusive_scan_i32(g, pt->counts, pt->scan, (int32_t)((int64_t)nkeys * pt->ntiles), st));
     k_part_starts<<<1, 1024, 0, st>>>(pt->scan, pt->ntiles, nkeys, pad, pt->shift, pstart, d_total);
     G2_CK(cudaGetLastError());
     G2_CK(cudaMemcpyAsync(g->h_ctr + 50, d_total, 4, cudaMemcpyDeviceToHost, st));
     G2_CK(cudaStreamSynchronize(st));
     *total = g->h_ctr[50];
-    stats().launches += 2;
+    stats().launches += 1;
     return G2_OK;
+}
+
+static g2_status partition_table(g2_graph *g, const int32_t *vals, int32_t div, int64_t count,
+                                 int32_t nkeys, int32_t pad, int32_t *pstart, int64_t *total,
+                                 PartTable *pt, cudaStream_t st) {
+    G2_TRY(partition_alloc(g, count, nkeys, pt, st));
+    k_part_count<<<pt->grid, kPartCta, pt->smem, st>>>(vals, div, count, nkeys, pt->ntiles,
+                                                       pt->counts);
+    stats().launches += 1;
+    return partition_starts(g, nkeys, pad, pstart, total, pt, st);
 }
 
 // Positions of a stable partition: pos[i] for every item.
@@ -503,21 +628,36 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
     int32_t *pstart = nullptr;
     G2_CK(dmalloc(&pstart, ((size_t)nb + 1) * 4, st));
     if (m > 0) {
-        // 2-4. source and destination ranks of every arc, stable partition
-        // by source block with every arc placed in the position pass;
-        // padding keeps rank 0 in its block and points at the spare slot n
+        // 2-4. source ranks of every arc with the counts of its block key,
+        // destination ranks, the stable partition by source block with
+        // every arc placed in the position pass; the padding keeps rank 0 of
+        // its block and points at the spare slot n
         int32_t *srank = nullptr, *drank = nullptr, *dst = nullptr;
         G2_CK(dmalloc(&srank, (size_t)m * 4, st));
         G2_CK(dmalloc(&drank, (size_t)m * 4, st));
-        k_blk_src_ranks<<<grid_for(g, m, kCta), kCta, 0, st>>>(t->ccol, rank, m, srank);
-        k_blk_dst_ranks<<<grid_for(g, (int64_t)n * 32, kCta), kCta, 0, st>>>(t->crowptr, rank, n, drank);
-        stats().launches += 2;
         PartTable pt;
-        G2_TRY(partition_table(g, srank, S, m, nb, kBlkArcs, pstart, &total, &pt, st));
+        G2_TRY(partition_alloc(g, m, nb, &pt, st));
+        k_blk_src_count<<<pt.grid, kPartCta, pt.smem, st>>>(t->ccol, rank, S, m, nb, pt.ntiles,
+                                                             srank, pt.counts);
+        {
+            const int32_t groups = (int32_t)(((int64_t)n + 31) / 32);
+            int32_t *pieces = nullptr, *pstart_d = nullptr;
+            G2_CK(dmalloc(&pieces, ((size_t)groups + 1) * 4, st));
+            G2_CK(dmalloc(&pstart_d, ((size_t)groups + 1) * 4, st));
+            k_blk_dst_pieces<<<grid_for(g, groups, kCta), kCta, 0, st>>>(t->crowptr, n, pieces);
+            G2_TRY(exclusive_scan_i32(g, pieces, pstart_d, groups, st));
+            k_blk_dst_ranks<<<(int)std::max(1, t->sm_count * 8), kCta, 0, st>>>(
+                t->crowptr, rank, n, pstart_d, drank);
+            dfree(pieces, st);
+            dfree(pstart_d, st);
+        }
+        stats().launches += 3;
+        G2_TRY(partition_starts(g, nb, kBlkArcs, pstart, &total, &pt, st));
         G2_CK(dmalloc(&t->blk_loc, ((size_t)total + kPad) * 2, st));
         G2_CK(dmalloc(&dst, (size_t)total * 4, st));
-        G2_CK(cudaMemsetAsync(t->blk_loc, 0, ((size_t)total + kPad) * 2, st));
-        k_fill_i32_blk<<<grid_for(g, total, kCta), kCta, 0, st>>>(dst, total, n);
+        G2_CK(cudaMemsetAsync(t->blk_loc + total, 0, (size_t)kPad * 2, st));
+        k_blk_fill_pad<<<std::min(nb, 1024), kCta, 0, st>>>(pt.scan, pt.ntiles, pstart, nb, n,
+                                                             t->blk_loc, dst);
         k_blk_place<<<pt.grid, kPartCta, pt.smem, st>>>(srank, drank, S, m, nb, pt.ntiles, pt.scan,
                                                          pt.shift, t->blk_loc, dst);
         stats().launches += 2;
@@ -529,7 +669,7 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
         uint32_t *head = nullptr;
         G2_CK(dmalloc(&head, ((size_t)words + kPad) * 4, st));
         G2_CK(cudaMemsetAsync(head + words, 0, kPad * 4, st));
-        k_blk_heads<<<grid_for(g, words * 32, kCta), kCta, 0, st>>>(dst, total, head);
+        k_blk_heads<<<grid_for(g, total / 4, kCta), kCta, 0, st>>>(dst, total, head);
         k_blk_mark_starts<<<(nb + 1 + kCta - 1) / kCta, kCta, 0, st>>>(pstart, nb, total, head,
                                                                        t->blk_bchunk);
         int32_t *ccount = nullptr;
