@@ -404,65 +404,96 @@ __global__ void k_blk_cta_split(const int32_t *chunk_rank, int64_t nchunks, int3
 }
 
 // --------------------------------------------------------- vertex passes
-// x0 = 1/n (written in vertex order: the same value everywhere), the first
-// shares in rank order and D0 = (#vertices without out-arcs)/n into the slots.
+// The first shares in rank order (x0 = 1/n), D0 = (#vertices without
+// out-arcs)/n into the slots (one reduction per CTA), and x0 in the caller's
+// array where there are no rounds to write it (x: the same value everywhere).
 __global__ void __launch_bounds__(kCta) k_pr_blk_init(const int32_t *deg, int32_t n, float *share,
                                                       double *dslots, float *x, double inv_n) {
+    __shared__ float s_d[kCta / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const float x0 = (float)inv_n;
     float dangling = 0.f;
-    for (int k = 0; k < 4; ++k) {
-        const int64_t r = r0 + k;
-        if (r >= n) break;
-        const int32_t od = deg[r];
-        share[r] = od > 0 ? x0 / (float)od : 0.f;
-        if (od == 0) dangling += 1.f;
-        if (x) x[r] = x0;
+    if (r0 + 4 <= n) {
+        const int4 d4 = *reinterpret_cast<const int4 *>(deg + r0);
+        const int32_t od[4] = {d4.x, d4.y, d4.z, d4.w};
+        float sh[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sh[k] = od[k] > 0 ? x0 / (float)od[k] : 0.f;
+            dangling += od[k] == 0 ? 1.f : 0.f;
+        }
+        *reinterpret_cast<float4 *>(share + r0) = make_float4(sh[0], sh[1], sh[2], sh[3]);
+        if (x) *reinterpret_cast<float4 *>(x + r0) = make_float4(x0, x0, x0, x0);
+    } else {
+        for (int k = 0; k < 4; ++k) {
+            const int64_t r = r0 + k;
+            if (r >= n) break;
+            const int32_t od = deg[r];
+            share[r] = od > 0 ? x0 / (float)od : 0.f;
+            if (od == 0) dangling += 1.f;
+            if (x) x[r] = x0;
+        }
     }
-    // at most 128 per warp: exact in fp32; scaled by 1/n in fp64
+    // at most 1,024 per CTA: exact in fp32; scaled by 1/n in fp64
     for (int o = 16; o > 0; o >>= 1) dangling += __shfl_xor_sync(G2_FULL, dangling, o);
-    if ((threadIdx.x & 31) == 0 && dangling != 0.f) {
-        const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        atomicAdd(dslots + (gw % kDSlots) * kDStride, (double)dangling * inv_n);
+    if (lane == 0) s_d[warp] = dangling;
+    __syncthreads();
+    if (warp == 0) {
+        float v = lane < kCta / 32 ? s_d[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(G2_FULL, v, o);
+        if (lane == 0 && v != 0.f)
+            atomicAdd(dslots + (blockIdx.x % kDSlots) * kDStride, (double)v * inv_n);
     }
 }
 
 // After a sweep: x_t from y, the next shares, the next D; y back to zero.
-// Four consecutive ranks per thread with 16-byte loads and stores; the last
-// round also writes x_t to the caller's array in vertex order.
-template <bool WRITE_X>
-__global__ void __launch_bounds__(kCta, 6) k_pr_blk_vertex(const int32_t *deg, const int32_t *order,
-                                                           int32_t n, float *y, float *share_next,
-                                                           float *x, const double *dprev,
-                                                           double *dslots, float base, float damp,
-                                                           double inv_n) {
-    const int lane = threadIdx.x & 31;
-    const int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    const bool full = r0 + 4 <= n;
-    int32_t od[4] = {0, 0, 0, 0};
-    float yv[4] = {0.f, 0.f, 0.f, 0.f};
-    if (full) {
-        const int4 d4 = *reinterpret_cast<const int4 *>(deg + r0);
-        const float4 y4 = *reinterpret_cast<const float4 *>(y + r0);
-        od[0] = d4.x; od[1] = d4.y; od[2] = d4.z; od[3] = d4.w;
-        yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
-    } else if (r0 < n) {
-        for (int k = 0; k < 4; ++k)
-            if (r0 + k < n) {
-                od[k] = deg[r0 + k];
-                yv[k] = y[r0 + k];
+// A thread takes U groups of four consecutive ranks (16-byte loads and
+// stores), the groups of a CTA adjacent, all U groups' loads issued before
+// their arithmetic; the last round also writes x_t to the caller's array in
+// vertex order.  D's partial sums meet in shared memory: one fp64 reduction
+// per CTA.
+template <bool WRITE_X, int U>
+__global__ void __launch_bounds__(kCta) k_pr_blk_vertex(const int32_t *deg, const int32_t *order,
+                                                        int32_t n, float *y, float *share_next,
+                                                        float *x, const double *dprev,
+                                                        double *dslots, float base, float damp,
+                                                        double inv_n) {
+    __shared__ float s_d[kCta / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t cta0 = (int64_t)blockIdx.x * (kCta * 4 * U);
+    int32_t od[U][4];
+    float yv[U][4];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t r0 = cta0 + ((int64_t)u * kCta + threadIdx.x) * 4;
+        if (r0 + 4 <= n) {
+            const int4 d4 = *reinterpret_cast<const int4 *>(deg + r0);
+            const float4 y4 = *reinterpret_cast<const float4 *>(y + r0);
+            od[u][0] = d4.x; od[u][1] = d4.y; od[u][2] = d4.z; od[u][3] = d4.w;
+            yv[u][0] = y4.x; yv[u][1] = y4.y; yv[u][2] = y4.z; yv[u][3] = y4.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                od[u][k] = r0 + k < n ? deg[r0 + k] : 0;
+                yv[u][k] = r0 + k < n ? y[r0 + k] : 0.f;
             }
+        }
     }
     const float dterm = (float)(*dprev * inv_n);
     float dsum = 0.f;
-    if (r0 < n) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t r0 = cta0 + ((int64_t)u * kCta + threadIdx.x) * 4;
+        if (r0 >= n) continue;
+        const bool full = r0 + 4 <= n;
         float xs[4], sh[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            xs[k] = base + damp * (yv[k] + dterm);
+            xs[k] = base + damp * (yv[u][k] + dterm);
             sh[k] = 0.f;
             if (r0 + k >= n) continue;
-            if (od[k] > 0) sh[k] = xs[k] / (float)od[k];
+            if (od[u][k] > 0) sh[k] = xs[k] / (float)od[u][k];
             else dsum += xs[k];
         }
         if (full) {
@@ -488,11 +519,14 @@ __global__ void __launch_bounds__(kCta, 6) k_pr_blk_vertex(const int32_t *deg, c
             }
         }
     }
-    // D partial of the warp into one of the fp64 slots; the next sweep folds them
+    // D partial of the CTA into one of the fp64 slots; the next sweep folds them
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(G2_FULL, dsum, o);
-    if (lane == 0 && dsum != 0.f) {
-        const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        atomicAdd(dslots + (gw % kDSlots) * kDStride, (double)dsum);
+    if (lane == 0) s_d[warp] = dsum;
+    __syncthreads();
+    if (warp == 0) {
+        float v = lane < kCta / 32 ? s_d[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(G2_FULL, v, o);
+        if (lane == 0 && v != 0.f) atomicAdd(dslots + (blockIdx.x % kDSlots) * kDStride, (double)v);
     }
 }
 
@@ -738,7 +772,8 @@ g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *ran
     G2_TRY(ws(g, B_D1, 8 + R, &dd));
     G2_CK(cudaMemsetAsync(dd, 0, (8 + R) * sizeof(double), st));
     const int qblocks = (int)((((int64_t)n + 3) / 4 + kCta - 1) / kCta);
-    k_pr_blk_init<<<qblocks, kCta, 0, st>>>(t->blk_deg, n, cbuf[0], dd + 8, rank, inv_n);
+    k_pr_blk_init<<<qblocks, kCta, 0, st>>>(t->blk_deg, n, cbuf[0], dd + 8,
+                                            iters <= 0 ? rank : nullptr, inv_n);
     stats().launches += 1;
     if (iters <= 0) return G2_OK;
     const size_t smem = blk_smem_bytes(S);
@@ -749,6 +784,9 @@ g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *ran
     // without arcs: its first warp folds the dangling mass
     const int grid = t->blk_G;
     const int64_t nshare = ((int64_t)n + 3) & ~(int64_t)3;
+    constexpr int kVtxGroups = 2;  // 1: 14.9-15.1 us, 2: 13.5-13.8 us, 4: 14.7 us on RMAT-22
+    constexpr int64_t kVtxSpan = (int64_t)kCta * 4 * kVtxGroups;
+    const int vgrid = (int)(((int64_t)n + kVtxSpan - 1) / kVtxSpan);
     for (int32_t it = 0; it < iters; ++it) {
         double *dprev = dd + 2 + (it & 1);
         KTime kt;
@@ -771,14 +809,13 @@ g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *ran
         ktime_end(kt, st);
         KTime kv;
         ktime_begin(kv, "pr_vertex", st);
+        float *sn = cbuf[(it + 1) & 1];
         if (it == iters - 1)
-            k_pr_blk_vertex<true><<<qblocks, kCta, 0, st>>>(t->blk_deg, t->blk_order, n, y,
-                                                            cbuf[(it + 1) & 1], rank, dprev,
-                                                            dd + 8, base, damping, inv_n);
+            k_pr_blk_vertex<true, kVtxGroups><<<vgrid, kCta, 0, st>>>(
+                t->blk_deg, t->blk_order, n, y, sn, rank, dprev, dd + 8, base, damping, inv_n);
         else
-            k_pr_blk_vertex<false><<<qblocks, kCta, 0, st>>>(t->blk_deg, t->blk_order, n, y,
-                                                             cbuf[(it + 1) & 1], rank, dprev,
-                                                             dd + 8, base, damping, inv_n);
+            k_pr_blk_vertex<false, kVtxGroups><<<vgrid, kCta, 0, st>>>(
+                t->blk_deg, t->blk_order, n, y, sn, rank, dprev, dd + 8, base, damping, inv_n);
         ktime_end(kv, st);
         stats().launches += 2;
         stats().iterations++;
