@@ -1183,7 +1183,7 @@ def main():
                     help="requests per rate of the curve (--serve-rates)")
     ap.add_argument("--workload", choices=["rmat22", "grid", "batched", "serve", "tune", "gather", "lb"],
                     default="rmat22",
-                    help="rmat22: the default step (the JSON line the driver reads); grid and "
+                    help="rmat22: the default step (the benchmark's JSON line); grid and "
                          "batched: the road-grid and multi-source configurations")
     ap.add_argument("--grid", type=int, default=4096)
     ap.add_argument("--batch-scale", type=int, default=21)

@@ -69,7 +69,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return OUT
     tmp = OUT + f".tmp{os.getpid()}"
     # every symbol must resolve at link time (a missing definition is an error
-    # here, not at load time on the GPU machine)
+    # here, not when the library is first loaded)
     cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-Xlinker", "--no-undefined", "-o", tmp,
            *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
