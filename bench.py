@@ -275,6 +275,7 @@ def run_ours(args):
                 "bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_launch_ms * 1e3, 2),
                 "launches": pr_launches, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "vertex_pass_us": round(avg_vertex_ms * 1e3, 2),
+                "limits": (read_profile_record("pr_round") or {}).get("ncu_limits"),
                 "round": {"bytes": int(round_bytes), "us": round((avg_launch_ms + avg_vertex_ms) * 1e3, 2),
                           "achieved": round(round_achieved, 1), "frac": round(round_achieved / peak, 4)}}
 
@@ -598,9 +599,9 @@ def run_extras(g2, G22, dg22, src22, sb, sc):
     return out
 
 
-def read_traffic(kernel: str, G):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
-    was taken on the current source of that kernel (else None)."""
+def read_profile_record(kernel: str):
+    """The committed ncu record of `kernel`, if it was taken on the current
+    source of that kernel (else None)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     try:
@@ -608,13 +609,18 @@ def read_traffic(kernel: str, G):
             d = json.load(f)
         src = os.path.join(ROOT, "paper_2012_07990_gb300", "csrc", d["source"])
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if h != d["source_sha256_16"]:
-            return None
-        # traffic grows with the arcs swept: scale the captured case by m
-        per_arc = d["dram_bytes_per_launch"] / d["arcs_per_launch"]
-        return int(per_arc * G.m)
+        return d if h == d["source_sha256_16"] else None
     except Exception:
         return None
+
+
+def read_traffic(kernel: str, G):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu record, scaled
+    to the arcs of G (traffic grows with the arcs swept), else None."""
+    d = read_profile_record(kernel)
+    if d is None:
+        return None
+    return int(d["dram_bytes_per_launch"] / d["arcs_per_launch"] * G.m)
 
 
 # ---------------------------------------------------------------- oracle
