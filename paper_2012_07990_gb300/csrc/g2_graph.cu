@@ -108,23 +108,10 @@ __global__ void k_validate_rows(const int32_t *rowptr, int32_t n, int32_t m, uin
     }
 }
 
-__global__ void k_validate_cols(const int32_t *col, const int32_t *w, int32_t n, int32_t m,
-                                const uint32_t *rowstart, int32_t *bad) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int32_t v = col[e];
-        if (v < 0 || v >= n) atomicExch(bad, 4);
-        if (e + 1 < m) {
-            int64_t f = e + 1;
-            bool start = (rowstart[f >> 5] >> (f & 31)) & 1u;
-            if (!start && col[f] <= v) atomicExch(bad, 5);
-        }
-        if (w && w[e] < 0) atomicExch(bad, 6);
-    }
-}
-
 // Copy of the caller's column ids (and weights) into the graph's arrays with
-// the checks of k_validate_cols done on the way: the arcs are read once.
+// their checks done on the way (ids in [0, n), each list strictly ascending,
+// weights >= 0; the code of the failed check to *bad): the arcs are read once.
+// With dst null the kernel checks only (arcs already on the device).
 // `src`/`wsrc` are device-readable addresses: device memory, pinned host
 // memory, or pageable host memory on a device that reads it through the host
 // page tables (a coherent CPU-GPU link); the caller checks 16-byte alignment.
@@ -190,7 +177,9 @@ __global__ void __launch_bounds__(256) k_load_cols(const int32_t *__restrict__ s
                 }
                 if (wsrc && wv[u][k] < 0) code = code ? code : 6;
             }
-            if (full) {
+            if (!dst) {
+                // checks only
+            } else if (full) {
                 *reinterpret_cast<int4 *>(dst + e0) = make_int4(c[u][0], c[u][1], c[u][2], c[u][3]);
                 if (wsrc)
                     *reinterpret_cast<int4 *>(wdst + e0) =
@@ -1042,9 +1031,9 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
         else if (m > 0 && fused_copy)
             k_load_cols<1><<<t->sm_count * 8, 256, 0, st>>>(col_rd, w_rd, t->col, t->w, n,
                                                             (int32_t)m, rowstart, bad);
-        else if (m > 0)
-            k_validate_cols<<<grid_for(g, m, 256), 256, 0, st>>>(t->col, t->w, n, (int32_t)m,
-                                                                 rowstart, bad);
+        else if (m > 0)  // copied above: check the device copy, 16-byte reads
+            k_load_cols<2><<<t->sm_count * 8, 256, 0, st>>>(t->col, t->w, nullptr, nullptr, n,
+                                                            (int32_t)m, rowstart, bad);
         // into the handle's pinned counters: a copy to pageable memory would
         // block inside the driver until the upload ends, stalling the CUDA
         // calls of other host threads meanwhile
