@@ -1110,7 +1110,9 @@ def run_profile_case(args):
       the NULL schedule -- the level passes on a power-law graph;
     * batch_grid: the --grid x --grid road grid, the fused multi-source loops
       (64-source BFS, 32-source SSSP with delta 4096), the split into
-      single-source queries switched off."""
+      single-source queries switched off;
+    * pr_layout: RMAT at --scale, loaded --steps times, each load building
+      PageRank's source-blocked layout (a PageRank call with no rounds)."""
     import torch
     from paper_2012_07990_gb300 import build_native
     build_native.build()
@@ -1162,6 +1164,21 @@ def run_profile_case(args):
         print(json.dumps({"profile_case": case, "scale": args.scale, "levels": st["iterations"],
                           "launches": st["launches"]}))
         return
+    if case == "pr_layout":
+        dg.free()
+        out = torch.empty(G.n, dtype=torch.float32, device="cuda")
+        ms = []
+        for _ in range(args.steps):
+            dg = g2.load_graph(G)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2.g2_pagerank(dg, DAMPING, 0, out)
+            torch.cuda.synchronize()
+            ms.append(round((time.perf_counter() - t0) * 1e3, 3))
+            dg.free()
+        print(json.dumps({"profile_case": case, "scale": args.scale, "n": G.n, "m": G.m,
+                          "layout_ms": ms}))
+        return
     src = G.max_degree_vertex()
     out = torch.empty(G.n, dtype=torch.float32 if case == "pr" else torch.int32, device="cuda")
     for _ in range(args.steps):
@@ -1178,7 +1195,8 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["pr", "bfs", "cc", "road_fused", "bc_rmat", "batch_grid"],
+    ap.add_argument("--profile-case", choices=["pr", "bfs", "cc", "road_fused", "bc_rmat", "batch_grid",
+                                               "pr_layout"],
                     default=None)
     ap.add_argument("--serve-pool", choices=["full", "small"], default="full")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
