@@ -248,27 +248,36 @@ __global__ void k_blk_dst_ranks(const int32_t *crowptr, const int32_t *rank, int
 // The position pass of the stable partition of the arcs by source block
 // (keys srank / S), placing every arc directly: its source's rank within the
 // block and its destination's rank go to its position.  A warp's stores
-// fall into one contiguous run per block present among its 32 arcs.
+// fall into one contiguous run per block present among its 32 arcs.  Warps
+// take tiles from a counter (equal tiles, uneven costs).  Within a tile,
+// the first lane of each key's group among a step's 32 arcs claims the
+// group's positions with one shared-memory atomic that returns the key's
+// running count; eight steps' claims are issued back to back, and the warp's
+// claims to one counter are served in the order of its instructions, so the
+// tile's arcs of one key keep their order (were two steps' claims ever
+// served the other way round, a run would only split in two: positions stay
+// disjoint and every one is filled).
 __global__ void __launch_bounds__(kPartCta) k_blk_place(const int32_t *srank, const int32_t *drank,
                                                         int32_t S, int64_t count, int32_t nkeys,
                                                         int32_t ntiles, const int32_t *scan,
-                                                        const int32_t *shift, uint16_t *loc,
-                                                        int32_t *dst) {
+                                                        const int32_t *shift, int32_t *tile_ctr,
+                                                        uint16_t *loc, int32_t *dst) {
     extern __shared__ int32_t s_part[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     int32_t *c = s_part + wid * nkeys;
-    const int32_t wpc = kPartCta / 32;
-    for (int32_t tile = blockIdx.x * wpc + wid; tile < ntiles; tile += gridDim.x * wpc) {
+    const float inv = 1.0f / (float)S;
+    for (;;) {
+        int32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(tile_ctr, 1);
+        tile = __shfl_sync(G2_FULL, tile, 0);
+        if (tile >= ntiles) break;
         for (int k = lane; k < nkeys; k += 32) c[k] = scan[(int64_t)k * ntiles + tile] + shift[k];
         __syncwarp();
         const int64_t base = (int64_t)tile * kPartTile;
-        const float inv = 1.0f / (float)S;
-        // eight steps' ranks are loaded at once, so the placement's chain
-        // (match, counter, store) does not wait on a load every step
         constexpr int kB = 8;
         for (int s0 = 0; s0 < kPartTile / 32; s0 += kB) {
-            int32_t sr[kB], dr[kB];
+            int32_t sr[kB], dr[kB], got[kB], who[kB];
 #pragma unroll
             for (int j = 0; j < kB; ++j) {
                 const int64_t i = base + (s0 + j) * 32 + lane;
@@ -279,17 +288,22 @@ __global__ void __launch_bounds__(kPartCta) k_blk_place(const int32_t *srank, co
             for (int j = 0; j < kB; ++j) {
                 const int key = sr[j] >= 0 ? div_floor(sr[j], S, inv) : -1;
                 const unsigned peers = __match_any_sync(G2_FULL, key);
-                const int r = __popc(peers & lt);
-                if (key >= 0) {
-                    const int32_t p = c[key] + r;
+                const int lead = __ffs(peers) - 1;
+                got[j] = 0;
+                if (key >= 0 && lane == lead) got[j] = atomicAdd(&c[key], __popc(peers));
+                who[j] = (lead << 8) | __popc(peers & lt);
+            }
+#pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                const int32_t p = __shfl_sync(G2_FULL, got[j], who[j] >> 8) + (who[j] & 0xFF);
+                if (sr[j] >= 0) {
+                    const int key = div_floor(sr[j], S, inv);
                     loc[p] = (uint16_t)(sr[j] - key * S);
                     dst[p] = dr[j];
                 }
-                __syncwarp();
-                if (key >= 0 && r == 0) c[key] += __popc(peers);
-                __syncwarp();
             }
         }
+        __syncwarp();  // the tile's claims are done before the counters are reset
     }
 }
 
@@ -692,8 +706,12 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
         G2_CK(cudaMemsetAsync(t->blk_loc + total, 0, (size_t)kPad * 2, st));
         k_blk_fill_pad<<<std::min(nb, 1024), kCta, 0, st>>>(pt.scan, pt.ntiles, pstart, nb, n,
                                                              t->blk_loc, dst);
+        int32_t *tile_ctr = nullptr;
+        G2_TRY(ws(g, B_CTR, 64, &tile_ctr));
+        tile_ctr += 52;
+        G2_CK(cudaMemsetAsync(tile_ctr, 0, 4, st));
         k_blk_place<<<pt.grid, kPartCta, pt.smem, st>>>(srank, drank, S, m, nb, pt.ntiles, pt.scan,
-                                                         pt.shift, t->blk_loc, dst);
+                                                         pt.shift, tile_ctr, t->blk_loc, dst);
         stats().launches += 2;
         G2_CK(cudaGetLastError());
         pt.release(st);
