@@ -327,59 +327,53 @@ static __global__ void k_fill_i32_blk(int32_t *p, int64_t count, int32_t v) {
         p[i] = v;
 }
 
-// head bit of position p: its destination differs from position p-1's
-// (block starts are marked by k_blk_mark_starts).  A warp takes 128
-// positions a step, four per lane in one 16-byte load; a lane's four flags
-// form a nibble and eight lanes' nibbles a head word.  total is a multiple
-// of kBlkArcs.
-__global__ void k_blk_heads(const int32_t *dst, int64_t total, uint32_t *head) {
-    const int64_t steps = total / 128;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    for (int64_t q = gw; q < steps; q += nw) {
-        const int64_t p = q * 128 + lane * 4;
-        const int4 d = *reinterpret_cast<const int4 *>(dst + p);
-        int32_t prev = __shfl_up_sync(G2_FULL, d.w, 1);
-        if (lane == 0) prev = p > 0 ? dst[p - 1] : -1;
-        const uint32_t nib = (uint32_t)(d.x != prev) | ((uint32_t)(d.y != d.x) << 1) |
-                             ((uint32_t)(d.z != d.y) << 2) | ((uint32_t)(d.w != d.z) << 3);
-        uint32_t word = nib << (4 * (lane & 7));
-        word |= __shfl_xor_sync(G2_FULL, word, 1);
-        word |= __shfl_xor_sync(G2_FULL, word, 2);
-        word |= __shfl_xor_sync(G2_FULL, word, 4);
-        if ((lane & 7) == 0) head[q * 4 + (lane >> 3)] = word;
-    }
-}
-
-__global__ void k_blk_mark_starts(const int32_t *pstart, int32_t nb, int64_t total, uint32_t *head,
-                                  int32_t *bchunk) {
+// First chunk of every block (blocks start on chunk boundaries) and a flag
+// per chunk that starts a block with arcs.
+__global__ void k_blk_mark_starts(const int32_t *pstart, int32_t nb, int64_t total,
+                                  uint8_t *chunk_start, int32_t *bchunk) {
     for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += gridDim.x * blockDim.x) {
         const int32_t p = pstart[b];
         bchunk[b] = p / kBlkArcs;
-        if (b < nb && p < total && pstart[b + 1] > p) atomicOr(head + (p >> 5), 1u << (p & 31));
+        if (b < nb && p < total && pstart[b + 1] > p) chunk_start[p / kBlkArcs] = 1;
     }
 }
 
-__global__ void k_blk_chunk_heads(const uint32_t *head, int64_t nchunks, int32_t *cnt) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int s = 0;
-        for (int j = 0; j < kBlkHeadWords; ++j) s += __popc(head[c * kBlkHeadWords + j]);
-        cnt[c] = s;
-    }
-}
-
-// per lane of every chunk: its 8 head flags and the heads before it in the
-// chunk, (prefix << 8) | flags
-__global__ void k_blk_lane_heads(const uint32_t *head, int64_t lanes, uint16_t *out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lanes;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t w = i >> 2, w0 = (i >> 5) * kBlkHeadWords;
-        const int sh = (int)(i & 3) * 8;
-        int prefix = __popc(head[w] & ((1u << sh) - 1u));
-        for (int64_t j = w0; j < w; ++j) prefix += __popc(head[j]);
-        out[i] = (uint16_t)((prefix << 8) | ((head[w] >> sh) & 0xFFu));
+// The head flags of a chunk and what the sweep reads of them, a warp per
+// chunk: lane l holds arcs 8l .. 8l + 7 (two 16-byte loads of destinations);
+// arc k is a head where its destination differs from the arc before it, or
+// where it starts a block.  Out: the chunk's 8 head words (bit j of word w:
+// arc 32w + j), per lane (heads before the lane in the chunk << 8) | its 8
+// flags, and the chunk's head count.
+__global__ void k_blk_heads(const int32_t *dst, int64_t nchunks, const uint8_t *chunk_start,
+                            uint32_t *head, uint16_t *lane_heads, int32_t *ccount) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int64_t c = gw; c < nchunks; c += nw) {
+        const int64_t p = c * kBlkArcs + lane * 8;
+        const int4 d0 = *reinterpret_cast<const int4 *>(dst + p);
+        const int4 d1 = *reinterpret_cast<const int4 *>(dst + p + 4);
+        int32_t prev = __shfl_up_sync(G2_FULL, d1.w, 1);
+        if (lane == 0) prev = (p > 0 && !chunk_start[c]) ? dst[p - 1] : -1;
+        const int32_t d[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+        uint32_t hf = (uint32_t)(d[0] != prev);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) hf |= (uint32_t)(d[k] != d[k - 1]) << k;
+        // heads before this lane: exclusive scan of the lanes' counts
+        const int cnt = __popc(hf);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(G2_FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        lane_heads[c * 32 + lane] = (uint16_t)(((incl - cnt) << 8) | hf);
+        // head word w = the flags of lanes 4w .. 4w + 3
+        uint32_t word = hf << (8 * (lane & 3));
+        word |= __shfl_xor_sync(G2_FULL, word, 1);
+        word |= __shfl_xor_sync(G2_FULL, word, 2);
+        if ((lane & 3) == 0) head[c * kBlkHeadWords + (lane >> 2)] = word;
+        if (lane == 31) ccount[c] = incl;
     }
 }
 
@@ -719,15 +713,20 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
         dfree(drank, st);
         const int64_t words = total / 32, nchunks = total / kBlkArcs;
         uint32_t *head = nullptr;
+        uint8_t *cstart = nullptr;
+        int32_t *ccount = nullptr;
         G2_CK(dmalloc(&head, ((size_t)words + kPad) * 4, st));
         G2_CK(cudaMemsetAsync(head + words, 0, kPad * 4, st));
-        k_blk_heads<<<grid_for(g, total / 4, kCta), kCta, 0, st>>>(dst, total, head);
-        k_blk_mark_starts<<<(nb + 1 + kCta - 1) / kCta, kCta, 0, st>>>(pstart, nb, total, head,
-                                                                       t->blk_bchunk);
-        int32_t *ccount = nullptr;
+        G2_CK(dmalloc(&cstart, (size_t)nchunks + 16, st));
+        G2_CK(cudaMemsetAsync(cstart, 0, (size_t)nchunks + 16, st));
         G2_CK(dmalloc(&ccount, (size_t)nchunks * 4, st));
         G2_CK(dmalloc(&t->blk_chunk_rank, ((size_t)nchunks + kPad) * 4, st));
-        k_blk_chunk_heads<<<grid_for(g, nchunks, kCta), kCta, 0, st>>>(head, nchunks, ccount);
+        const int64_t lanes = nchunks * 32;
+        G2_CK(dmalloc(&t->blk_lane_heads, ((size_t)lanes + kPad) * 2, st));
+        k_blk_mark_starts<<<(nb + 1 + kCta - 1) / kCta, kCta, 0, st>>>(pstart, nb, total, cstart,
+                                                                       t->blk_bchunk);
+        k_blk_heads<<<grid_for(g, lanes, kCta), kCta, 0, st>>>(dst, nchunks, cstart, head,
+                                                               t->blk_lane_heads, ccount);
         G2_TRY(exclusive_scan_i32(g, ccount, t->blk_chunk_rank, (int32_t)nchunks, st));
         G2_CK(cudaMemcpyAsync(g->h_ctr + 51, t->blk_chunk_rank + nchunks, 4, cudaMemcpyDeviceToHost,
                               st));
@@ -740,15 +739,13 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
         k_fill_i32_blk<<<1, kPad, 0, st>>>(t->blk_nzrow + (size_t)nruns + 1, kPad, n);
         k_blk_nzrow<<<grid_for(g, words, kCta), kCta, 0, st>>>(head, t->blk_chunk_rank, dst, words,
                                                                t->blk_nzrow);
-        const int64_t lanes = nchunks * 32;
-        G2_CK(dmalloc(&t->blk_lane_heads, ((size_t)lanes + kPad) * 2, st));
-        k_blk_lane_heads<<<grid_for(g, lanes, kCta), kCta, 0, st>>>(head, lanes, t->blk_lane_heads);
         int32_t runcost = kBlkRunCost;
         if (const char *e = getenv("G2_PR_BLK_RUNCOST")) runcost = std::max(0, atoi(e));
         k_blk_cta_split<<<(G + 1 + kCta - 1) / kCta, kCta, 0, st>>>(t->blk_chunk_rank, nchunks, G,
                                                                     runcost, t->blk_cta);
-        stats().launches += 11;
+        stats().launches += 9;
         dfree(ccount, st);
+        dfree(cstart, st);
         dfree(dst, st);
         dfree(head, st);
         t->blk_nruns = nruns;

@@ -904,6 +904,10 @@ def test_load_paths_and_memory_reuse(g2, rmat14):
     check(g2.g2_load_csr(g.n, as_np(prp), as_np(pcl), as_np(pw), True))
     # the same through the copy engines (a load that overlaps other work)
     check(g2.g2_load_csr(g.n, as_np(prp), as_np(pcl), as_np(pw), True, overlap=True))
+    # an overlapping load of pageable arrays: the copy kernel on a quarter of
+    # the SMs (16-byte aligned numpy arrays)
+    assert g.col.ctypes.data % 16 == 0 and w.ctypes.data % 16 == 0
+    check(g2.g2_load_csr(g.n, g.rowptr, g.col, w, True, overlap=True))
     # 4-byte misaligned host views of the same data
     buf = np.empty(g.m + 1, np.int32)
     col_mis = buf[1:]
@@ -919,7 +923,8 @@ def test_load_paths_and_memory_reuse(g2, rmat14):
     # invalid input on the pinned and misaligned paths
     bad = g.col.copy()
     bad[g.m // 2 + 3] = g.n  # id out of range
-    for c in (as_np(torch.from_numpy(bad).pin_memory()), np.concatenate([np.zeros(1, np.int32), bad])[1:]):
+    for c in (as_np(torch.from_numpy(bad).pin_memory()), np.concatenate([np.zeros(1, np.int32), bad])[1:],
+              bad):
         for ov in (False, True):
             with pytest.raises(g2.G2Error) as e:
                 g2.g2_load_csr(g.n, g.rowptr, c, None, True, overlap=ov)
