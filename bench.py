@@ -181,9 +181,13 @@ def run_ours(args):
     # worker threads, each on a graph view (own workspace) and a stream of its
     # own, while PageRank runs on this thread's stream; their per-round host
     # round trips then overlap PageRank's sweeps instead of idling the GPU.
+    # PageRank's stream has the higher priority: the block scheduler starts
+    # its CTAs first, and BFS's and CC's fill the gaps between its kernels
+    # instead of holding SMs its whole-SM sweep CTAs wait for.
     from concurrent.futures import ThreadPoolExecutor
     views = {"bfs": g2.g2_graph_view(dg), "cc": g2.g2_graph_view(dg)}
     streams = {"bfs": torch.cuda.Stream(), "cc": torch.cuda.Stream()}
+    pr_stream = torch.cuda.Stream(priority=-5)  # the highest priority the device has
     pool = ThreadPoolExecutor(2)
 
     def bfs_job():
@@ -197,7 +201,7 @@ def run_ours(args):
     def step(t_algo=None):
         if t_algo is None:
             fb, fc = pool.submit(bfs_job), pool.submit(cc_job)
-            g2.g2_pagerank(dg, DAMPING, PR_ITERS, rank_t)
+            g2.g2_pagerank(dg, DAMPING, PR_ITERS, rank_t, stream=pr_stream)
             launches["n"] += g2.g2_last_stats()["launches"] + fb.result() + fc.result()
             return
         # the per-algorithm split: the three one after another on this stream
@@ -357,6 +361,9 @@ def run_e2e(args, g2, G, src, sb, sc, edges_per_step):
     depth = torch.empty(n, dtype=torch.int32, device="cuda")
     label = torch.empty(n, dtype=torch.int32, device="cuda")
     rank_t = torch.empty(n, dtype=torch.float32, device="cuda")
+    # all at the default priority: with PageRank's stream above the loader's
+    # the next graph's layout build starved and the pipeline slowed down
+    # (5.9-7.4 ms per step against 5.9-6.0)
     main = torch.cuda.current_stream()
     load_stream = torch.cuda.Stream()
     s_bfs, s_cc = torch.cuda.Stream(), torch.cuda.Stream()
