@@ -144,8 +144,9 @@ typedef struct g2_graph g2_graph;
  * comes from the library's stream-ordered pool (see g2_free_graph).
  * G2_PREPARE_PAGERANK: the layouts the tuned PageRank sweep needs (the
  * source-blocked arcs and the rank order of the vertices) are built
- * after the load returns, by a host thread on a stream of its own, while the
- * caller's next calls run; g2_pagerank (and g2_free_graph) wait for them.
+ * after the load returns, by a host thread on a stream of its own (with the
+ * priority of the load's stream), while the caller's next calls run;
+ * g2_pagerank (and g2_free_graph) wait for them.
  * Without the flag the first g2_pagerank builds them. */
 g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *col,
                       const int32_t *w, uint32_t flags, void *stream, g2_graph **out);

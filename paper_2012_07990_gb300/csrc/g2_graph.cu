@@ -820,7 +820,7 @@ static void handle_release(g2_graph *g) {
     delete g;
 }
 
-g2_status pr_prepare_start(g2_graph *g) {
+g2_status pr_prepare_start(g2_graph *g, cudaStream_t load_stream) {
     Topology *t = g->topo;
     std::lock_guard<std::mutex> lk(t->prep_mu);
     if (t->prep.joinable()) return G2_OK;
@@ -829,8 +829,14 @@ g2_status pr_prepare_start(g2_graph *g) {
         handle_release(h);
         return G2_ENOMEM;
     }
+    // the preparation runs at the priority of the load's stream
+    int prio = 0;
+    if (cudaStreamGetPriority(load_stream, &prio) != cudaSuccess) {
+        cudaGetLastError();
+        prio = 0;
+    }
     cudaStream_t s2 = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, prio);
     if (e != cudaSuccess) {
         handle_release(h);
         return cuda_fail(e, "stream for the background preparation");
@@ -1080,7 +1086,7 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(e, "CSC upload"));
     }
     if (flags & G2_PREPARE_PAGERANK) {
-        const g2_status ps = pr_prepare_start(g);
+        const g2_status ps = pr_prepare_start(g, st);
         if (ps != G2_OK) return bail(ps);
     }
     *out = g;

@@ -236,7 +236,7 @@ g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *ran
                            cudaStream_t st);
 // Start the background preparation for g's topology / wait for it (joins the
 // thread, releases its handle and stream; returns its status).
-g2_status pr_prepare_start(g2_graph *g);
+g2_status pr_prepare_start(g2_graph *g, cudaStream_t load_stream);
 g2_status pr_prepare_wait(Topology *t);
 
 // Largest out-degree of the graph (computed on the device once, then kept).
