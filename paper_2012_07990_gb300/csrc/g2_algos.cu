@@ -16,6 +16,8 @@ namespace g2 {
 
 g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                     const g2_schedule &s, cudaStream_t st, int32_t *d_err);
+g2_status bfs_fused_do(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
+                       const g2_hybrid &h, cudaStream_t st, int32_t *d_err);
 g2_status sssp_fused(g2_graph *g, int32_t src, int32_t delta, int32_t *dist,
                      const g2_schedule &s, cudaStream_t st, int32_t *d_err);
 
@@ -540,22 +542,25 @@ static bool bounded_degree(g2_graph *g, cudaStream_t st) {
 }
 
 // Tuned schedule for BFS when the caller passes none (measured on GB300 with
-// RMAT-22): direction-optimising hybrid, STRICT PUSH on a sparse queue while
-// the frontier holds < 2% of the vertices, else VERTEX_BASED PULL over a
-// bitmap input with an unfused bitmap output and no deduplication.  On a
-// bounded-degree graph: fused WM PUSH (measured on a 1024^2 road grid: 7.2 ms
-// against 35 ms for the hybrid).
+// RMAT-21/22): the direction-optimising hybrid fused into one launch, ETWC
+// PUSH (large entries handed to a grid-wide pass) while the frontier holds
+// < 2% of the vertices, else VERTEX_BASED PULL over a bitmap (0.22-0.24 ms
+// on RMAT-22 against 0.33 ms for the same hybrid as per-level launches with
+// STRICT PUSH).  On a bounded-degree graph: fused WM PUSH (measured on a
+// 1024^2 road grid: 7.2 ms against 35 ms for the hybrid).
 static g2_hybrid tuned_bfs_hybrid(g2_graph *g, cudaStream_t st) {
     if (bounded_degree(g, st)) return fused_wm_hybrid();
     g2_hybrid h = default_hybrid();
     h.criteria = G2_INPUT_VERTEXSET_SIZE;
     h.threshold = 0.02f;
-    h.s1.load_balance = G2_LB_STRICT;
+    h.s1.load_balance = G2_LB_ETWC;
+    h.s1.kernel_fusion = 1;
     h.s2.load_balance = G2_LB_VERTEX_BASED;
     h.s2.direction = G2_PULL;
     h.s2.pull_frontier = G2_BITMAP;
     h.s2.frontier_creation = G2_UNFUSED_BITMAP;
     h.s2.dedup = G2_DEDUP_DISABLED;
+    h.s2.kernel_fusion = 1;
     return h;
 }
 
@@ -582,7 +587,10 @@ g2_status g2_bfs(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent, cons
     if (h.s1.kernel_fusion) {
         if (h.criteria != G2_CRITERIA_NONE && !h.s2.kernel_fusion)
             return fail(G2_EUNSUPPORTED, "kernel fusion must be set on both hybrid schedules");
-        G2_TRY(bfs_fused(g, src, depth, parent, h.s1, st, d_err));
+        if (h.criteria != G2_CRITERIA_NONE && h.s2.direction == G2_PULL)
+            G2_TRY(bfs_fused_do(g, src, depth, parent, h, st, d_err));
+        else
+            G2_TRY(bfs_fused(g, src, depth, parent, h.s1, st, d_err));
     } else {
         G2_TRY(bfs_plain(g, src, depth, parent, h, st, d_err));
     }

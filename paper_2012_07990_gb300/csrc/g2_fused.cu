@@ -79,6 +79,167 @@ __global__ void __launch_bounds__(kCta) k_bfs_fused(FusedBfsArgs a) {
     }
 }
 
+// ------------------------------------------------- fused direction-optimising BFS
+// The hybrid of Table III inside one launch (kernel fusion, Sec. VI-C, over a
+// direction-optimising schedule): a level below `push_below` vertices runs
+// PUSH with load balancing LB from a sparse list, a larger one runs PULL
+// (VERTEX_BASED, a thread per vertex scanning its ascending in-list until the
+// first in-frontier neighbour, the canonical parent) over a bitmap of the
+// frontier.  A PUSH level's output is a list, a PULL level's a bitmap (each
+// word stored by the one warp that owns its 32 vertices, so it needs no
+// clearing) with its population; the representation is converted where the
+// direction changes.  Rotating counters as in k_bfs_fused: at the start of
+// level d, cnt[(d+1)%3] and bcnt[(d+1)%3] are zero and cnt[(d+2)%3],
+// bcnt[(d+2)%3] are cleared for level d+1.  Every CTA reads the same counts
+// after a barrier, so all take the same branches.
+struct FusedDoBfsArgs {
+    DevGraph g;
+    int32_t *depth;
+    int32_t *parent;
+    int32_t *q[2];
+    int32_t *cnt;        // [3] list lengths; cnt[0] = 1 (the source) at launch, the rest 0
+    uint32_t *bm[2];     // frontier bitmaps, (n + 31) / 32 words each
+    int32_t *bcnt;       // [3] bitmap populations, 0 at launch
+    int32_t push_below;  // PUSH while the frontier holds fewer vertices
+    EtwcEntry<int32_t> *spq;  // ETWC: a level's entries of kEtwcSpill arcs or more ...
+    int32_t *spcnt;           // ... and their counts per level parity, 0 at launch
+    int32_t *result;     // [0] levels, [1] PULL levels
+    GridBarrier bar;
+    int32_t *err;
+    uint64_t limit_ns;
+    unsigned long long *ctr;
+};
+
+template <int LB>
+__global__ void __launch_bounds__(kCta) k_bfs_fused_do(FusedDoBfsArgs a) {
+    OpBFS op{a.depth, a.parent};
+    PullBFS pop{a.depth, a.parent};
+    const int lane = threadIdx.x & 31;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gwarp = gt >> 5, nwarps = nt >> 5;
+    const int32_t n = a.g.n;
+    const int32_t words = (n + 31) / 32;
+    OutCtx out;
+    memset(&out, 0, sizeof(out));
+    out.mode = OUT_SPARSE;
+    out.dedup = DD_NONE;  // the compare-and-swap on depth admits each vertex once
+    out.cap = n;
+    out.err = a.err;
+    bool sparse = true;  // level d's frontier is a list (else a bitmap)
+    int d = 0, pulls = 0;
+    for (;; ++d) {
+        int32_t size = sparse ? ld_relaxed_i32(a.cnt + d % 3) : ld_relaxed_i32(a.bcnt + d % 3);
+        if (size == 0) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.cnt[(d + 2) % 3] = 0;
+            a.bcnt[(d + 2) % 3] = 0;
+            if (a.spcnt) a.spcnt[(d + 1) & 1] = 0;
+        }
+        if (size < a.push_below) {
+            if (!sparse) {
+                // bitmap -> list d & 1 (cnt[d % 3] is zero: cleared two levels ago)
+                const uint32_t *bm = a.bm[d & 1];
+                for (int64_t base = gwarp * 32; base < words; base += nwarps * 32) {
+                    const int64_t w = base + lane;
+                    const uint32_t bits = w < words ? bm[w] : 0u;
+                    const int c = __popc(bits);
+                    int incl = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(G2_FULL, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    const int tot = __shfl_sync(G2_FULL, incl, 31);
+                    int32_t pos = 0;
+                    if (lane == 31 && tot) pos = atomicAdd(a.cnt + d % 3, tot);
+                    pos = __shfl_sync(G2_FULL, pos, 31) + incl - c;
+                    uint32_t b = bits;
+                    while (b) {
+                        const int j = __ffs(b) - 1;
+                        b &= b - 1;
+                        if (pos < n) a.q[d & 1][pos] = (int32_t)(w * 32 + j);
+                        ++pos;
+                    }
+                }
+                if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+                size = ld_relaxed_i32(a.cnt + d % 3);
+                sparse = true;
+            }
+            FrontierIn fin{a.q[d & 1], size, nullptr};
+            out.q = a.q[(d + 1) & 1];
+            out.cnt = a.cnt + (d + 1) % 3;
+            if (LB == G2_LB_ETWC && a.spcnt) {
+                // Algorithm 3 with the CTA-stage entries of kEtwcSpill arcs or
+                // more handed to a grid-wide pass after the barrier (a hub
+                // would otherwise keep one CTA busy while the rest wait)
+                int32_t *spc = a.spcnt + (d & 1);
+                lb_etwc(a.g, fin, size, op, out, blockIdx.x, gridDim.x, a.ctr,
+                        EtwcSpill<int32_t>{a.spq, spc});
+                if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+                if (ld_relaxed_i32(spc) > 0) {
+                    lb_etwc_spill(a.g, a.spq, spc, op, out, blockIdx.x, gridDim.x);
+                    if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+                }
+            } else {
+                run_lb<LB>(a.g, fin, size, op, out, a.ctr);
+                if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+            }
+        } else {
+            uint32_t *cur = a.bm[d & 1];
+            if (sparse) {
+                // list d & 1 -> bitmap: clear it, then set the list's bits
+                for (int64_t w = gt; w < words; w += nt) cur[w] = 0u;
+                if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+                const int32_t *q = a.q[d & 1];
+                for (int64_t i = gt; i < size; i += nt) {
+                    const int32_t v = q[i];
+                    atomicOr(&cur[v >> 5], 1u << (v & 31));
+                }
+                if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+            }
+            // bottom-up over every vertex; the next level as a bitmap
+            Member mem{MEM_BITMAP, cur, nullptr};
+            uint32_t *next = a.bm[(d + 1) & 1];
+            int32_t found = 0;
+            for (int64_t base = gwarp * 32; base < n; base += nwarps * 32) {
+                const int64_t v = base + lane;
+                int code = 0, scanned = 0;
+                if (v < n) {
+                    const int32_t c = pop.ctx((int32_t)v);
+                    if (pop.filter(c)) {
+                        int32_t acc = pop.identity();
+                        const int32_t e1 = a.g.crowptr[v + 1];
+                        for (int32_t e = a.g.crowptr[v]; e < e1; ++e) {
+                            const int32_t u = a.g.ccol[e];
+                            ++scanned;
+                            if (mem.has(u)) {
+                                acc = u;  // ascending in-list: the first hit is the smallest
+                                break;
+                            }
+                        }
+                        code = pop.finish((int32_t)v, c, acc);
+                    }
+                }
+                count_arcs(a.ctr, scanned);
+                const unsigned mask = __ballot_sync(G2_FULL, code & 1);
+                if (lane == 0) {
+                    next[base >> 5] = mask;
+                    found += __popc(mask);
+                }
+            }
+            if (lane == 0 && found) atomicAdd(a.bcnt + (d + 1) % 3, found);
+            if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
+            sparse = false;
+            ++pulls;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.result[0] = d;
+        a.result[1] = pulls;
+    }
+}
+
 struct FusedSsspArgs {
     DevGraph g;
     int32_t *dist;
@@ -775,6 +936,71 @@ g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     stats().iterations = level;
     stats().push_rounds = level;
     stats().barriers = level;
+    return G2_OK;
+}
+
+// The direction-optimising hybrid in one launch (k_bfs_fused_do): h.s1 is the
+// PUSH schedule (a load balancing of the fused loops), h.s2 VERTEX_BASED
+// PULL over a bitmap; PUSH while the frontier holds fewer than threshold * n
+// vertices.
+g2_status bfs_fused_do(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
+                       const g2_hybrid &h, cudaStream_t st, int32_t *d_err) {
+    G2_TRY(check_fused_lb(h.s1));
+    if (h.criteria != G2_INPUT_VERTEXSET_SIZE)
+        return fail(G2_EUNSUPPORTED, "a fused hybrid switches on the input vertexset size");
+    if (h.s2.direction != G2_PULL || h.s2.load_balance != G2_LB_VERTEX_BASED ||
+        h.s2.pull_frontier != G2_BITMAP)
+        return fail(G2_EUNSUPPORTED, "the fused hybrid's PULL schedule is VERTEX_BASED over a bitmap");
+    Topology *t = g->topo;
+    const int32_t n = t->n;
+    int32_t *ctrs = d_err - 62;
+    FusedDoBfsArgs a;
+    a.g = t->view();
+    a.depth = depth;
+    a.parent = parent;
+    G2_TRY(ws(g, B_Q0, (size_t)std::max(n, 1), &a.q[0]));
+    G2_TRY(ws(g, B_Q1, (size_t)std::max(n, 1), &a.q[1]));
+    const size_t words = ((size_t)n + 31) / 32 + 1;
+    G2_TRY(ws(g, B_BM0, words, &a.bm[0]));
+    G2_TRY(ws(g, B_BM1, words, &a.bm[1]));
+    a.cnt = ctrs + 20;
+    a.bcnt = ctrs + 46;  // [46..48]
+    a.spq = nullptr;
+    a.spcnt = nullptr;
+    if (h.s1.load_balance == G2_LB_ETWC) {
+        // every handed-off entry has at least kEtwcSpill arcs
+        const size_t cap = (size_t)t->m / kEtwcSpill + 1;
+        G2_TRY(ws(g, B_TWC_L, cap, &a.spq));
+        a.spcnt = ctrs + 54;  // [54..55]
+    }
+    const double pb = (double)h.threshold * (double)n;
+    a.push_below = (int32_t)std::min<double>(std::max<double>(pb, 0.0), 2147483647.0);
+    a.result = ctrs + 24;
+    a.bar = GridBarrier{reinterpret_cast<unsigned long long *>(ctrs + 28)};
+    a.err = d_err;
+    a.limit_ns = barrier_limit_ns();
+    a.ctr = nullptr;
+    if (count_arcs_enabled()) G2_TRY(ws(g, B_ARCS, 2, &a.ctr));
+    if (parent) G2_CK(cudaMemsetAsync(parent, 0xFF, (size_t)n * 4, st));
+    G2_CK(cudaMemsetAsync(depth, 0xFF, (size_t)n * 4, st));
+    int32_t zero = 0, one = 1;
+    G2_TRY(put_i32(st, {{depth + src, zero}, {parent ? parent + src : nullptr, src}, {a.q[0], src},
+                        {a.cnt, one}, {a.cnt + 1, zero}, {a.cnt + 2, zero}}));
+    G2_TRY(put_i32(st, {{a.bcnt, zero}, {a.bcnt + 1, zero}, {a.bcnt + 2, zero},
+                        {a.spcnt, zero}, {a.spcnt ? a.spcnt + 1 : nullptr, zero}}));
+    // the PULL levels sweep every vertex: four CTAs per SM (measured on
+    // RMAT-21/22: 0.17-0.24 ms against 0.29-0.53 ms with one)
+    const int want = env_i32("G2_FUSED_DO_CTAS_PER_SM", 4);
+    switch (h.s1.load_balance) {
+        case G2_LB_WM: G2_TRY(launch_coop(g, k_bfs_fused_do<G2_LB_WM>, a, st, want)); break;
+        case G2_LB_CM: G2_TRY(launch_coop(g, k_bfs_fused_do<G2_LB_CM>, a, st, want)); break;
+        case G2_LB_ETWC: G2_TRY(launch_coop(g, k_bfs_fused_do<G2_LB_ETWC>, a, st, want)); break;
+        default: G2_TRY(launch_coop(g, k_bfs_fused_do<G2_LB_VERTEX_BASED>, a, st, want)); break;
+    }
+    G2_TRY(read_counters(g, ctrs + 24, 2, st, d_err));
+    stats().iterations = g->h_ctr[0];
+    stats().pull_rounds = g->h_ctr[1];
+    stats().push_rounds = g->h_ctr[0] - g->h_ctr[1];
     return G2_OK;
 }
 

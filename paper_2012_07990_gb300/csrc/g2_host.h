@@ -262,19 +262,21 @@ inline uint64_t barrier_limit_ns() {
 // Cooperative launch of a fused kernel taking one argument struct: resident
 // CTAs only (co-residency is what makes its grid barriers safe).
 template <class K, class A>
-inline g2_status launch_coop(g2_graph *g, K kernel, A &args, cudaStream_t st) {
+inline g2_status launch_coop(g2_graph *g, K kernel, A &args, cudaStream_t st, int want = 0) {
     int per_sm = 0;
     G2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCta, 0));
     if (per_sm < 1) return fail(G2_EUNSUPPORTED, "fused kernel does not fit on an SM");
     // fewer resident CTAs make every grid barrier cheaper; the round's work
     // is spread over the virtual CTAs either way.  One CTA per SM measured
-    // best on road grids (G2_FUSED_CTAS_PER_SM overrides for sweeps).
+    // best on road grids (G2_FUSED_CTAS_PER_SM overrides for sweeps); a
+    // caller whose rounds sweep every vertex asks for more (`want`).
     static int cap = -1;
     if (cap < 0) {
         const char *e = getenv("G2_FUSED_CTAS_PER_SM");
         cap = e ? atoi(e) : 1;
     }
-    if (cap > 0 && cap < per_sm) per_sm = cap;
+    const int use = want > 0 ? want : cap;
+    if (use > 0 && use < per_sm) per_sm = use;
     int grid = per_sm * g->topo->sm_count;
     void *params[] = {&args};
     G2_CK(cudaLaunchCooperativeKernel((const void *)kernel, dim3(grid), dim3(kCta), params, 0, st));

@@ -337,12 +337,22 @@ __device__ void lb_etwc_spill(const DevGraph &g, const EtwcEntry<typename Op::S>
                               const int32_t *cnt, const Op &op, const OutCtx &out, int bid,
                               int nb) {
     const int32_t k = *cnt;
+    const int lane = threadIdx.x & 31;
     for (int32_t j = 0; j < k; ++j) {
         const EtwcEntry<typename Op::S> en = q[j];
-        for (int64_t e = en.beg + (int64_t)bid * kCta + threadIdx.x; e < en.end;
-             e += (int64_t)nb * kCta) {
-            const int32_t v = g.col[e];
-            emit(out, v, op.relax(en.u, en.s, v, (int32_t)e));
+        // a warp takes 32 consecutive arcs a step, lanes past the entry's end
+        // emit nothing, so every lane reaches the warp-wide append (entries
+        // are whole multiples of kCta arcs, but the loop does not rely on it)
+        for (int64_t base = en.beg + (int64_t)bid * kCta + (threadIdx.x & ~31); base < en.end;
+             base += (int64_t)nb * kCta) {
+            const int64_t e = base + lane;
+            int32_t v = 0;
+            int code = 0;
+            if (e < en.end) {
+                v = g.col[e];
+                code = op.relax(en.u, en.s, v, (int32_t)e);
+            }
+            emit(out, v, code);
         }
     }
 }

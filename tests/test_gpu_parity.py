@@ -130,6 +130,31 @@ def test_bfs_fused(g2, rmat14, grid, lb, monkeypatch):
         assert st["launches"] == 1 and st["iterations"] == od.max() + 1
 
 
+@pytest.mark.parametrize("lb", ["CM", "WM", "VERTEX_BASED", "ETWC"])
+def test_bfs_fused_direction_optimising(g2, rmat14, grid, lb):
+    """The direction-optimising hybrid in one launch: PUSH levels from a list,
+    PULL levels over a bitmap, the representation converted where the
+    direction changes; depth and the canonical parent bit-exact for the
+    thresholds that always pull, switch, and always push, on power-law,
+    grid, directed, star and path graphs."""
+    # star(10000): ETWC hands the centre's 9,984-arc CTA part to the
+    # grid-wide pass inside the launch
+    graphs = [rmat14, grid, gg.gnp(400, 0.02, 11, symmetric=False), gg.star(3000),
+              gg.star(10000), gg.path(700), gg.from_arcs(5, [], [])]
+    pull = g2.schedule("VERTEX_BASED", direction=g2.G2_PULL, pull_frontier=g2.G2_BITMAP,
+                       frontier_creation=g2.G2_UNFUSED_BITMAP, dedup=False, kernel_fusion=True)
+    for g in graphs:
+        src = g.max_degree_vertex() if g.m else 0
+        od, op = oracle.bfs_graph(g, src)
+        for tau in (0.0, 0.02, 0.3, 2.0):
+            h = g2.hybrid(g2.schedule(lb, kernel_fusion=True), pull, tau)
+            d, p = run_bfs(g2, g, src, h)
+            assert np.array_equal(d, od), (g.name, lb, tau)
+            assert np.array_equal(p, op), (g.name, lb, tau)
+            st = g2.g2_last_stats()
+            assert st["launches"] == 1 and st["iterations"] == od.max() + 1, (g.name, lb, tau, st)
+
+
 def _handover_launches(levels, hi, lo):
     """Launches of a fused WM BFS whose levels (vertex counts by depth) move
     between the one-cluster loop (until a level holds more than `hi`) and the
