@@ -257,10 +257,13 @@ g2_status g2_edgeset_apply(g2_graph *g, g2_op op, g2_frontier *in, void *vdata, 
  * the levels of up to 1024 vertices per cluster CTA (16384 with 16-CTA
  * clusters) inside one thread-block cluster and hands larger levels to the
  * grid-wide kernel (back below half that size), one launch per hand-over.
- * NULL schedule:
- * direction-optimising hybrid, STRICT PUSH below 2% of n, VERTEX_BASED PULL
- * over a bitmap otherwise; on a bounded-degree graph (largest out-degree
- * <= 32: road networks, meshes) fused WM PUSH instead. */
+ * A hybrid with kernel fusion on both schedules and s2 VERTEX_BASED PULL over
+ * a bitmap runs in one cooperative kernel too, choosing the direction per
+ * level (ETWC's CTA-stage entries of 4096 arcs or more go to a grid-wide
+ * pass inside the launch).  NULL schedule: that fused hybrid, ETWC PUSH below
+ * 2% of n, VERTEX_BASED PULL over a bitmap otherwise; on a bounded-degree
+ * graph (largest out-degree <= 32: road networks, meshes) fused WM PUSH
+ * instead. */
 g2_status g2_bfs(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                  const g2_hybrid *sched, void *stream);
 
@@ -314,8 +317,9 @@ g2_status g2_pagerank(g2_graph *g, float damping, int32_t iters, float *rank,
  * bounded-degree graph the levels of at most 256 vertices per cluster CTA run
  * inside one thread-block cluster (forward and backward), the larger ones in
  * the grid-wide kernel.  NULL schedule: the
- * direction-optimising hybrid of g2_bfs; fused WM PUSH on a bounded-degree
- * graph (largest out-degree <= 32). */
+ * direction-optimising hybrid as per-level launches (STRICT PUSH below 2% of
+ * n, VERTEX_BASED PULL); fused WM PUSH on a bounded-degree graph (largest
+ * out-degree <= 32). */
 g2_status g2_bc(g2_graph *g, const int32_t *srcs, int32_t k, double *bc,
                 const g2_hybrid *sched, void *stream);
 
