@@ -142,21 +142,19 @@ def make_graph(scale: int):
 
 
 def bfs_schedule(g2):
-    """The library's tuned BFS schedule (NULL): the direction-optimising
-    hybrid (Table III) fused into one launch, ETWC PUSH while |frontier| < 2%
-    of n, else VERTEX_BASED PULL over a bitmap.  Used where BFS runs alone."""
+    """The library's tuned BFS schedule (NULL): direction-optimising hybrid
+    (Table III), STRICT PUSH on a sparse queue while |frontier| < 2% of n,
+    else VERTEX_BASED PULL over a bitmap input with an unfused bitmap output
+    and no deduplication."""
     return None
 
 
-def bfs_step_schedule(g2):
-    """The same hybrid as per-level launches (STRICT PUSH below 2% of n, else
-    VERTEX_BASED PULL over a bitmap with an unfused bitmap output and no
-    deduplication), for BFS beside PageRank: its short kernels interleave
-    with PageRank's whole-SM sweeps, where the fused form's cooperative grid
-    holds SMs for its whole run."""
+def bfs_fused_hybrid(g2):
+    """The same hybrid fused into one cooperative launch (ETWC PUSH, its large
+    entries handed to a grid-wide pass inside the launch)."""
     pull = g2.schedule("VERTEX_BASED", direction=g2.G2_PULL, pull_frontier=g2.G2_BITMAP,
-                       frontier_creation=g2.G2_UNFUSED_BITMAP, dedup=False)
-    return g2.hybrid(g2.schedule("STRICT"), pull, 0.02)
+                       frontier_creation=g2.G2_UNFUSED_BITMAP, dedup=False, kernel_fusion=True)
+    return g2.hybrid(g2.schedule("ETWC", kernel_fusion=True), pull, 0.02)
 
 
 def cc_schedule(g2):
@@ -185,7 +183,7 @@ def run_ours(args):
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     label = torch.empty(n, dtype=torch.int32, device="cuda")
     rank_t = torch.empty(n, dtype=torch.float32, device="cuda")
-    sb, sc = bfs_step_schedule(g2), cc_schedule(g2)
+    sb, sc = bfs_schedule(g2), cc_schedule(g2)
     launches = {"n": 0}
     # BFS and CC are independent of PageRank: in a step they run from two
     # worker threads, each on a graph view (own workspace) and a stream of its
@@ -308,7 +306,7 @@ def run_ours(args):
     e2e = run_e2e(args, g2, G, src, sb, sc, edges_per_step) if not args.no_e2e else None
     extras = None
     if rank == 0 and ws == 1 and not args.no_extras:
-        extras = run_extras(g2, G, dg, src, bfs_schedule(g2), sc)
+        extras = run_extras(g2, G, dg, src, sb, sc)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(G, src, budget_s=args.cpu_budget)
@@ -325,9 +323,6 @@ def run_ours(args):
                        "n": n, "m": m, "src": src, "pr_rounds": PR_ITERS, "damping": DAMPING,
                        "edges_per_step": edges_per_step, "bfs_reached_arcs": m_bfs,
                        "bfs_parent": True,
-                       "bfs_schedule": "direction-optimising hybrid as per-level launches (STRICT PUSH "
-                                       "below 2% of n, VERTEX_BASED PULL); workloads.rmat22_bfs: the "
-                                       "library's tuned schedule, the same hybrid fused into one launch",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (CSR 513 MB vs 129 MB L2); no flush"},
             "per_algo": {"bfs_ms": round(bfs_ms, 4), "cc_ms": round(cc_ms, 4), "pr_ms": round(pr_ms, 4),
@@ -500,12 +495,16 @@ def run_extras(g2, G22, dg22, src22, sb, sc):
         g2.g2_set_count_arcs(False)
         ms = _timed(lambda: g2.g2_bfs(dg, src, depth, parent, sb), reps=7)
         ms_np = _timed(lambda: g2.g2_bfs(dg, src, depth, None, sb), reps=7)
+        # the same hybrid fused into one launch, from the same source
+        fh = bfs_fused_hybrid(g2)
+        ms_fh = _timed(lambda: g2.g2_bfs(dg, src, depth, parent, fh), reps=7)
         reached = reached_arcs(G, depth, -1)
         b = 4 * bfs_arcs + 12 * n
         rows = {"bfs": {"ms": round(ms, 4), "gteps": round(reached / ms / 1e6, 2), "reached_arcs": reached,
                         "arcs_examined": int(bfs_arcs), "bytes": int(b),
                         "achieved_gbs": round(b / ms / 1e6, 1), "frac": round(b / ms / 1e6 / peak, 4),
-                        "ms_without_parent": round(ms_np, 4)}}
+                        "ms_without_parent": round(ms_np, 4),
+                        "fused_hybrid_ms": round(ms_fh, 4)}}
         if with_cc:
             ms = _timed(lambda: g2.g2_cc(dg, label, sc), reps=7)
             b = 4 * cc_arcs + 8 * n
