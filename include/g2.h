@@ -259,11 +259,12 @@ g2_status g2_edgeset_apply(g2_graph *g, g2_op op, g2_frontier *in, void *vdata, 
  * grid-wide kernel (back below half that size), one launch per hand-over.
  * A hybrid with kernel fusion on both schedules and s2 VERTEX_BASED PULL over
  * a bitmap runs in one cooperative kernel too, choosing the direction per
- * level (ETWC's CTA-stage entries of 4096 arcs or more go to a grid-wide
- * pass inside the launch).  NULL schedule: direction-optimising hybrid as
- * per-level launches, STRICT PUSH below 2% of n, VERTEX_BASED PULL over a
- * bitmap otherwise; on a bounded-degree graph (largest out-degree <= 32:
- * road networks, meshes) fused WM PUSH instead. */
+ * level; its PUSH half is VERTEX_BASED, WM, CM, ETWC (CTA-stage entries of
+ * 4096 arcs or more go to a grid-wide pass inside the launch) or STRICT (the
+ * prefix sum of the level's degrees taken over the grid inside the launch).
+ * NULL schedule: that fused direction-optimising hybrid, STRICT PUSH below 2%
+ * of n, VERTEX_BASED PULL over a bitmap otherwise; on a bounded-degree graph
+ * (largest out-degree <= 32: road networks, meshes) fused WM PUSH instead. */
 g2_status g2_bfs(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                  const g2_hybrid *sched, void *stream);
 

@@ -542,25 +542,29 @@ static bool bounded_degree(g2_graph *g, cudaStream_t st) {
 }
 
 // Tuned schedule for BFS when the caller passes none (measured on GB300 with
-// RMAT-22): direction-optimising hybrid, STRICT PUSH on a sparse queue while
-// the frontier holds < 2% of the vertices, else VERTEX_BASED PULL over a
-// bitmap input with an unfused bitmap output and no deduplication.  (The
-// same hybrid fused into one launch is faster from RMAT-22's hub, 0.24 ms
-// against 0.34, but up to four times slower from sources whose PUSH levels
-// carry hub arcs: ETWC's stages leave the persistent grid unbalanced where
-// STRICT divides the arcs evenly.)  On a bounded-degree graph: fused WM PUSH
-// (measured on a 1024^2 road grid: 7.2 ms against 35 ms for the hybrid).
+// RMAT-21 and RMAT-22): the direction-optimising hybrid fused into one
+// launch, STRICT PUSH on a sparse queue while the frontier holds < 2% of the
+// vertices, else VERTEX_BASED PULL over a bitmap.  Against the same hybrid
+// as per-level launches it is faster from every source measured (RMAT-22,
+// the hub and 8 random sources: 5.7 ms against 6.9 ms in all; from the hub
+// 0.26 against 0.35 ms): no frontier size goes back to the host per level.
+// STRICT divides a level's arcs evenly over the persistent grid where ETWC's
+// stages leave it unbalanced behind hub arcs (fused ETWC: 20.8 ms over the
+// same sources).  On a bounded-degree graph: fused WM PUSH (measured on a
+// 1024^2 road grid: 7.2 ms against 35 ms for the hybrid).
 static g2_hybrid tuned_bfs_hybrid(g2_graph *g, cudaStream_t st) {
     if (bounded_degree(g, st)) return fused_wm_hybrid();
     g2_hybrid h = default_hybrid();
     h.criteria = G2_INPUT_VERTEXSET_SIZE;
     h.threshold = 0.02f;
     h.s1.load_balance = G2_LB_STRICT;
+    h.s1.kernel_fusion = 1;
     h.s2.load_balance = G2_LB_VERTEX_BASED;
     h.s2.direction = G2_PULL;
     h.s2.pull_frontier = G2_BITMAP;
     h.s2.frontier_creation = G2_UNFUSED_BITMAP;
     h.s2.dedup = G2_DEDUP_DISABLED;
+    h.s2.kernel_fusion = 1;
     return h;
 }
 

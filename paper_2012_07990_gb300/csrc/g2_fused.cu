@@ -101,6 +101,8 @@ struct FusedDoBfsArgs {
     uint32_t *bm[2];     // frontier bitmaps, (n + 31) / 32 words each
     int32_t *bcnt;       // [3] bitmap populations, 0 at launch
     int32_t push_below;  // PUSH while the frontier holds fewer vertices
+    int32_t *scan;       // STRICT: prefix sums of a PUSH level's degrees (n + 1) ...
+    int32_t *ctasum;     // ... and the slice totals of the CTAs (one per CTA)
     EtwcEntry<int32_t> *spq;  // ETWC: a level's entries of kEtwcSpill arcs or more ...
     int32_t *spcnt;           // ... and their counts per level parity, 0 at launch
     int32_t *result;     // [0] levels, [1] PULL levels
@@ -109,6 +111,48 @@ struct FusedDoBfsArgs {
     uint64_t limit_ns;
     unsigned long long *ctr;
 };
+
+// STRICT inside a fused loop: scan[i] = the degrees of list entries before i
+// and scan[size] = their sum, over the whole grid in two phases separated by
+// barriers (each CTA scans an equal slice of the list and leaves its total,
+// then adds the totals of the slices before its own).  False: a barrier
+// wait gave up (the error word says why).
+__device__ bool fused_strict_scan(const DevGraph &g, const int32_t *q, int32_t size,
+                                  int32_t *scan, int32_t *ctasum, const GridBarrier &bar,
+                                  int32_t *err, uint64_t limit_ns) {
+    __shared__ int s_warp[kWarps];
+    __shared__ int s_part[kWarps];
+    const int bid = blockIdx.x, nb = gridDim.x;
+    const int32_t i0 = (int32_t)((int64_t)size * bid / nb);
+    const int32_t i1 = (int32_t)((int64_t)size * (bid + 1) / nb);
+    int run = 0;
+    for (int32_t t = i0; t < i1; t += kCta) {
+        const int32_t i = t + (int32_t)threadIdx.x;
+        int dg = 0;
+        if (i < i1) {
+            const int32_t u = q[i];
+            dg = g.rowptr[u + 1] - g.rowptr[u];
+        }
+        int tot;
+        const int incl = block_incl_scan(dg, s_warp, &tot);
+        if (i < i1) scan[i] = run + incl - dg;
+        run += tot;
+        __syncthreads();  // s_warp is read above before the next tile writes it
+    }
+    if (threadIdx.x == 0) ctasum[bid] = run;
+    if (!grid_sync(bar, err, limit_ns)) return false;
+    int part = 0;
+    for (int j = threadIdx.x; j < bid; j += kCta) part += ctasum[j];
+    part = __reduce_add_sync(G2_FULL, (unsigned)part);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+    __syncthreads();
+    int off = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) off += s_part[w];
+    for (int32_t i = i0 + (int32_t)threadIdx.x; i < i1; i += kCta) scan[i] += off;
+    if (bid == nb - 1 && threadIdx.x == 0) scan[size] = off + run;
+    return grid_sync(bar, err, limit_ns);
+}
 
 template <int LB>
 __global__ void __launch_bounds__(kCta) k_bfs_fused_do(FusedDoBfsArgs a) {
@@ -181,6 +225,13 @@ __global__ void __launch_bounds__(kCta) k_bfs_fused_do(FusedDoBfsArgs a) {
                     lb_etwc_spill(a.g, a.spq, spc, op, out, blockIdx.x, gridDim.x);
                     if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
                 }
+            } else if (LB == G2_LB_STRICT) {
+                // the same number of arcs for every thread of the grid
+                if (!fused_strict_scan(a.g, a.q[d & 1], size, a.scan, a.ctasum, a.bar, a.err,
+                                       a.limit_ns))
+                    return;
+                lb_strict(a.g, fin, size, a.scan, op, out, blockIdx.x, gridDim.x, a.ctr);
+                if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
             } else {
                 run_lb<LB>(a.g, fin, size, op, out, a.ctr);
                 if (!grid_sync(a.bar, a.err, a.limit_ns)) return;
@@ -945,7 +996,15 @@ g2_status bfs_fused(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
 // vertices.
 g2_status bfs_fused_do(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                        const g2_hybrid &h, cudaStream_t st, int32_t *d_err) {
-    G2_TRY(check_fused_lb(h.s1));
+    // the PUSH half: a load balancing of the fused loops, or STRICT (its
+    // prefix sum taken inside the launch)
+    if (h.s1.load_balance == G2_LB_STRICT) {
+        g2_schedule s1 = h.s1;
+        s1.load_balance = G2_LB_WM;
+        G2_TRY(check_fused_lb(s1));
+    } else {
+        G2_TRY(check_fused_lb(h.s1));
+    }
     if (h.criteria != G2_INPUT_VERTEXSET_SIZE)
         return fail(G2_EUNSUPPORTED, "a fused hybrid switches on the input vertexset size");
     if (h.s2.direction != G2_PULL || h.s2.load_balance != G2_LB_VERTEX_BASED ||
@@ -967,6 +1026,13 @@ g2_status bfs_fused_do(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent
     a.bcnt = ctrs + 46;  // [46..48]
     a.spq = nullptr;
     a.spcnt = nullptr;
+    a.scan = nullptr;
+    a.ctasum = nullptr;
+    if (h.s1.load_balance == G2_LB_STRICT) {
+        // one slice total per CTA: at most 2,048 threads, so 8 CTAs, per SM
+        G2_TRY(ws(g, B_SCAN, (size_t)n + 1, &a.scan));
+        G2_TRY(ws(g, B_SCANTMP, (size_t)t->sm_count * (2048 / kCta) + 1, &a.ctasum));
+    }
     if (h.s1.load_balance == G2_LB_ETWC) {
         // every handed-off entry has at least kEtwcSpill arcs
         const size_t cap = (size_t)t->m / kEtwcSpill + 1;
@@ -995,6 +1061,7 @@ g2_status bfs_fused_do(g2_graph *g, int32_t src, int32_t *depth, int32_t *parent
         case G2_LB_WM: G2_TRY(launch_coop(g, k_bfs_fused_do<G2_LB_WM>, a, st, want)); break;
         case G2_LB_CM: G2_TRY(launch_coop(g, k_bfs_fused_do<G2_LB_CM>, a, st, want)); break;
         case G2_LB_ETWC: G2_TRY(launch_coop(g, k_bfs_fused_do<G2_LB_ETWC>, a, st, want)); break;
+        case G2_LB_STRICT: G2_TRY(launch_coop(g, k_bfs_fused_do<G2_LB_STRICT>, a, st, want)); break;
         default: G2_TRY(launch_coop(g, k_bfs_fused_do<G2_LB_VERTEX_BASED>, a, st, want)); break;
     }
     G2_TRY(read_counters(g, ctrs + 24, 2, st, d_err));

@@ -130,7 +130,7 @@ def test_bfs_fused(g2, rmat14, grid, lb, monkeypatch):
         assert st["launches"] == 1 and st["iterations"] == od.max() + 1
 
 
-@pytest.mark.parametrize("lb", ["CM", "WM", "VERTEX_BASED", "ETWC"])
+@pytest.mark.parametrize("lb", ["CM", "WM", "VERTEX_BASED", "ETWC", "STRICT"])
 def test_bfs_fused_direction_optimising(g2, rmat14, grid, lb):
     """The direction-optimising hybrid in one launch: PUSH levels from a list,
     PULL levels over a bitmap, the representation converted where the
@@ -138,7 +138,8 @@ def test_bfs_fused_direction_optimising(g2, rmat14, grid, lb):
     thresholds that always pull, switch, and always push, on power-law,
     grid, directed, star and path graphs."""
     # star(10000): ETWC hands the centre's 9,984-arc CTA part to the
-    # grid-wide pass inside the launch
+    # grid-wide pass inside the launch; STRICT takes its prefix sum over the
+    # grid inside the launch (the path: one vertex per level)
     graphs = [rmat14, grid, gg.gnp(400, 0.02, 11, symmetric=False), gg.star(3000),
               gg.star(10000), gg.path(700), gg.from_arcs(5, [], [])]
     pull = g2.schedule("VERTEX_BASED", direction=g2.G2_PULL, pull_frontier=g2.G2_BITMAP,
@@ -258,8 +259,9 @@ def test_eight_cta_clusters(g2, grid, monkeypatch):
 
 def test_null_schedule_follows_the_degree_bound(g2, rmat14, grid):
     """With no schedule, a bounded-degree graph (road grid, largest degree
-    <= 32) runs BFS, SSSP and BC as one fused kernel; a power-law graph runs
-    the direction-optimising rounds.  Results are the oracle's either way."""
+    <= 32) runs BFS, SSSP and BC as one fused kernel; on a power-law graph
+    BFS runs the direction-optimising hybrid fused into one launch, with
+    PULL levels.  Results are the oracle's either way."""
     w = gg.pair_weights(grid, 1000, seed=2)
     dg = g2.load_graph(grid, w)
     od, op = oracle.bfs_graph(grid, 3)
@@ -276,9 +278,12 @@ def test_null_schedule_follows_the_degree_bound(g2, rmat14, grid):
     assert bc_close(host(bc), oracle.bc_graph(grid, [3, 77]))
     dr = g2.load_graph(rmat14)
     d = dev(rmat14.n)
-    g2.g2_bfs(dr, 0, d, None, None)
-    assert np.array_equal(host(d), oracle.bfs_graph(rmat14, 0)[0])
-    assert g2.g2_last_stats()["launches"] > 1
+    p = dev(rmat14.n)
+    g2.g2_bfs(dr, 0, d, p, None)
+    od, op = oracle.bfs_graph(rmat14, 0)
+    assert np.array_equal(host(d), od) and np.array_equal(host(p), op)
+    st = g2.g2_last_stats()
+    assert st["launches"] == 1 and st["pull_rounds"] > 0, st
 
 
 def test_bfs_edge_cases(g2):
