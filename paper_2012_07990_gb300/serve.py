@@ -160,6 +160,16 @@ class GpuExecutor:
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.views = [{name: g.handle.view() for name, g in pool.graphs.items()} for _ in range(slots)]
         self.fused = g2.schedule("WM", kernel_fusion=True)
+        # A single BFS on a power-law graph: with several slots, the tuned
+        # hybrid's schedules as per-level launches, whose small kernels
+        # interleave with the other slots' work (the fused form's cooperative
+        # launch needs every SM at once, so the slots' launches would run one
+        # at a time); with one slot, the library's tuned schedule (NULL).
+        self.powerlaw_bfs = None
+        if slots > 1:
+            pull = g2.schedule("VERTEX_BASED", direction=g2.G2_PULL, pull_frontier=g2.G2_BITMAP,
+                               frontier_creation=g2.G2_UNFUSED_BITMAP, dedup=False)
+            self.powerlaw_bfs = g2.hybrid(g2.schedule("STRICT"), pull, 0.02)
 
     def execute(self, slot: int, batch: list[Request]) -> dict:
         import torch
@@ -175,7 +185,8 @@ class GpuExecutor:
             if r0.kind == "bfs":
                 out = torch.empty(k * n, dtype=torch.int32, device="cuda")
                 if k == 1:
-                    g2.g2_bfs(view, int(srcs[0]), out, None, single)
+                    g2.g2_bfs(view, int(srcs[0]), out, None,
+                              single if pg.spec.road else self.powerlaw_bfs)
                 else:
                     g2.g2_bfs_batch(view, srcs, out, None)
             elif r0.kind == "sssp":
