@@ -961,7 +961,7 @@ g2_status g2_load_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
     t->max_out_deg = -1;
     t->pr_hot = -1; t->pr_hot_min_deg = 0; t->pr_slot_of = t->pr_ccol = nullptr;
     t->seg_head = nullptr; t->seg_nzrow = t->seg_chunk_rank = nullptr; t->seg_nnzrow = 0;
-    t->blk_S = 0; t->blk_nb = 0; t->blk_nchunks = 0; t->blk_nruns = 0;
+    t->blk_S = 0; t->blk_nb = 0; t->blk_nchunks = 0; t->blk_nruns = 0; t->blk_nact = 0;
     t->blk_loc = nullptr; t->blk_lane_heads = nullptr;
     t->blk_chunk_rank = t->blk_nzrow = t->blk_bchunk = t->blk_order = t->blk_deg = nullptr;
     t->blk_cta = nullptr; t->blk_G = 0;

@@ -141,6 +141,7 @@ struct Topology {
     int32_t blk_G;            // CTAs of the sweep (one per SM)
     int64_t blk_nchunks;
     int32_t blk_nruns;
+    int32_t blk_nact;         // ranks with out-arcs (they come first)
     uint16_t *blk_loc;
     uint16_t *blk_lane_heads;
     int32_t *blk_chunk_rank, *blk_nzrow, *blk_bchunk, *blk_order, *blk_deg;

@@ -455,18 +455,20 @@ __global__ void __launch_bounds__(kCta) k_pr_blk_init(const int32_t *deg, int32_
     }
 }
 
-// After a sweep: x_t from y, the next shares, the next D; y back to zero.
-// A thread takes U groups of four consecutive ranks (16-byte loads and
-// stores), the groups of a CTA adjacent, all U groups' loads issued before
-// their arithmetic; the last round also writes x_t to the caller's array in
-// vertex order.  D's partial sums meet in shared memory: one fp64 reduction
-// per CTA.
+// After a sweep: x_t from y, the next shares, the next D; y back to zero,
+// over ranks [0, n).  A thread takes U groups of four consecutive ranks
+// (16-byte loads and stores), the groups of a CTA adjacent, all U groups'
+// loads issued before their arithmetic; the last round also writes x_t to
+// the caller's array in vertex order.  D's partial sums meet in shared
+// memory: one fp64 reduction per CTA.  ntail isolated vertices ranked after
+// n (no arc in or out: y = 0, no share) are left out, their x_t being the
+// same for all: CTA 0 adds ntail * x_t to D.
 template <bool WRITE_X, int U>
 __global__ void __launch_bounds__(kCta) k_pr_blk_vertex(const int32_t *deg, const int32_t *order,
-                                                        int32_t n, float *y, float *share_next,
-                                                        float *x, const double *dprev,
-                                                        double *dslots, float base, float damp,
-                                                        double inv_n) {
+                                                        int32_t n, int32_t ntail, float *y,
+                                                        float *share_next, float *x,
+                                                        const double *dprev, double *dslots,
+                                                        float base, float damp, double inv_n) {
     __shared__ float s_d[kCta / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t cta0 = (int64_t)blockIdx.x * (kCta * 4 * U);
@@ -527,6 +529,8 @@ __global__ void __launch_bounds__(kCta) k_pr_blk_vertex(const int32_t *deg, cons
             }
         }
     }
+    if (ntail > 0 && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(dslots, (double)ntail * (double)(base + damp * (0.f + dterm)));
     // D partial of the CTA into one of the fp64 slots; the next sweep folds them
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(G2_FULL, dsum, o);
     if (lane == 0) s_d[warp] = dsum;
@@ -660,6 +664,8 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
     k_blk_vkey<<<grid, kCta, 0, st>>>(t->rowptr, n, vkey);
     int64_t vtotal = 0;
     G2_TRY(stable_partition(g, vkey, 1, n, kDegBuckets, 1, rank, vstart, &vtotal, st));
+    // the first rank without out-arcs (bucket 0 is ranked last)
+    G2_CK(cudaMemcpyAsync(g->h_ctr + 52, vstart + (kDegBuckets - 1), 4, cudaMemcpyDeviceToHost, st));
     k_blk_order<<<grid, kCta, 0, st>>>(t->rowptr, rank, n, t->blk_order, t->blk_deg);
     G2_CK(cudaMemsetAsync(t->blk_order + n, 0, kPad * 4, st));
     G2_CK(cudaMemsetAsync(t->blk_deg + n, 0, kPad * 4, st));
@@ -761,6 +767,7 @@ g2_status ensure_blk_layout(g2_graph *g, int32_t S, cudaStream_t st) {
     t->blk_nb = nb;
     t->blk_G = G;
     t->blk_nchunks = total / kBlkArcs;
+    t->blk_nact = g->h_ctr[52];
     t->blk_S = S;
     return G2_OK;
 }
@@ -779,8 +786,11 @@ g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *ran
     G2_TRY(ws(g, B_F0, nshare_alloc, &cbuf[0]));
     G2_TRY(ws(g, B_F1, nshare_alloc, &cbuf[1]));
     G2_TRY(ws(g, B_F2, (size_t)n + 4, &y));
+    // In a symmetric graph a vertex without out-arcs has no in-arcs either:
+    // the non-final vertex passes leave those ranks (the last ones) out.
+    const int32_t nact = t->symmetric ? t->blk_nact : n;
     for (int i = 0; i < 2; ++i)
-        G2_CK(cudaMemsetAsync(cbuf[i] + n, 0, (nshare_alloc - n) * 4, st));
+        G2_CK(cudaMemsetAsync(cbuf[i] + nact, 0, (nshare_alloc - nact) * 4, st));
     G2_CK(cudaMemsetAsync(y, 0, ((size_t)n + 4) * 4, st));
     constexpr size_t R = (size_t)kDSlots * kDStride;
     double *dd;
@@ -802,6 +812,7 @@ g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *ran
     constexpr int kVtxGroups = 2;  // 1: 14.9-15.1 us, 2: 13.5-13.8 us, 4: 14.7 us on RMAT-22
     constexpr int64_t kVtxSpan = (int64_t)kCta * 4 * kVtxGroups;
     const int vgrid = (int)(((int64_t)n + kVtxSpan - 1) / kVtxSpan);
+    const int vgrid_act = std::max(1, (int)(((int64_t)nact + kVtxSpan - 1) / kVtxSpan));
     for (int32_t it = 0; it < iters; ++it) {
         double *dprev = dd + 2 + (it & 1);
         KTime kt;
@@ -827,10 +838,11 @@ g2_status pagerank_blk_run(g2_graph *g, float damping, int32_t iters, float *ran
         float *sn = cbuf[(it + 1) & 1];
         if (it == iters - 1)
             k_pr_blk_vertex<true, kVtxGroups><<<vgrid, kCta, 0, st>>>(
-                t->blk_deg, t->blk_order, n, y, sn, rank, dprev, dd + 8, base, damping, inv_n);
+                t->blk_deg, t->blk_order, n, 0, y, sn, rank, dprev, dd + 8, base, damping, inv_n);
         else
-            k_pr_blk_vertex<false, kVtxGroups><<<vgrid, kCta, 0, st>>>(
-                t->blk_deg, t->blk_order, n, y, sn, rank, dprev, dd + 8, base, damping, inv_n);
+            k_pr_blk_vertex<false, kVtxGroups><<<vgrid_act, kCta, 0, st>>>(
+                t->blk_deg, t->blk_order, nact, n - nact, y, sn, rank, dprev, dd + 8, base,
+                damping, inv_n);
         ktime_end(kv, st);
         stats().launches += 2;
         stats().iterations++;
