@@ -1134,7 +1134,10 @@ def run_profile_case(args):
     capture names a committed command:
 
     * pr / bfs / cc: RMAT at --scale, the algorithm --steps times with the
-      tuned schedule;
+      tuned schedule (BFS: the direction-optimising hybrid fused into one
+      launch);
+    * bfs_levels: the same BFS hybrid as per-level launches (the bench
+      step's form);
     * road_fused: the --grid x --grid road grid (weights U[1, 1000]), one fused
       WM BFS from vertex 0 (no parent array) and one fused WM delta-stepping
       SSSP from vertex 0 with delta 1024 -- the one-cluster loops;
@@ -1218,6 +1221,8 @@ def run_profile_case(args):
             g2.g2_pagerank(dg, DAMPING, PR_ITERS, out)
         elif case == "bfs":
             g2.g2_bfs(dg, src, out, None, None)
+        elif case == "bfs_levels":
+            g2.g2_bfs(dg, src, out, None, bfs_per_level_hybrid(g2))
         else:
             g2.g2_cc(dg, out, None)
     torch.cuda.synchronize()
@@ -1227,8 +1232,8 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["pr", "bfs", "cc", "road_fused", "bc_rmat", "batch_grid",
-                                               "pr_layout"],
+    ap.add_argument("--profile-case", choices=["pr", "bfs", "bfs_levels", "cc", "road_fused", "bc_rmat",
+                                               "batch_grid", "pr_layout"],
                     default=None)
     ap.add_argument("--serve-pool", choices=["full", "small"], default="full")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
