@@ -23,6 +23,9 @@ from dataclasses import dataclass, field
 
 LBS = ["VERTEX_BASED", "CM", "WM", "STRICT", "EDGE_ONLY", "ETWC", "TWC"]
 PUSH_FRONTIER_LBS = ["VERTEX_BASED", "CM", "WM", "STRICT", "ETWC", "TWC"]
+# PUSH load balancing of a direction-optimising BFS hybrid fused into one
+# launch (its PULL half: VERTEX_BASED over a bitmap, fused too)
+FUSED_DO_PUSH_LBS = ["VERTEX_BASED", "WM", "CM", "ETWC", "STRICT"]
 PULL_LBS = ["VERTEX_BASED", "WM", "CM"]
 
 
@@ -43,6 +46,9 @@ def sample_schedule(algo: str, rng: random.Random) -> dict:
         if algo == "bfs" and rng.random() < 0.15:
             push.update(lb=rng.choice(["VERTEX_BASED", "WM", "CM", "ETWC"]), kernel_fusion=True)
             return {"criteria": 0, "threshold": 0.0, "s1": push, "s2": push}
+        if algo == "bfs" and rng.random() < 0.15:
+            return fused_do_hybrid(rng.choice(FUSED_DO_PUSH_LBS),
+                                   rng.choice([0.002, 0.005, 0.01, 0.02, 0.05, 0.1]))
         pull = _simple(lb=rng.choice(PULL_LBS), direction=1, pull_frontier=rng.randrange(2),
                        frontier_creation=rng.randrange(3), dedup=False)
         tau = rng.choice([0.0, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 1e9])
@@ -85,9 +91,22 @@ def sample_schedule(algo: str, rng: random.Random) -> dict:
     raise ValueError(f"unknown algorithm {algo}")
 
 
+def fused_do_hybrid(lb: str, tau: float) -> dict:
+    """The direction-optimising BFS hybrid in one cooperative launch: PUSH with
+    load balancing `lb` while the frontier holds fewer than tau * n vertices,
+    VERTEX_BASED PULL over a bitmap otherwise, kernel fusion on both."""
+    return {"criteria": 1, "threshold": tau, "s1": _simple(lb=lb, kernel_fusion=True),
+            "s2": _simple(lb="VERTEX_BASED", direction=1, pull_frontier=1, frontier_creation=2,
+                          dedup=False, kernel_fusion=True)}
+
+
 def seeds(algo: str) -> list[dict]:
     """Known-good starting points always included in the sample."""
-    if algo in ("bfs", "bc"):
+    if algo == "bfs":
+        # the library's tuned hybrid fused and as per-level launches, and the
+        # fused WM loop of bounded-degree graphs
+        return [fused_do_hybrid("STRICT", 0.02)] + seeds("bc")
+    if algo == "bc":
         return [{"criteria": 1, "threshold": 0.02, "s1": _simple(lb="STRICT"),
                  "s2": _simple(lb="VERTEX_BASED", direction=1, pull_frontier=1, frontier_creation=2,
                                dedup=False)},
@@ -155,8 +174,11 @@ class ExhaustiveResult:
 def exhaustive(cost, reps: int = 2, top: int = 4,
                thresholds=HYBRID_THRESHOLDS) -> ExhaustiveResult:
     """Time every simple schedule of both directions (each alone, criteria
-    NONE), then every hybrid of the `top` fastest PUSH and PULL schedules at
-    each threshold; the fastest of all is the optimum of the space."""
+    NONE), then every hybrid of the `top` fastest unfused PUSH and PULL
+    schedules at each threshold, and the direction-optimising hybrid fused
+    into one launch with each of its PUSH load balancings at each threshold
+    (algorithms without that form refuse it); the fastest of all is the
+    optimum of the space."""
     timed = []
     evaluated = rejected = 0
     per_dir = {}
@@ -190,6 +212,16 @@ def exhaustive(cost, reps: int = 2, top: int = 4,
                     rejected += 1
                     continue
                 timed.append((t, d))
+    for lb in FUSED_DO_PUSH_LBS:
+        for tau in thresholds:
+            d = fused_do_hybrid(lb, tau)
+            evaluated += 1
+            try:
+                t = min(cost(d) for _ in range(reps))
+            except Exception:
+                rejected += 1
+                continue
+            timed.append((t, d))
     timed.sort(key=lambda x: x[0])
     if not timed:
         raise RuntimeError("no schedule could be evaluated")

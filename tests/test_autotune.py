@@ -21,7 +21,13 @@ def test_samples_are_valid_points():
                 if s["direction"] == 1:
                     # PageRank's PULL + EDGE_ONLY is the arc-balanced CSC sweep
                     assert s["lb"] in at.PULL_LBS or (algo == "pr" and s["lb"] == "EDGE_ONLY")
-                if s["kernel_fusion"]:
+                if s["kernel_fusion"] and d["criteria"] == 1:
+                    # the direction-optimising BFS hybrid fused into one launch
+                    assert algo == "bfs" and d["s1"]["kernel_fusion"] and d["s2"]["kernel_fusion"]
+                    assert d["s1"]["direction"] == 0 and d["s1"]["lb"] in at.FUSED_DO_PUSH_LBS
+                    assert d["s2"]["direction"] == 1 and d["s2"]["lb"] == "VERTEX_BASED"
+                    assert d["s2"]["pull_frontier"] == 1
+                elif s["kernel_fusion"]:
                     assert s["lb"] in ("VERTEX_BASED", "WM", "CM", "ETWC") and s["direction"] == 0
                 if s["edge_blocking"]:
                     assert s["lb"] == "EDGE_ONLY"
@@ -71,8 +77,32 @@ def test_exhaustive_search_finds_the_optimum_and_drops_rejected_points():
     assert abs(res.best_ms - 4.5) < 1e-9
     assert res.rejected >= 336  # every EdgeBlocking point of both directions, fused PULL
     # every simple point of both directions, then the hybrids of the 4
-    # fastest PUSH x the 4 fastest PULL schedules (none fused here) at each threshold
-    assert res.evaluated == 2 * 336 + 4 * 4 * len(at.HYBRID_THRESHOLDS)
+    # fastest PUSH x the 4 fastest PULL schedules (none fused here) at each
+    # threshold, then the fused direction-optimising hybrid with each of its
+    # PUSH load balancings at each threshold (refused here: fused PULL)
+    nt = len(at.HYBRID_THRESHOLDS)
+    assert res.evaluated == 2 * 336 + 4 * 4 * nt + len(at.FUSED_DO_PUSH_LBS) * nt
+    assert res.rejected >= 336 + len(at.FUSED_DO_PUSH_LBS) * nt
+
+
+def test_exhaustive_search_includes_the_fused_direction_optimising_hybrid():
+    """Where the fused hybrid runs and is fastest (STRICT PUSH at 2% here),
+    the exhaustive search returns it, with both halves fused."""
+    def cost(d):
+        s1, s2 = d["s1"], d["s2"]
+        if s1["edge_blocking"] or s2["edge_blocking"]:
+            raise RuntimeError("unsupported")
+        if d["criteria"] == 1 and s1["kernel_fusion"] and s2["kernel_fusion"]:
+            return 1.0 + (0.0 if s1["lb"] == "STRICT" else 0.5) + abs(d["threshold"] - 0.02)
+        if s1["kernel_fusion"] != s2["kernel_fusion"] or (s1["direction"] == 1 and s1["kernel_fusion"]):
+            raise RuntimeError("unsupported")
+        return 3.0 + at.LBS.index(s1["lb"])
+
+    res = at.exhaustive(cost, reps=1)
+    assert res.best == at.fused_do_hybrid("STRICT", 0.02)
+    assert res.best_ms == 1.0
+    assert at.seeds("bfs")[0] == at.fused_do_hybrid("STRICT", 0.02)
+    assert all(not (s["s1"]["kernel_fusion"] and s["criteria"] == 1) for s in at.seeds("bc"))
 
 
 def test_successive_halving_finds_the_minimum_under_noise():
