@@ -270,6 +270,21 @@ def test_pagerank_closed_forms_and_sum():
     for g in [gg.cycle(11), gg.complete(7), gg.from_arcs(6, [], [])]:
         x = oracle.pagerank_graph(g, 0.85, 20)
         assert np.allclose(x, 1.0 / g.n, rtol=0, atol=1e-15)
+    # K_c beside k isolated vertices: every vertex of K_c holds a_t, every
+    # isolated one b_t, and only the isolated ones are dangling (D = k b), so
+    #   a_t = (1-d)/n + d (a_{t-1} + k b_{t-1} / n),  b_t = (1-d)/n + d k b_{t-1} / n
+    # from a_0 = b_0 = 1/n (by symmetry, in exact fractions)
+    c, k = 6, 9
+    n = c + k
+    g = gg.disjoint_union(gg.complete(c), gg.from_arcs(k, [], []))
+    d = Fraction(85, 100)
+    a = b = Fraction(1, n)
+    for _ in range(20):
+        a, b = (1 - d) / n + d * (a + k * b / n), (1 - d) / n + d * k * b / n
+    x = oracle.pagerank_graph(g, 0.85, 20)
+    assert np.allclose(x[:c], float(a), rtol=0, atol=1e-15)
+    assert np.allclose(x[c:], float(b), rtol=0, atol=1e-15)
+    assert c * a + k * b == 1
     g = gg.rmat(12)
     x = oracle.pagerank_graph(g, 0.85, 20)
     assert abs(x.sum() - 1.0) < 1e-12
